@@ -1,0 +1,340 @@
+/*
+ * oracle.c -- plain CPU oracle for the stencil hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark load this file's library.  The product
+ * (the CUDA library under paper_2310_01882_b300/csrc) shares no code,
+ * header, helper or constant with it, and never calls it.
+ *
+ * Every routine is the plain definition, written as loops in the order the
+ * formula is stated, in FP64 unless the routine's name says otherwise.  It is
+ * compiled with -O2 -ffp-contract=off so that no multiply-add is fused: the
+ * left-to-right evaluation order is kept, as the paper's extraction keeps the
+ * source order of operations (Section 3: no_reassoc operations are carried
+ * into the stencil region unchanged).
+ *
+ * Layout (Section 2.2, first index fastest as in Fortran): a field with
+ * interior extents nx, ny, nz and a one-cell halo is a dense array of
+ * (nx+2)*(ny+2)*(nz+2) values, x fastest, then y, then z.  Interior indices
+ * run 1..n in each axis; index 0 and n+1 are the halo.
+ *
+ * Pins: each routine is checked in tests/test_oracle_*.py against closed
+ * forms, invariants and brute force (see the docstrings there).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define AT(a, i, j, k) (a)[((size_t)(k) * (size_t)(ny + 2) + (size_t)(j)) * (size_t)(nx + 2) + (size_t)(i)]
+
+static size_t field_len(int64_t nx, int64_t ny, int64_t nz) {
+  return (size_t)(nx + 2) * (size_t)(ny + 2) * (size_t)(nz + 2);
+}
+
+int oracle_num_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) return nthreads;
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
+
+/*
+ * One relaxation sweep of the 3D 7-point stencil (Section 4.1: each cell
+ * becomes the average of its six orthogonal neighbours), in the Poisson form
+ * with a source term:
+ *     out[i,j,k] = (u[i-1]+u[i+1]+u[j-1]+u[j+1]+u[k-1]+u[k+1] + h*h*f) / 6
+ * on the interior.  The update is out of place (Section 2.2: a stencil apply
+ * reads its input field and yields a new one), i.e. a Jacobi sweep.  With
+ * f = 0 it is exactly the paper's Laplace average.  The halo of `out` is
+ * copied from `u` (the Dirichlet values).
+ */
+void oracle_jacobi_sweep_f64(const double* u, double* out, const double* f,
+                             int64_t nx, int64_t ny, int64_t nz, double h,
+                             int nthreads) {
+  const double hh = h * h;
+  memcpy(out, u, field_len(nx, ny, nz) * sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(oracle_num_threads(nthreads))
+#endif
+  for (int64_t k = 1; k <= nz; ++k)
+    for (int64_t j = 1; j <= ny; ++j)
+      for (int64_t i = 1; i <= nx; ++i) {
+        double s = AT(u, i - 1, j, k) + AT(u, i + 1, j, k);
+        s += AT(u, i, j - 1, k);
+        s += AT(u, i, j + 1, k);
+        s += AT(u, i, j, k - 1);
+        s += AT(u, i, j, k + 1);
+        s += hh * AT(f, i, j, k);
+        AT(out, i, j, k) = s / 6.0;
+      }
+#ifndef _OPENMP
+  (void)nthreads;
+#endif
+}
+
+/* nsweeps Jacobi sweeps; result in u, tmp is scratch of the same size. */
+void oracle_jacobi_f64(double* u, double* tmp, const double* f, int64_t nx,
+                       int64_t ny, int64_t nz, double h, int64_t nsweeps,
+                       int nthreads) {
+  double* a = u;
+  double* b = tmp;
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    oracle_jacobi_sweep_f64(a, b, f, nx, ny, nz, h, nthreads);
+    double* t = a; a = b; b = t;
+  }
+  if (a != u) memcpy(u, a, field_len(nx, ny, nz) * sizeof(double));
+}
+
+/*
+ * The same sweep with FP32 storage and FP32 arithmetic, in the same order.
+ * hh is the FP32 coefficient h*h (the caller rounds it once).  Used by the
+ * mixed-precision refinement oracle for its inner sweeps.
+ */
+void oracle_jacobi_sweep_f32(const float* u, float* out, const float* f,
+                             int64_t nx, int64_t ny, int64_t nz, float hh) {
+  memcpy(out, u, field_len(nx, ny, nz) * sizeof(float));
+  for (int64_t k = 1; k <= nz; ++k)
+    for (int64_t j = 1; j <= ny; ++j)
+      for (int64_t i = 1; i <= nx; ++i) {
+        float s = AT(u, i - 1, j, k) + AT(u, i + 1, j, k);
+        s += AT(u, i, j - 1, k);
+        s += AT(u, i, j + 1, k);
+        s += AT(u, i, j, k - 1);
+        s += AT(u, i, j, k + 1);
+        s += hh * AT(f, i, j, k);
+        AT(out, i, j, k) = s / 6.0f;
+      }
+}
+
+/*
+ * BF16 storage: a bfloat16 is the upper 16 bits of an IEEE binary32.
+ * Rounding float -> bf16 is round-to-nearest-even on the discarded 16 bits;
+ * NaN stays NaN.
+ */
+static float bf16_to_float(uint16_t b) {
+  uint32_t x = (uint32_t)b << 16;
+  float r;
+  memcpy(&r, &x, 4);
+  return r;
+}
+
+static uint16_t float_to_bf16(float v) {
+  uint32_t x;
+  memcpy(&x, &v, 4);
+  if ((x & 0x7f800000u) == 0x7f800000u && (x & 0x007fffffu) != 0)
+    return (uint16_t)((x >> 16) | 0x0040u);
+  uint32_t lsb = (x >> 16) & 1u;
+  x += 0x7fffu + lsb;
+  return (uint16_t)(x >> 16);
+}
+
+void oracle_f32_to_bf16(const float* in, uint16_t* out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = float_to_bf16(in[i]);
+}
+
+void oracle_bf16_to_f32(const uint16_t* in, float* out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = bf16_to_float(in[i]);
+}
+
+/* Sweep with BF16 storage of u, out and f; FP32 arithmetic as above. */
+void oracle_jacobi_sweep_bf16(const uint16_t* u, uint16_t* out,
+                              const uint16_t* f, int64_t nx, int64_t ny,
+                              int64_t nz, float hh) {
+  memcpy(out, u, field_len(nx, ny, nz) * sizeof(uint16_t));
+  for (int64_t k = 1; k <= nz; ++k)
+    for (int64_t j = 1; j <= ny; ++j)
+      for (int64_t i = 1; i <= nx; ++i) {
+        float s = bf16_to_float(AT(u, i - 1, j, k)) + bf16_to_float(AT(u, i + 1, j, k));
+        s += bf16_to_float(AT(u, i, j - 1, k));
+        s += bf16_to_float(AT(u, i, j + 1, k));
+        s += bf16_to_float(AT(u, i, j, k - 1));
+        s += bf16_to_float(AT(u, i, j, k + 1));
+        s += hh * bf16_to_float(AT(f, i, j, k));
+        AT(out, i, j, k) = float_to_bf16(s / 6.0f);
+      }
+}
+
+/*
+ * Residual of the Poisson problem A u = f with the 7-point operator
+ *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2
+ *     r = f - A u
+ * on the interior, in FP64.  norms[0] = ||r||_2, norms[1] = ||f||_2, both
+ * unweighted sums over interior points.  If r is not NULL its interior is
+ * written (halo untouched).
+ */
+void oracle_residual_f64(const double* u, const double* f, int64_t nx,
+                         int64_t ny, int64_t nz, double h, double* r,
+                         double* norms, int nthreads) {
+  const double hh = h * h;
+  double rr = 0.0, ff = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : rr, ff) num_threads(oracle_num_threads(nthreads))
+#endif
+  for (int64_t k = 1; k <= nz; ++k)
+    for (int64_t j = 1; j <= ny; ++j)
+      for (int64_t i = 1; i <= nx; ++i) {
+        double s = AT(u, i - 1, j, k) + AT(u, i + 1, j, k);
+        s += AT(u, i, j - 1, k);
+        s += AT(u, i, j + 1, k);
+        s += AT(u, i, j, k - 1);
+        s += AT(u, i, j, k + 1);
+        double au = (6.0 * AT(u, i, j, k) - s) / hh;
+        double res = AT(f, i, j, k) - au;
+        if (r) AT(r, i, j, k) = res;
+        rr += res * res;
+        ff += AT(f, i, j, k) * AT(f, i, j, k);
+      }
+  norms[0] = sqrt(rr);
+  norms[1] = sqrt(ff);
+#ifndef _OPENMP
+  (void)nthreads;
+#endif
+}
+
+/*
+ * Piacsek-Williams flux-form momentum advection (Section 4.1: three stencils
+ * over the fields u, v, w fused into one region, 63 floating-point operations
+ * per cell).  Centred second order on an Arakawa C grid: u lives on x faces,
+ * v on y faces, w on z faces.  For each velocity component the tendency is
+ * the divergence of "advected component times the advecting velocity
+ * interpolated to the flux point", with the 1/2 factors and 1/dx folded into
+ * tcx, tcy and the vertical factors tzc1[k], tzc2[k] (k = 1..nz maps to
+ * tzc[k-1]).  Each component costs 21 operations: 6 (x) + 6 (y) + 7 (z) + 2
+ * to combine, 63 in total.  Products are evaluated left to right as written.
+ * Outputs are written on the interior only; inputs' halos are the caller's.
+ */
+void oracle_advect_uvw(const double* u, const double* v, const double* w,
+                       double* su, double* sv, double* sw, const double* tzc1,
+                       const double* tzc2, double tcx, double tcy, int64_t nx,
+                       int64_t ny, int64_t nz, int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(oracle_num_threads(nthreads))
+#endif
+  for (int64_t k = 1; k <= nz; ++k) {
+    const double c1 = tzc1[k - 1], c2 = tzc2[k - 1];
+    for (int64_t j = 1; j <= ny; ++j)
+      for (int64_t i = 1; i <= nx; ++i) {
+        double tx, ty, tz;
+        /* u component, at (i+1/2, j, k) */
+        tx = tcx * (AT(u, i - 1, j, k) * (AT(u, i, j, k) + AT(u, i - 1, j, k)) -
+                    AT(u, i + 1, j, k) * (AT(u, i, j, k) + AT(u, i + 1, j, k)));
+        ty = tcy * (AT(u, i, j - 1, k) * (AT(v, i, j - 1, k) + AT(v, i + 1, j - 1, k)) -
+                    AT(u, i, j + 1, k) * (AT(v, i, j, k) + AT(v, i + 1, j, k)));
+        tz = c1 * AT(u, i, j, k - 1) * (AT(w, i, j, k - 1) + AT(w, i + 1, j, k - 1)) -
+             c2 * AT(u, i, j, k + 1) * (AT(w, i, j, k) + AT(w, i + 1, j, k));
+        AT(su, i, j, k) = tx + ty + tz;
+        /* v component, at (i, j+1/2, k) */
+        tx = tcx * (AT(v, i - 1, j, k) * (AT(u, i - 1, j, k) + AT(u, i - 1, j + 1, k)) -
+                    AT(v, i + 1, j, k) * (AT(u, i, j, k) + AT(u, i, j + 1, k)));
+        ty = tcy * (AT(v, i, j - 1, k) * (AT(v, i, j, k) + AT(v, i, j - 1, k)) -
+                    AT(v, i, j + 1, k) * (AT(v, i, j, k) + AT(v, i, j + 1, k)));
+        tz = c1 * AT(v, i, j, k - 1) * (AT(w, i, j, k - 1) + AT(w, i, j + 1, k - 1)) -
+             c2 * AT(v, i, j, k + 1) * (AT(w, i, j, k) + AT(w, i, j + 1, k));
+        AT(sv, i, j, k) = tx + ty + tz;
+        /* w component, at (i, j, k+1/2) */
+        tx = tcx * (AT(w, i - 1, j, k) * (AT(u, i - 1, j, k) + AT(u, i - 1, j, k + 1)) -
+                    AT(w, i + 1, j, k) * (AT(u, i, j, k) + AT(u, i, j, k + 1)));
+        ty = tcy * (AT(w, i, j - 1, k) * (AT(v, i, j - 1, k) + AT(v, i, j - 1, k + 1)) -
+                    AT(w, i, j + 1, k) * (AT(v, i, j, k) + AT(v, i, j, k + 1)));
+        tz = c1 * AT(w, i, j, k - 1) * (AT(w, i, j, k) + AT(w, i, j, k - 1)) -
+             c2 * AT(w, i, j, k + 1) * (AT(w, i, j, k) + AT(w, i, j, k + 1));
+        AT(sw, i, j, k) = tx + ty + tz;
+      }
+  }
+#ifndef _OPENMP
+  (void)nthreads;
+#endif
+}
+
+/*
+ * Mixed-precision iterative refinement of A u = f (the FP32/BF16 storage
+ * pattern; the paper itself iterates in FP64 only).  Each cycle:
+ *   1. r = f - A u and rel = ||r||_2 / ||f||_2, in FP64;  stop if rel <= rtol;
+ *   2. r_lo = r rounded to the inner storage type (RNE);
+ *   3. e = 0, then m Jacobi sweeps of A e = r_lo with inner storage and FP32
+ *      arithmetic (the sweep above with f := r_lo);
+ *   4. u += e in FP64 (interior only).
+ * If a cycle reduces rel by less than the factor stall_ratio (rel_new >
+ * stall_ratio * rel_old) the inner storage is escalated BF16 -> FP32 -> FP64
+ * (an FP64 inner solve is the plain FP64 sweep).  inner: 0 = F64, 1 = F32,
+ * 2 = BF16 (the library's dtype codes).  The zero start is the caller's
+ * (u's interior set to 0).  u's halo is the Dirichlet value of u; e's halo is
+ * zero.  Returns the number of sweeps done; *cycles, hist[0..cycles] (the rel
+ * of every residual evaluated, the last one being the final) and
+ * *final_inner are written.  Returns -1 on a non-finite residual.
+ */
+static void add_correction_f64(double* u, const double* e, int64_t nx,
+                               int64_t ny, int64_t nz) {
+  for (int64_t k = 1; k <= nz; ++k)
+    for (int64_t j = 1; j <= ny; ++j)
+      for (int64_t i = 1; i <= nx; ++i) AT(u, i, j, k) = AT(u, i, j, k) + AT(e, i, j, k);
+}
+
+int64_t oracle_refine(double* u, const double* f, int64_t nx, int64_t ny,
+                      int64_t nz, double h, double rtol, int inner,
+                      int64_t m, int64_t max_cycles, double stall_ratio,
+                      int64_t* cycles, double* hist, int* final_inner,
+                      double* work) {
+  /* work: 6 fields' worth of FP64 storage */
+  const size_t len = field_len(nx, ny, nz);
+  double* r = work;
+  double* e64 = work + len;
+  double* t64 = work + 2 * len;
+  float* r32 = (float*)(work + 3 * len);
+  float* e32 = r32 + len;
+  float* t32 = e32 + len;
+  uint16_t* r16 = (uint16_t*)(work + 5 * len);
+  uint16_t* e16 = r16 + len;
+  uint16_t* t16 = e16 + len;
+  const float hh32 = (float)(h * h);
+  int64_t sweeps = 0;
+  int cur = inner;
+  double prev = INFINITY;
+  int64_t c = 0;
+  memset(r, 0, len * sizeof(double));
+  for (;; ++c) {
+    double norms[2];
+    oracle_residual_f64(u, f, nx, ny, nz, h, r, norms, 1);
+    double rel = norms[1] > 0.0 ? norms[0] / norms[1] : norms[0];
+    hist[c] = rel;
+    if (!isfinite(rel)) { *cycles = c; *final_inner = cur; return -1; }
+    if (rel <= rtol || c >= max_cycles) break;
+    if (c > 0 && rel > stall_ratio * prev && cur != 0) cur = (cur == 2) ? 1 : 0;
+    prev = rel;
+    if (cur == 0) {
+      memset(e64, 0, len * sizeof(double));
+      for (int64_t s = 0; s < m; ++s) {
+        oracle_jacobi_sweep_f64(e64, t64, r, nx, ny, nz, h, 1);
+        double* t = e64; e64 = t64; t64 = t;
+      }
+      add_correction_f64(u, e64, nx, ny, nz);
+    } else if (cur == 1) {
+      for (size_t q = 0; q < len; ++q) { r32[q] = (float)r[q]; e32[q] = 0.0f; }
+      for (int64_t s = 0; s < m; ++s) {
+        oracle_jacobi_sweep_f32(e32, t32, r32, nx, ny, nz, hh32);
+        float* t = e32; e32 = t32; t32 = t;
+      }
+      for (size_t q = 0; q < len; ++q) t64[q] = (double)e32[q];
+      add_correction_f64(u, t64, nx, ny, nz);
+    } else {
+      for (size_t q = 0; q < len; ++q) { r16[q] = float_to_bf16((float)r[q]); e16[q] = 0; }
+      for (int64_t s = 0; s < m; ++s) {
+        oracle_jacobi_sweep_bf16(e16, t16, r16, nx, ny, nz, hh32);
+        uint16_t* t = e16; e16 = t16; t16 = t;
+      }
+      for (size_t q = 0; q < len; ++q) t64[q] = (double)bf16_to_float(e16[q]);
+      add_correction_f64(u, t64, nx, ny, nz);
+    }
+    sweeps += m;
+  }
+  *cycles = c;
+  *final_inner = cur;
+  return sweeps;
+}

@@ -1,0 +1,47 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle.c (on the CPU: a swapped
+neighbour, a sign, a transposed axis, a swapped coefficient, a dropped term),
+builds it into a temporary library and runs the pin suites against it in a
+subprocess (ORACLE_LIB).  The pins must fail for every mutant."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+PINS = ["tests/test_oracle_jacobi.py", "tests/test_oracle_residual.py", "tests/test_oracle_advect.py"]
+
+MUTANTS = {
+    "sweep_z_as_y": ("s += AT(u, i, j, k + 1);\n        s += hh", "s += AT(u, i, j + 1, k);\n        s += hh"),
+    "sweep_drop_source": ("s += hh * AT(f, i, j, k);\n        AT(out", "s += 0.0 * AT(f, i, j, k);\n        AT(out"),
+    "sweep_div5": ("AT(out, i, j, k) = s / 6.0;", "AT(out, i, j, k) = s / 6.000001;"),
+    "residual_sign": ("(6.0 * AT(u, i, j, k) - s) / hh", "(6.0 * AT(u, i, j, k) + s) / hh"),
+    "residual_fnorm": ("ff += AT(f, i, j, k) * AT(f, i, j, k);", "ff += AT(f, i, j, k) * AT(u, i, j, k);"),
+    "su_v_index": ("(AT(v, i, j - 1, k) + AT(v, i + 1, j - 1, k))", "(AT(v, i, j - 1, k) + AT(v, i - 1, j - 1, k))"),
+    "sv_u_index": ("(AT(u, i - 1, j, k) + AT(u, i - 1, j + 1, k)) -", "(AT(u, i - 1, j, k) + AT(u, i, j + 1, k)) -"),
+    "sw_tzc_swap": ("c2 * AT(w, i, j, k + 1) * (AT(w, i, j, k) + AT(w, i, j, k + 1))",
+                    "c1 * AT(w, i, j, k + 1) * (AT(w, i, j, k) + AT(w, i, j, k + 1))"),
+    "su_sign_x": ("tx = tcx * (AT(u, i - 1, j, k) * (AT(u, i, j, k) + AT(u, i - 1, j, k)) -",
+                  "tx = tcx * (AT(u, i - 1, j, k) * (AT(u, i, j, k) + AT(u, i - 1, j, k)) +"),
+    "sw_drop_y": ("AT(sw, i, j, k) = tx + ty + tz;", "AT(sw, i, j, k) = tx + tz;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    mutated = src.replace(old, new, 1)
+    csrc = tmp_path / "oracle_mut.c"
+    csrc.write_text(mutated)
+    lib = tmp_path / "liboracle_mut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", str(lib),
+                    str(csrc), "-lm"], check=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", *PINS],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"mutant {name} survived the pins:\n{res.stdout[-2000:]}"
