@@ -1,0 +1,356 @@
+"""Benchmark of the stencil hot path on one B300 (or N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (the throughput configuration): Jacobi 7-point Poisson relaxation on
+a 512^3 grid in FP64 storage, source f a k^-3 Gaussian random field (seed 2),
+u0 ~ U[0,1) (seed 3), zero Dirichlet halo, h = 1/513.  One step = 1000
+sweeps through stencil_jacobi_sweep.  Metric: GLUP/s (10^9 lattice-site
+updates per second) and the fraction of the measured HBM roofline.
+
+Side measurements on the same line: the same step with FP32 and BF16
+storage, the FP64 residual and the PW advection (512x512x256) throughput,
+an end-to-end run from pinned host buffers, and the CPU oracle on the
+host cores (a bounded sample).  Inputs (1.1 GB per FP64 field) are larger
+than the 126 MB L2, so no flush is needed between timed iterations.
+
+Multi-GPU: one process per GPU (torchrun); the work is replicated, not
+sharded (independent problems), so scaling is weak and no collective touches
+the data path.  Every rank prints nothing; rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512        # grid extent (--grid overrides, for profiling runs only)
+SWEEPS = 1000  # sweeps per step (--sweeps overrides)
+ALGO_BYTES = {"f64": 24, "f32": 12, "bf16": 6}   # read u, read f, write u' per lattice update
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs():
+    from paper_2310_01882_b300 import inputs
+    f = inputs.grf(N, seed=2)
+    u0 = inputs.uniform(N, N, N, seed=3)
+    return u0, f, 1.0 / (N + 1)
+
+
+def cpu_baseline(u0, f, h, budget_s=12.0):
+    """The oracle as it stands, on all host cores, for a bounded sample of
+    the workload: whole 512^3 sweeps until about budget_s seconds."""
+    import oracle
+    threads = oracle.num_threads(0)
+    t0 = time.perf_counter()
+    oracle.jacobi(u0, f, h, 1, nthreads=threads)
+    one = time.perf_counter() - t0
+    n = max(1, min(20, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.jacobi(u0, f, h, n, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": round(N ** 3 * n / dt / 1e9, 4), "unit": "GLUP/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n} FP64 Jacobi sweeps of the 512^3 grid (plain C oracle, OpenMP over z, {threads} threads)"}
+
+
+def reference_arm(args, rank):
+    """--impl reference: the CPU oracle timed on this machine's host cores."""
+    if rank != 0:
+        return
+    import oracle
+    u0, f, h = make_inputs()
+    threads = oracle.num_threads(0)
+    per_step_sweeps = 1
+    for _ in range(args.warmup):
+        oracle.jacobi(u0, f, h, per_step_sweeps, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.jacobi(u0, f, h, per_step_sweeps, nthreads=threads)
+    dt = time.perf_counter() - t0
+    value = N ** 3 * per_step_sweeps * args.steps / dt / 1e9
+    sample = f"each step: {per_step_sweeps} FP64 Jacobi sweep of the 512^3 grid (plain C oracle, {threads} threads)"
+    line = {"impl": "reference", "metric": "GLUP/s (512^3 FP64 Jacobi 7-point Poisson sweeps)", "value": round(value, 4),
+            "unit": "GLUP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "jacobi_512cubed_f64", "grid": [N, N, N], "sweeps_per_step": per_step_sweeps},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GLUP/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2310_01882_b300 import stencil as S
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ctx = S.Context(local_rank)
+    stream = torch.cuda.current_stream()
+    u0, f_np, h = make_inputs()
+    hbm_peak, peak_kind = load_peaks()
+
+    def fields(dtype):
+        u = S.Field.from_numpy(u0, dtype, device=dev)
+        f = S.Field.from_numpy(f_np, dtype, device=dev)
+        return u, u.like(), f
+
+    work = S.Field(N, N, N, S.F64, dev)  # FP64 workspace (resident fixed point)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_steps(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps
+
+    if args.only in ("f32", "bf16"):
+        dt = S.F32 if args.only == "f32" else S.BF16
+        u, ut, f = fields(dt)
+        ms = timed_steps(lambda: S.stencil_jacobi_sweep(ctx, u, ut, f, None, h, SWEEPS, args.spp, 0), args.steps,
+                         args.warmup)
+        S.stencil_ctx_status(ctx)
+        if rank == 0:
+            print(json.dumps({"metric": f"GLUP/s (profiling run, {args.only} step only)", "spp": args.spp,
+                              "value": round(N ** 3 * SWEEPS / (ms * 1e-3) / 1e9, 2), "unit": "GLUP/s",
+                              "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3)}))
+        ctx.close()
+        return
+
+    # ---- headline: FP64, 1000 sweeps per step --------------------------------
+    u, ut, f = fields(S.F64)
+
+    def step64():
+        S.stencil_jacobi_sweep(ctx, u, ut, f, work, h, SWEEPS, args.spp, S.SWEEP_AUTO)
+
+    with ClockSampler(local_rank) as clk:
+        ms = timed_steps(step64, args.steps, args.warmup)
+    S.stencil_ctx_status(ctx)
+    glups = N ** 3 * SWEEPS / (ms * 1e-3) / 1e9
+    # dominant kernel (the sweep kernel, 1000 launches per step): per-launch
+    # time bounded above by the step time / 1000 (the step also runs one
+    # range reduction and one halo copy).
+    per_launch_s = ms * 1e-3 / SWEEPS
+    achieved = N ** 3 * ALGO_BYTES["f64"] / per_launch_s / 1e9
+    launches_per_step = SWEEPS + 4  # halo copy, range, pack, 1000 sweeps, unpack
+
+    if args.only == "f64":
+        if rank == 0:
+            print(json.dumps({"metric": "GLUP/s (profiling run, FP64 step only)", "value": round(glups, 2),
+                              "unit": "GLUP/s", "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3)}))
+        ctx.close()
+        return
+    # ---- variants: FP32 / BF16 storage (sweeps per pass 1, 2, 4), FP64 ------
+    variants = {}
+    cases = [("f64_fixed_T2", S.F64, 0, 2), ("f64_native", S.F64, S.SWEEP_FP64_NATIVE, 1)]
+    variants_work = {"f64_fixed_T2": work}
+    for dname, dt in (("f32", S.F32), ("bf16", S.BF16)):
+        for T in (1, 2, 4):
+            cases.append((f"{dname}_T{T}", dt, 0, T))
+    for name, dt, flags, T in cases:
+        a, b, c = fields(dt)
+        nsw = SWEEPS if name != "f64_native" else 200
+        wk = variants_work.get(name)
+        vms = timed_steps(lambda: S.stencil_jacobi_sweep(ctx, a, b, c, wk, h, nsw, T, flags), 2, 1)
+        S.stencil_ctx_status(ctx)
+        gl = N ** 3 * nsw / (vms * 1e-3) / 1e9
+        bytes_per = ALGO_BYTES[name.split("_")[0]] / T
+        variants[name] = {"glups": round(gl, 2), "sweeps_per_pass": T, "ms_per_sweep": round(vms / nsw, 4),
+                          "hbm_gbs": round(gl * bytes_per, 1),
+                          "frac_of_measured_hbm": round(gl * bytes_per / hbm_peak, 4)}
+        del a, b, c
+    torch.cuda.empty_cache()
+
+    # ---- residual (FP64) -------------------------------------------------------
+    norms = torch.zeros(2, dtype=torch.float64, device=dev)
+    rms = timed_steps(lambda: S.stencil_residual(ctx, u, f, h, norms), 5, 2)
+    components = {"residual_f64": {"ms": round(rms, 3), "gpts": round(N ** 3 / (rms * 1e-3) / 1e9, 2)}}
+
+    # ---- advection 512x512x256 (FP64) -----------------------------------------
+    from paper_2310_01882_b300 import inputs
+    del u, ut, f, work
+    torch.cuda.empty_cache()
+    uw, vw, ww = inputs.winds(512, 512, 256)
+    fu, fv, fw = (S.Field.from_numpy(a, S.F64, device=dev) for a in (uw, vw, ww))
+    su, sv, sw = fu.like(), fu.like(), fu.like()
+    t1 = torch.from_numpy(inputs.tzc(256, 7)).to(dev)
+    t2 = torch.from_numpy(inputs.tzc(256, 8)).to(dev)
+    ams = timed_steps(lambda: S.stencil_advect_uvw(ctx, fu, fv, fw, su, sv, sw, t1, t2, 0.25, 0.25), 5, 2)
+    pts = 512 * 512 * 256
+    components["advect_f64"] = {"ms": round(ams, 3), "gpts": round(pts / (ams * 1e-3) / 1e9, 2),
+                                "hbm_gbs": round(48 * pts / (ams * 1e-3) / 1e9, 1),
+                                "frac_of_measured_hbm": round(48 * pts / (ams * 1e-3) / 1e9 / hbm_peak, 4)}
+    del fu, fv, fw, su, sv, sw
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the public API from pinned host buffers ------------
+    u_host = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+    f_host = torch.from_numpy(np.ascontiguousarray(f_np)).pin_memory()
+    out_host = torch.empty_like(u_host).pin_memory()
+    ue, ute, fe = S.Field(N, N, N, S.F64, dev), S.Field(N, N, N, S.F64, dev), S.Field(N, N, N, S.F64, dev)
+    work = S.Field(N, N, N, S.F64, dev)
+
+    def step_e2e():
+        ue.cells.copy_(u_host, non_blocking=True)
+        fe.cells.copy_(f_host, non_blocking=True)
+        S.stencil_jacobi_sweep(ctx, ue, ute, fe, work, h, SWEEPS, 0, S.SWEEP_AUTO)
+        out_host.copy_(ue.cells, non_blocking=True)
+
+    ems = timed_steps(step_e2e, 2, 1)
+    e2e = {"value": round(world * N ** 3 * SWEEPS / (ems * 1e-3) / 1e9, 2), "unit": "GLUP/s",
+           "h2d_bytes_per_step": int(u_host.numel() * 8 + f_host.numel() * 8),
+           "d2h_bytes_per_step": int(out_host.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(u0, f_np, h)
+
+    if rank == 0:
+        line = {
+            "metric": "GLUP/s and % HBM roofline at 1 B300 (512^3 FP64 Jacobi 7-point Poisson sweeps)",
+            "value": round(world * glups, 2), "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 storage, i64 fixed-point arithmetic", "data": "synthetic",
+            "config": {"workload": "jacobi_512cubed_f64", "grid": [N, N, N], "sweeps_per_step": SWEEPS,
+                       "source": "k^-3 Gaussian random field seed 2", "u0": "U[0,1) seed 3",
+                       "l2": "inputs 1.1 GB per field > 126 MB L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(achieved / hbm_peak, 4), "traffic": args.traffic,
+                         "kernel": "jacobi_tb<PolResident,T=1>", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": N ** 3 * ALGO_BYTES["f64"]},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "variants": variants,
+            "components": components,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--grid", type=int, default=None, help="grid extent (profiling runs; default 512)")
+    ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step (profiling runs; default 1000)")
+    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16"],
+                    help="run one dtype's step only (profiling runs)")
+    ap.add_argument("--spp", type=int, default=0, help="sweeps per pass for --only runs (0 = library default)")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu DRAM bytes per launch of the dominant kernel, if known")
+    args = ap.parse_args()
+    global N, SWEEPS
+    if args.grid:
+        N = args.grid
+    if args.sweeps:
+        SWEEPS = args.sweeps
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

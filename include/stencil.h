@@ -1,0 +1,207 @@
+/*
+ * stencil.h -- C ABI of the B300 stencil library (libstencil.so).
+ *
+ * The library applies the two stencil kernels measured in arXiv 2310.01882
+ * (Brown et al., SC-W 2023) over 3D structured grids on one GPU:
+ *   - the 7-point relaxation sweep (Section 4.1, "Gauss Seidel" benchmark:
+ *     each cell becomes the average of its six orthogonal neighbours), in
+ *     the Poisson form with a source term, applied out of place (Jacobi) as
+ *     a stencil apply is (Section 2.2);
+ *   - the Piacsek-Williams flux-form advection of u, v, w (Section 4.1,
+ *     three stencils fused into one region, 63 operations per cell);
+ * plus the FP64 residual used to judge convergence.
+ *
+ * Conventions (Section 2.2: first index fastest, offsets relative to the
+ * cell; Section 3: data crosses the boundary as raw pointers, and, with the
+ * optimised data approach of Section 4.3, stays resident on the device):
+ *   - A field is a stencil_grid: interior extents nx, ny, nz >= 1 and a
+ *     one-cell halo, stored x fastest.  `data` is a DEVICE pointer to the
+ *     halo cell (0,0,0); cell (i,j,k), 0 <= i <= nx+1 etc., is at
+ *     data + i + j*sy + k*sz (element strides, x stride 1).
+ *   - Interior cells are 1..n per axis; index 0 and n+1 are the halo, which
+ *     holds the boundary values (Dirichlet values for the Poisson routines,
+ *     caller-filled periodic/zero values for advection).
+ *   - Alignment: `data` must be 16-byte aligned and sy*elem, sz*elem must be
+ *     multiples of 16 bytes (the tiles are staged by the tensor-memory
+ *     accelerator); sy >= nx+2, sz >= sy*(ny+2).  Violations return
+ *     STENCIL_ERR_ALIGN or STENCIL_ERR_ARG and launch nothing.
+ *   - Ownership: the caller owns every grid and stream.  The library never
+ *     allocates, frees or copies caller memory to the host.  Scratch memory
+ *     belongs to the stencil_ctx (allocated in stencil_ctx_create).
+ *   - Asynchrony: every compute call only enqueues work on `stream` (a
+ *     cudaStream_t; NULL = the legacy default stream) and returns.  Errors
+ *     detected on the host are returned immediately; errors detected on the
+ *     device (a bounded wait that expired, a non-finite input to a
+ *     fixed-point sweep) are recorded in the ctx and returned by
+ *     stencil_ctx_status().
+ *   - Thread safety: one ctx per host thread (or external locking).  Calls
+ *     through the same ctx that overlap on the GPU (different streams) race
+ *     on its scratch memory.
+ *   - Errors: 0 on success, a negative STENCIL_ERR_* code otherwise;
+ *     stencil_last_error() describes the last error of the calling thread.
+ *     Nothing crosses the ABI as an exception, nothing prints or exits.
+ */
+#ifndef STENCIL_H_
+#define STENCIL_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STENCIL_API __attribute__((visibility("default")))
+#else
+#define STENCIL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STENCIL_OK 0
+#define STENCIL_ERR_ARG (-1)           /* bad argument or descriptor */
+#define STENCIL_ERR_ALIGN (-2)         /* pointer or stride alignment */
+#define STENCIL_ERR_DTYPE (-3)         /* unsupported dtype combination */
+#define STENCIL_ERR_CUDA (-4)          /* a CUDA runtime/driver call failed */
+#define STENCIL_ERR_TIMEOUT (-5)       /* a bounded device wait expired */
+#define STENCIL_ERR_NONFINITE (-6)     /* NaN/Inf input where not allowed */
+#define STENCIL_ERR_NOT_CONVERGED (-7) /* tolerance not reached */
+#define STENCIL_ERR_RANGE (-8)         /* values beyond the fixed-point range */
+
+typedef enum {
+  STENCIL_F64 = 0,  /* IEEE binary64 */
+  STENCIL_F32 = 1,  /* IEEE binary32 */
+  STENCIL_BF16 = 2  /* bfloat16 storage (upper half of a binary32) */
+} stencil_dtype;
+
+typedef struct {
+  void* data;             /* device pointer to halo cell (0,0,0) */
+  int64_t nx, ny, nz;     /* interior extents (>= 1) */
+  int64_t sy, sz;         /* element strides of y and z */
+  int32_t dtype;          /* stencil_dtype */
+  int32_t reserved;       /* must be 0 */
+} stencil_grid;
+
+typedef struct stencil_ctx stencil_ctx;
+
+/* Library version string (static storage). */
+STENCIL_API const char* stencil_version(void);
+
+/* Description of the calling thread's last error (static/thread storage). */
+STENCIL_API const char* stencil_last_error(void);
+
+/*
+ * Create a context bound to CUDA device `device`: allocates the scratch
+ * memory the routines below use (a few KB of reduction space).  *out
+ * receives the handle.  Not to be called while a stream capture is active.
+ */
+STENCIL_API int stencil_ctx_create(int device, stencil_ctx** out);
+
+/* Release a context and its scratch memory (synchronises the device). */
+STENCIL_API int stencil_ctx_destroy(stencil_ctx* ctx);
+
+/*
+ * Read and clear the device-side status of ctx: synchronises `stream`, then
+ * returns STENCIL_OK, STENCIL_ERR_TIMEOUT (a bounded wait inside a kernel
+ * expired; the kernel stopped early and its outputs are incomplete) or
+ * STENCIL_ERR_NONFINITE (a fixed-point sweep saw NaN/Inf input and wrote
+ * NaN to its output interior).
+ */
+STENCIL_API int stencil_ctx_status(stencil_ctx* ctx, void* stream);
+
+/* Sweep arithmetic for F64 grids (the `flags` argument below). */
+#define STENCIL_SWEEP_AUTO 0         /* library's choice (FIXED for F64) */
+#define STENCIL_SWEEP_FP64_NATIVE 1  /* binary64 adds/multiplies */
+#define STENCIL_SWEEP_FP64_FIXED 2   /* exact 64-bit fixed-point integers */
+
+/*
+ * stencil_jacobi_sweep -- nsweeps Jacobi sweeps of the 7-point Poisson
+ * relaxation (Section 4.1; Section 2.2 for the out-of-place apply):
+ *     u'[i,j,k] = (u[i-1,j,k] + u[i+1,j,k] + u[i,j-1,k] + u[i,j+1,k]
+ *                 + u[i,j,k-1] + u[i,j,k+1] + h*h*f[i,j,k]) / 6
+ * on the interior; the halo of u is the Dirichlet boundary and is never
+ * changed.  With f = 0 this is exactly the paper's Laplace average.
+ *
+ *   u        in/out: the iterate; the result of the last sweep ends in u.
+ *            (While the call runs its interior may hold other encodings.)
+ *   u_tmp    scratch grid of the same extents and dtype (its halo is
+ *            overwritten with u's halo; its interior is clobbered).
+ *   f        source, same extents and dtype as u.
+ *   work     NULL, or an F64 scratch grid of the same extents (interior
+ *            clobbered).  With it, F64 fixed-point sweeps convert u and f
+ *            once per call instead of once per pass (faster for nsweeps of
+ *            4 or more).  Ignored for F32/BF16 and FP64_NATIVE.
+ *   h        grid spacing (the coefficient is h*h).
+ *   nsweeps  >= 0 sweeps (0 is a no-op).
+ *   sweeps_per_pass  sweeps fused into one pass over HBM (temporal
+ *            blocking; 0 = library's choice; 1..8; the library uses the
+ *            largest compiled pass length not above it).
+ *   flags    STENCIL_SWEEP_* (F64 only; ignored for F32/BF16).
+ *
+ * dtype F64: binary64 storage.  FP64_NATIVE computes each sweep in binary64
+ * (adds in the order written, h*h*f fused, then a multiply by 1/6).
+ * FP64_FIXED (the default) computes in 64-bit fixed point with one scale per
+ * call, 2^-S, chosen from max|u| and max|f| with the maximum-principle bound
+ * of the iteration so that no sum can overflow (S = 58 - ceil(log2 B), B
+ * the bound on the six-neighbour sum); sums are exact, the division by 6 is
+ * rounded to the nearest 2^-S, and values are rounded to binary64 once per
+ * pass (without `work`) or once per call (with `work`).  The error is below
+ * that of binary64 arithmetic on the same sweeps.  FIXED needs finite inputs
+ * with |values| < 2^900 (otherwise the interior is set to NaN and the ctx
+ * status reports STENCIL_ERR_NONFINITE or STENCIL_ERR_RANGE).
+ * dtype F32: binary32 storage and arithmetic.  dtype BF16: bfloat16
+ * storage, binary32 arithmetic; each pass rounds to bfloat16 once
+ * (round-to-nearest-even), intermediate sweeps of a pass stay binary32.
+ */
+STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
+                         const stencil_grid* u_tmp, const stencil_grid* f,
+                         const stencil_grid* work, double h, int64_t nsweeps,
+                         int32_t sweeps_per_pass, int32_t flags, void* stream);
+
+/*
+ * stencil_residual -- the residual of A u = f for the 7-point operator
+ *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2,
+ *     r = f - A u on the interior,
+ * always in binary64 (the convergence judge of the iterative solve).
+ *   u, f      F64 grids of equal extents (u's halo is the boundary).
+ *   r         NULL, or an F64 grid of the same extents: its interior
+ *             receives r (halo untouched).
+ *   norms_dev DEVICE pointer to 2 doubles: ||r||_2 and ||f||_2 over the
+ *             interior (unweighted).  The sum order is fixed (per-block
+ *             partial sums combined in block order), so the result is
+ *             bitwise reproducible run to run.
+ * Uses ctx scratch memory.
+ */
+STENCIL_API int stencil_residual(stencil_ctx* ctx, const stencil_grid* u,
+                     const stencil_grid* f, double h, const stencil_grid* r,
+                     double* norms_dev, void* stream);
+
+/*
+ * stencil_advect_uvw -- Piacsek-Williams flux-form momentum advection
+ * (Section 4.1: three stencils over u, v, w fused into one region, 63
+ * floating-point operations per cell).  Centred second order on a C grid
+ * (u on x faces, v on y faces, w on z faces); for interior (i,j,k) and
+ * c1 = tzc1[k-1], c2 = tzc2[k-1]:
+ *   su = tcx*(u[i-1]*(u+u[i-1]) - u[i+1]*(u+u[i+1]))
+ *      + tcy*(u[j-1]*(v[j-1]+v[i+1,j-1]) - u[j+1]*(v+v[i+1]))
+ *      + c1*u[k-1]*(w[k-1]+w[i+1,k-1]) - c2*u[k+1]*(w+w[i+1])
+ *   sv = tcx*(v[i-1]*(u[i-1]+u[i-1,j+1]) - v[i+1]*(u+u[j+1]))
+ *      + tcy*(v[j-1]*(v+v[j-1]) - v[j+1]*(v+v[j+1]))
+ *      + c1*v[k-1]*(w[k-1]+w[j+1,k-1]) - c2*v[k+1]*(w+w[j+1])
+ *   sw = tcx*(w[i-1]*(u[i-1]+u[i-1,k+1]) - w[i+1]*(u+u[k+1]))
+ *      + tcy*(w[j-1]*(v[j-1]+v[j-1,k+1]) - w[j+1]*(v+v[k+1]))
+ *      + c1*w[k-1]*(w+w[k-1]) - c2*w[k+1]*(w+w[k+1])
+ * (unnamed offsets are 0).  All six grids F64 with equal extents; inputs'
+ * halos are filled by the caller; outputs are written on the interior only.
+ * tzc1, tzc2: DEVICE arrays of nz doubles.  Binary64 arithmetic.
+ */
+STENCIL_API int stencil_advect_uvw(stencil_ctx* ctx, const stencil_grid* u,
+                       const stencil_grid* v, const stencil_grid* w,
+                       const stencil_grid* su, const stencil_grid* sv,
+                       const stencil_grid* sw, const double* tzc1,
+                       const double* tzc2, double tcx, double tcy,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_H_ */

@@ -1,0 +1,270 @@
+// api.cu -- the C ABI (include/stencil.h): contexts, argument validation,
+// error reporting and TMA descriptors.  No compute happens here; every entry
+// point validates on the host, then enqueues kernels on the caller's stream.
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace stencil {
+
+static thread_local char g_last_error[512] = "no error";
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return STENCIL_OK;
+  return set_error(STENCIL_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int elem_size(int dtype) {
+  switch (dtype) {
+    case STENCIL_F64: return 8;
+    case STENCIL_F32: return 4;
+    case STENCIL_BF16: return 2;
+    default: return 0;
+  }
+}
+
+int validate_grid(const stencil_grid* g, const char* name, Grid* out, bool need_tma) {
+  if (!g) return set_error(STENCIL_ERR_ARG, "%s: null grid descriptor", name);
+  const int e = elem_size(g->dtype);
+  if (!e) return set_error(STENCIL_ERR_DTYPE, "%s: unknown dtype %d", name, g->dtype);
+  if (!g->data) return set_error(STENCIL_ERR_ARG, "%s: null data pointer", name);
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+    return set_error(STENCIL_ERR_ARG, "%s: extents must be >= 1 (got %lld x %lld x %lld)", name,
+                     (long long)g->nx, (long long)g->ny, (long long)g->nz);
+  if (g->nx > (1 << 30) || g->ny > (1 << 30) || g->nz > (1 << 30))
+    return set_error(STENCIL_ERR_ARG, "%s: extent too large", name);
+  if (g->sy < g->nx + 2 || g->sz < g->sy * (g->ny + 2))
+    return set_error(STENCIL_ERR_ARG, "%s: strides too small (sy=%lld sz=%lld)", name,
+                     (long long)g->sy, (long long)g->sz);
+  if (g->reserved != 0) return set_error(STENCIL_ERR_ARG, "%s: reserved field must be 0", name);
+  if (need_tma) {
+    if ((reinterpret_cast<uintptr_t>(g->data) & 15) != 0)
+      return set_error(STENCIL_ERR_ALIGN, "%s: data must be 16-byte aligned", name);
+    if (((g->sy * e) & 15) != 0 || ((g->sz * e) & 15) != 0)
+      return set_error(STENCIL_ERR_ALIGN, "%s: sy and sz must be multiples of 16 bytes", name);
+    if (g->nz + 2 > (1ll << 31) || g->sz * e >= (1ll << 40))
+      return set_error(STENCIL_ERR_ARG, "%s: grid too large for a tensor map", name);
+  }
+  out->data = g->data;
+  out->nx = g->nx; out->ny = g->ny; out->nz = g->nz;
+  out->sy = g->sy; out->sz = g->sz;
+  out->dtype = g->dtype;
+  out->elem = e;
+  return STENCIL_OK;
+}
+
+int same_extents(const Grid& a, const Grid& b, const char* an, const char* bn) {
+  if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz)
+    return set_error(STENCIL_ERR_ARG, "%s and %s have different extents", an, bn);
+  return STENCIL_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+int make_tensor_map(CUtensorMap* map, const Grid& g, int box_x, int box_y) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(STENCIL_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  CUtensorMapDataType dt = g.dtype == STENCIL_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                           : g.dtype == STENCIL_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                           : g.dtype == kDtypeU64   ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const cuuint64_t dims[3] = {(cuuint64_t)(g.nx + 2), (cuuint64_t)(g.ny + 2), (cuuint64_t)(g.nz + 2)};
+  const cuuint64_t strides[2] = {(cuuint64_t)(g.sy * g.elem), (cuuint64_t)(g.sz * g.elem)};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, dt, 3, g.data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return set_error(STENCIL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return STENCIL_OK;
+}
+
+// Make ctx's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  int rc = STENCIL_OK;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) rc = check_cuda(cudaSetDevice(dev), "cudaSetDevice");
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace stencil
+
+using namespace stencil;
+
+extern "C" {
+
+const char* stencil_version(void) { return "b300-stencil 0.1 (sm_103a)"; }
+
+const char* stencil_last_error(void) { return g_last_error; }
+
+int stencil_ctx_create(int device, stencil_ctx** out) {
+  if (!out) return set_error(STENCIL_ERR_ARG, "ctx_create: null out pointer");
+  *out = nullptr;
+  int n = 0;
+  int rc = check_cuda(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+  if (rc) return rc;
+  if (device < 0 || device >= n) return set_error(STENCIL_ERR_ARG, "ctx_create: bad device %d", device);
+  DeviceGuard dg(device);
+  if (dg.rc) return dg.rc;
+  cudaDeviceProp prop;
+  rc = check_cuda(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  if (rc) return rc;
+  if (prop.major < 10)
+    return set_error(STENCIL_ERR_CUDA, "device %d is sm_%d%d; this library is built for sm_103a",
+                     device, prop.major, prop.minor);
+  stencil_ctx* c = new (std::nothrow) stencil_ctx();
+  if (!c) return set_error(STENCIL_ERR_ARG, "ctx_create: out of host memory");
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  c->scratch_bytes = kScratchBytes;
+  void* p = nullptr;
+  rc = check_cuda(cudaMalloc(&p, c->scratch_bytes), "cudaMalloc(ctx scratch)");
+  if (rc) { delete c; return rc; }
+  c->scratch = static_cast<unsigned char*>(p);
+  rc = check_cuda(cudaMemset(p, 0, c->scratch_bytes), "cudaMemset(ctx scratch)");
+  if (rc) { cudaFree(p); delete c; return rc; }
+  *out = c;
+  return STENCIL_OK;
+}
+
+int stencil_ctx_destroy(stencil_ctx* ctx) {
+  if (!ctx) return STENCIL_OK;
+  DeviceGuard dg(ctx->device);
+  int rc = check_cuda(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  cudaFree(ctx->scratch);
+  delete ctx;
+  return rc;
+}
+
+int stencil_ctx_status(stencil_ctx* ctx, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "ctx_status: null ctx");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t bits = 0;
+  int rc = check_cuda(cudaMemcpyAsync(&bits, ctx->scratch + kScratchStatus, 4, cudaMemcpyDeviceToHost, st),
+                      "status read");
+  if (rc) return rc;
+  rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (rc) return rc;
+  rc = check_cuda(cudaMemsetAsync(ctx->scratch + kScratchStatus, 0, 4, st), "status clear");
+  if (rc) return rc;
+  rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (rc) return rc;
+  if (bits & kStatusTimeout) return set_error(STENCIL_ERR_TIMEOUT, "a bounded device wait expired");
+  if (bits & kStatusNonFinite)
+    return set_error(STENCIL_ERR_NONFINITE, "non-finite input to a fixed-point sweep");
+  if (bits & kStatusRange) return set_error(STENCIL_ERR_RANGE, "input beyond the fixed-point range");
+  return STENCIL_OK;
+}
+
+int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
+                         const stencil_grid* f, const stencil_grid* work, double h, int64_t nsweeps,
+                         int32_t sweeps_per_pass, int32_t flags, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "jacobi_sweep: null ctx");
+  Grid gu, gt, gf, gw;
+  int rc = validate_grid(u, "u", &gu, true);
+  if (!rc) rc = validate_grid(u_tmp, "u_tmp", &gt, true);
+  if (!rc) rc = validate_grid(f, "f", &gf, true);
+  if (!rc && work) rc = validate_grid(work, "work", &gw, true);
+  if (rc) return rc;
+  if ((rc = same_extents(gu, gt, "u", "u_tmp")) || (rc = same_extents(gu, gf, "u", "f"))) return rc;
+  if (work && (rc = same_extents(gu, gw, "u", "work"))) return rc;
+  if (gu.dtype != gt.dtype || gu.dtype != gf.dtype)
+    return set_error(STENCIL_ERR_DTYPE, "jacobi_sweep: u, u_tmp and f must share one dtype");
+  if (work && gw.dtype != STENCIL_F64)
+    return set_error(STENCIL_ERR_DTYPE, "jacobi_sweep: work must be F64");
+  if (gu.data == gt.data || gu.data == gf.data || gt.data == gf.data ||
+      (work && (gw.data == gu.data || gw.data == gt.data || gw.data == gf.data)))
+    return set_error(STENCIL_ERR_ARG, "jacobi_sweep: u, u_tmp, f and work must be distinct buffers");
+  if (nsweeps < 0) return set_error(STENCIL_ERR_ARG, "jacobi_sweep: nsweeps < 0");
+  if (sweeps_per_pass < 0 || sweeps_per_pass > 8)
+    return set_error(STENCIL_ERR_ARG, "jacobi_sweep: sweeps_per_pass must be 0..8");
+  if (flags < STENCIL_SWEEP_AUTO || flags > STENCIL_SWEEP_FP64_FIXED)
+    return set_error(STENCIL_ERR_ARG, "jacobi_sweep: unknown flags %d", flags);
+  if (!(h > 0.0) || !(h < 1.0e150)) return set_error(STENCIL_ERR_ARG, "jacobi_sweep: h must be positive and finite");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  const bool use_work = work && gu.dtype == STENCIL_F64;
+  return launch_jacobi(ctx, gu, gt, gf, use_work ? &gw : nullptr, h, nsweeps, sweeps_per_pass, flags,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int stencil_residual(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* f, double h,
+                     const stencil_grid* r, double* norms_dev, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "residual: null ctx");
+  Grid gu, gf, gr;
+  int rc = validate_grid(u, "u", &gu, false);
+  if (!rc) rc = validate_grid(f, "f", &gf, false);
+  if (!rc && r) rc = validate_grid(r, "r", &gr, false);
+  if (rc) return rc;
+  if ((rc = same_extents(gu, gf, "u", "f"))) return rc;
+  if (r && (rc = same_extents(gu, gr, "u", "r"))) return rc;
+  if (gu.dtype != STENCIL_F64 || gf.dtype != STENCIL_F64 || (r && gr.dtype != STENCIL_F64))
+    return set_error(STENCIL_ERR_DTYPE, "residual: u, f and r must be F64");
+  if (!norms_dev) return set_error(STENCIL_ERR_ARG, "residual: null norms pointer");
+  if (!(h > 0.0) || !(h < 1.0e150)) return set_error(STENCIL_ERR_ARG, "residual: h must be positive and finite");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  return launch_residual(ctx, gu, gf, h, r ? &gr : nullptr, norms_dev,
+                         static_cast<cudaStream_t>(stream));
+}
+
+int stencil_advect_uvw(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* v,
+                       const stencil_grid* w, const stencil_grid* su, const stencil_grid* sv,
+                       const stencil_grid* sw, const double* tzc1, const double* tzc2, double tcx,
+                       double tcy, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "advect: null ctx");
+  Grid g[6];
+  const stencil_grid* in[6] = {u, v, w, su, sv, sw};
+  const char* names[6] = {"u", "v", "w", "su", "sv", "sw"};
+  for (int i = 0; i < 6; ++i) {
+    int rc = validate_grid(in[i], names[i], &g[i], false);
+    if (rc) return rc;
+    if (g[i].dtype != STENCIL_F64) return set_error(STENCIL_ERR_DTYPE, "advect: %s must be F64", names[i]);
+    if (i && (rc = same_extents(g[0], g[i], names[0], names[i]))) return rc;
+  }
+  for (int i = 3; i < 6; ++i)
+    for (int j = 0; j < 6; ++j)
+      if (i != j && g[i].data == g[j].data)
+        return set_error(STENCIL_ERR_ARG, "advect: output %s aliases %s", names[i], names[j]);
+  if (!tzc1 || !tzc2) return set_error(STENCIL_ERR_ARG, "advect: null tzc pointer");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  return launch_advect(ctx, g[0], g[1], g[2], g[3], g[4], g[5], tzc1, tzc2, tcx, tcy,
+                       static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/stencil.h"
+
+struct stencil_ctx {
+  int device;
+  int num_sms;
+  unsigned char* scratch;  // device memory owned by the ctx
+  size_t scratch_bytes;
+};
+
+namespace stencil {
+
+// Device status bits (ctx scratch word), read back by stencil_ctx_status.
+constexpr uint32_t kStatusTimeout = 1u;
+constexpr uint32_t kStatusNonFinite = 2u;
+constexpr uint32_t kStatusRange = 4u;
+
+// Layout of the ctx scratch block (device memory).
+constexpr size_t kScratchStatus = 0;      // uint32 status bits
+constexpr size_t kScratchMaxU = 16;       // uint64 bits of max|u| (incl. halo)
+constexpr size_t kScratchMaxF = 24;       // uint64 bits of max|f| (interior)
+constexpr size_t kScratchPartials = 256;  // residual partial sums
+constexpr int kMaxPartials = 2048;        // blocks of the residual kernel
+constexpr size_t kScratchBytes = kScratchPartials + sizeof(double) * 2 * kMaxPartials;
+
+// Internal dtype code: biased 64-bit fixed-point iterate (never in the ABI).
+constexpr int kDtypeU64 = 100;
+// Below this many sweeps the resident fixed-point path costs more (one
+// conversion pass each way) than converting in every pass.
+constexpr int64_t kResidentMinSweeps = 4;
+
+// Validated view of a stencil_grid.
+struct Grid {
+  void* data;
+  int64_t nx, ny, nz, sy, sz;
+  int dtype;
+  int elem;
+};
+
+// Returns STENCIL_OK or an error code (and sets the thread's last error).
+int set_error(int code, const char* fmt, ...);
+int check_cuda(cudaError_t e, const char* what);
+int validate_grid(const stencil_grid* g, const char* name, Grid* out, bool need_tma);
+int same_extents(const Grid& a, const Grid& b, const char* an, const char* bn);
+
+// TMA descriptor of a 3D halo grid with box (bx, by, 1).
+int make_tensor_map(CUtensorMap* map, const Grid& g, int box_x, int box_y);
+
+// Kernel launchers (jacobi.cu, residual.cu, advect.cu).
+int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
+                  double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
+int launch_residual(stencil_ctx* ctx, const Grid& u, const Grid& f, double h, const Grid* r,
+                    double* norms_dev, cudaStream_t st);
+int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w, const Grid& su,
+                  const Grid& sv, const Grid& sw, const double* tzc1, const double* tzc2,
+                  double tcx, double tcy, cudaStream_t st);
+
+}  // namespace stencil

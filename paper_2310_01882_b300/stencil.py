@@ -1,0 +1,191 @@
+"""Thin Python binding of libstencil.so (include/stencil.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Fields live in torch CUDA tensors (torch is used for device memory
+and streams); the binding passes their raw device pointers and strides
+across the C ABI.  If the library has not been built, the first call raises;
+there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libstencil.so")
+
+F64, F32, BF16 = 0, 1, 2
+SWEEP_AUTO, SWEEP_FP64_NATIVE, SWEEP_FP64_FIXED = 0, 1, 2
+
+OK = 0
+ERRORS = {
+    -1: "STENCIL_ERR_ARG", -2: "STENCIL_ERR_ALIGN", -3: "STENCIL_ERR_DTYPE", -4: "STENCIL_ERR_CUDA",
+    -5: "STENCIL_ERR_TIMEOUT", -6: "STENCIL_ERR_NONFINITE", -7: "STENCIL_ERR_NOT_CONVERGED",
+    -8: "STENCIL_ERR_RANGE",
+}
+ELEM = {F64: 8, F32: 4, BF16: 2}
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class stencil_grid(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("sy", ctypes.c_int64), ("sz", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+# Every exported symbol of include/stencil.h, with its ctypes signature.
+_P = ctypes.c_void_p
+_G = ctypes.POINTER(stencil_grid)
+SIGNATURES = {
+    "stencil_version": ([], ctypes.c_char_p),
+    "stencil_last_error": ([], ctypes.c_char_p),
+    "stencil_ctx_create": ([ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "stencil_ctx_destroy": ([_P], ctypes.c_int),
+    "stencil_ctx_status": ([_P, _P], ctypes.c_int),
+    "stencil_jacobi_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
+                              ctypes.c_int32, _P], ctypes.c_int),
+    "stencil_residual": ([_P, _G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
+    "stencil_advect_uvw": ([_P, _G, _G, _G, _G, _G, _G, _P, _P, ctypes.c_double, ctypes.c_double, _P],
+                           ctypes.c_int),
+}
+
+
+def lib():
+    """Load libstencil.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2310_01882_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise StencilError(rc, lib().stencil_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Field:
+    """A halo-padded 3D field in a torch CUDA tensor.
+
+    Storage shape (nz+2, ny+2, sy) with sy = nx+2 rounded up to 16 bytes, so
+    every row starts 16-byte aligned; `.cells` is the (nz+2, ny+2, nx+2)
+    view of the grid cells, halo included (x fastest)."""
+
+    TORCH_DTYPES = None
+
+    def __init__(self, nx, ny, nz, dtype=F64, device="cuda", storage=None):
+        import torch
+        if Field.TORCH_DTYPES is None:
+            Field.TORCH_DTYPES = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}
+        self.nx, self.ny, self.nz, self.dtype = int(nx), int(ny), int(nz), dtype
+        g = 16 // ELEM[dtype]
+        self.sy = (self.nx + 2 + g - 1) // g * g
+        if storage is None:
+            storage = torch.zeros((self.nz + 2, self.ny + 2, self.sy), dtype=Field.TORCH_DTYPES[dtype],
+                                  device=device)
+        assert storage.shape == (self.nz + 2, self.ny + 2, self.sy) and storage.is_contiguous()
+        self.storage = storage
+        self.sz = self.sy * (self.ny + 2)
+
+    @property
+    def cells(self):
+        return self.storage[:, :, : self.nx + 2]
+
+    def grid(self):
+        return stencil_grid(self.storage.data_ptr(), self.nx, self.ny, self.nz, self.sy, self.sz,
+                            self.dtype, 0)
+
+    @classmethod
+    def from_numpy(cls, a, dtype=F64, device="cuda"):
+        """a: (nz+2, ny+2, nx+2) array (float64/float32; bf16 is rounded RNE)."""
+        import torch
+        nz, ny, nx = (s - 2 for s in a.shape)
+        f = cls(nx, ny, nz, dtype, device)
+        src = torch.from_numpy(np.ascontiguousarray(a))
+        f.cells.copy_(src.to(device=device, dtype=Field.TORCH_DTYPES[dtype]))
+        return f
+
+    def to_numpy(self, dtype=np.float64):
+        import torch
+        return self.cells.to(torch.float64).cpu().numpy().astype(dtype, copy=False)
+
+    def like(self):
+        return Field(self.nx, self.ny, self.nz, self.dtype, self.storage.device)
+
+
+class Context:
+    """Owns a stencil_ctx (its device scratch memory)."""
+
+    def __init__(self, device=0):
+        h = ctypes.c_void_p()
+        _check(lib().stencil_ctx_create(int(device), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().stencil_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stencil_version():
+    return lib().stencil_version().decode()
+
+
+def stencil_ctx_status(ctx, stream=None):
+    return _check(lib().stencil_ctx_status(ctx.handle, _stream(stream)))
+
+
+def stencil_jacobi_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, flags=SWEEP_AUTO,
+                         stream=None):
+    """work: None or an F64 Field of u's extents (see include/stencil.h)."""
+    gu, gt, gf = u.grid(), u_tmp.grid(), f.grid()
+    gw = work.grid() if work is not None else None
+    return _check(lib().stencil_jacobi_sweep(ctx.handle, ctypes.byref(gu), ctypes.byref(gt), ctypes.byref(gf),
+                                             ctypes.byref(gw) if gw is not None else None,
+                                             float(h), int(nsweeps), int(sweeps_per_pass), int(flags),
+                                             _stream(stream)))
+
+
+def stencil_residual(ctx, u, f, h, norms_dev, r=None, stream=None):
+    """norms_dev: a float64 CUDA tensor of >= 2 elements (receives ||r||, ||f||)."""
+    gu, gf = u.grid(), f.grid()
+    gr = r.grid() if r is not None else None
+    return _check(lib().stencil_residual(ctx.handle, ctypes.byref(gu), ctypes.byref(gf), float(h),
+                                         ctypes.byref(gr) if gr is not None else None,
+                                         ctypes.c_void_p(norms_dev.data_ptr()), _stream(stream)))
+
+
+def stencil_advect_uvw(ctx, u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, stream=None):
+    """tzc1, tzc2: float64 CUDA tensors of nz elements."""
+    gs = [x.grid() for x in (u, v, w, su, sv, sw)]
+    return _check(lib().stencil_advect_uvw(ctx.handle, *[ctypes.byref(g) for g in gs],
+                                           ctypes.c_void_p(tzc1.data_ptr()), ctypes.c_void_p(tzc2.data_ptr()),
+                                           float(tcx), float(tcy), _stream(stream)))
