@@ -175,6 +175,37 @@ STENCIL_API int stencil_residual(stencil_ctx* ctx, const stencil_grid* u,
                      double* norms_dev, void* stream);
 
 /*
+ * stencil_residual_noalloc -- the same residual and norms as
+ * stencil_residual, for callers that cannot allocate device memory: code
+ * running where allocation is forbidden or unavailable (a host application
+ * that owns all device memory through its own allocator, a no-allocation
+ * real-time loop, a stream that is being captured), and that therefore
+ * cannot create a stencil_ctx either.  This call allocates nothing and takes
+ * no context: its partial sums live in a fixed array built into the
+ * library (128 KiB per device that loads the library, held until the
+ * process exits).  The paper has no counterpart; it is a deployment
+ * convenience.
+ *   u, f, h, r, norms_dev   as for stencil_residual; the grids must be on
+ *            the current CUDA device, and the call runs on `stream`.
+ *   Limit:   ny * nz <= 524288 (one partial sum per 64 rows, 8192 sums);
+ *            larger grids are rejected with STENCIL_ERR_ARG before any
+ *            launch (use stencil_residual with a context for them).
+ *   r values are bitwise those of stencil_residual; the norms use a
+ *   different (fixed) partition of the sum, so they agree to rounding and
+ *   are reproducible run to run.
+ *   The first call on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture.  Every call on a device shares the one array: calls
+ *   that overlap on the GPU (different streams, or threads without
+ *   ordering) race and give wrong norms.  Each call overwrites every
+ *   partial sum it reads, so nothing has to be cleared between calls.
+ */
+STENCIL_API int stencil_residual_noalloc(const stencil_grid* u,
+                                         const stencil_grid* f, double h,
+                                         const stencil_grid* r,
+                                         double* norms_dev, void* stream);
+
+/*
  * stencil_advect_uvw -- Piacsek-Williams flux-form momentum advection
  * (Section 4.1: three stencils over u, v, w fused into one region, 63
  * floating-point operations per cell).  Centred second order on a C grid

@@ -11,6 +11,7 @@
 // scratch, and summed in block order by a single-block kernel, so the norms
 // are reproducible bit for bit from run to run.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -117,4 +118,80 @@ int launch_residual(stencil_ctx* ctx, const Grid& u, const Grid& f, double h, co
                               r, norms_dev, st);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free residual (stencil_residual_noalloc).
+//
+// For callers that may not allocate device memory themselves and cannot hold
+// a stencil_ctx (whose creation allocates): the per-block partial sums live
+// in a fixed array compiled into this library, so the call allocates
+// nothing.  The array is shared by every call on a device, so calls that
+// overlap on that device race; every call overwrites all the partial sums
+// it reads, so nothing needs clearing between calls.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxPartials = 8192;   // partial-sum pairs the array holds (128 KiB)
+constexpr int kNoAllocRowsPerBlock = 64;    // interior (y, z) rows per block
+constexpr int64_t kNoAllocMaxRows = static_cast<int64_t>(kNoAllocMaxPartials) * kNoAllocRowsPerBlock;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[2 * kNoAllocMaxPartials];
+
+// Device address of g_noalloc_partials, looked up once per device (with that
+// device current) on the first call made on it.
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+static int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices)
+    return set_error(STENCIL_ERR_ARG, "residual_noalloc: device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    int rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials),
+                        "residual_noalloc: cudaGetSymbolAddress");
+    if (rc) return rc;
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return STENCIL_OK;
+}
+
 }  // namespace stencil
+
+extern "C" int stencil_residual_noalloc(const stencil_grid* u, const stencil_grid* f, double h,
+                                        const stencil_grid* r, double* norms_dev, void* stream) {
+  using namespace stencil;
+  Grid gu, gf, gr;
+  int rc = validate_grid(u, "u", &gu, false);
+  if (!rc) rc = validate_grid(f, "f", &gf, false);
+  if (!rc && r) rc = validate_grid(r, "r", &gr, false);
+  if (rc) return rc;
+  if ((rc = same_extents(gu, gf, "u", "f"))) return rc;
+  if (r && (rc = same_extents(gu, gr, "u", "r"))) return rc;
+  if (gu.dtype != STENCIL_F64 || gf.dtype != STENCIL_F64 || (r && gr.dtype != STENCIL_F64))
+    return set_error(STENCIL_ERR_DTYPE, "residual_noalloc: u, f and r must be F64");
+  if (!norms_dev) return set_error(STENCIL_ERR_ARG, "residual_noalloc: null norms pointer");
+  if (!(h > 0.0) || !(h < 1.0e150))
+    return set_error(STENCIL_ERR_ARG, "residual_noalloc: h must be positive and finite");
+  const int64_t rows = gu.ny * gu.nz;
+  if (rows > kNoAllocMaxRows)
+    return set_error(STENCIL_ERR_ARG,
+                     "residual_noalloc: ny*nz = %lld exceeds %lld, the most its built-in scratch "
+                     "(%d partial sums) covers; use stencil_residual with a context",
+                     (long long)rows, (long long)kNoAllocMaxRows, kNoAllocMaxPartials);
+  int device = -1;
+  rc = check_cuda(cudaGetDevice(&device), "residual_noalloc: cudaGetDevice");
+  if (rc) return rc;
+  double* partials = nullptr;
+  rc = noalloc_scratch(device, &partials);
+  if (rc) return rc;
+  const int blocks = static_cast<int>((rows + kNoAllocRowsPerBlock - 1) / kNoAllocRowsPerBlock);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  residual_kernel<<<blocks, dim3(32, kResWarps), 0, st>>>(
+      static_cast<const double*>(gu.data), static_cast<const double*>(gf.data),
+      r ? static_cast<double*>(gr.data) : nullptr, gu.nx, gu.ny, gu.nz, gu.sy, gu.sz, gf.sy, gf.sz,
+      r ? gr.sy : 0, r ? gr.sz : 0, h * h, partials);
+  rc = check_cuda(cudaGetLastError(), "residual_noalloc kernel");
+  if (rc) return rc;
+  residual_finish_kernel<<<1, 256, 0, st>>>(partials, blocks, norms_dev);
+  return check_cuda(cudaGetLastError(), "residual_noalloc finish kernel");
+}

@@ -54,6 +54,7 @@ SIGNATURES = {
     "stencil_residual": ([_P, _G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
     "stencil_advect_uvw": ([_P, _G, _G, _G, _G, _G, _G, _P, _P, ctypes.c_double, ctypes.c_double, _P],
                            ctypes.c_int),
+    "stencil_residual_noalloc": ([_G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
 }
 
 
@@ -181,6 +182,16 @@ def stencil_residual(ctx, u, f, h, norms_dev, r=None, stream=None):
     return _check(lib().stencil_residual(ctx.handle, ctypes.byref(gu), ctypes.byref(gf), float(h),
                                          ctypes.byref(gr) if gr is not None else None,
                                          ctypes.c_void_p(norms_dev.data_ptr()), _stream(stream)))
+
+
+def stencil_residual_noalloc(u, f, h, norms_dev, r=None, stream=None):
+    """stencil_residual without a context or any allocation (see
+    include/stencil.h for its limit and the shared scratch it uses)."""
+    gu, gf = u.grid(), f.grid()
+    gr = r.grid() if r is not None else None
+    return _check(lib().stencil_residual_noalloc(ctypes.byref(gu), ctypes.byref(gf), float(h),
+                                                 ctypes.byref(gr) if gr is not None else None,
+                                                 ctypes.c_void_p(norms_dev.data_ptr()), _stream(stream)))
 
 
 def stencil_advect_uvw(ctx, u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, stream=None):
