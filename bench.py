@@ -37,6 +37,15 @@ SWEEPS = 1000  # sweeps per step (--sweeps overrides)
 ALGO_BYTES = {"f64": 24, "f32": 12, "bf16": 6}   # read u, read f, write u' per lattice update
 
 
+# ncu DRAM bytes (read + write) per launch of the dominant kernel, measured on
+# a 320^3 launch and scaled by the lattice points to 512^3 (the traffic grows
+# with the points); keyed by the kernel configuration it was measured on.
+# Command: ncu --set full --clock-control none -k regex:jacobi_tb -s 3 -c 1
+#   python bench.py --grid 320 --sweeps 8 --only f64 --steps 1 --warmup 1 --no-cpu
+MEASURED_TRAFFIC = {"jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (617.844736e6 + 232.756480e6) * (512 / 320) ** 3}
+DOMINANT_KERNEL = "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>"
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -307,8 +316,11 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs 1.1 GB per field > 126 MB L2 (no flush needed)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                         "frac": round(achieved / hbm_peak, 4), "traffic": args.traffic,
-                         "kernel": "jacobi_tb<PolResident,T=1>", "peak_kind": peak_kind,
+                         "frac": round(achieved / hbm_peak, 4),
+                         "traffic": args.traffic if args.traffic is not None else
+                         (round(MEASURED_TRAFFIC[DOMINANT_KERNEL]) if N == 512 and DOMINANT_KERNEL in MEASURED_TRAFFIC
+                          else None),
+                         "kernel": DOMINANT_KERNEL, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": N ** 3 * ALGO_BYTES["f64"]},
             "cpu_baseline": cpu,
             "e2e": e2e,
