@@ -36,7 +36,7 @@ def lib():
         L.oracle_bf16_to_f32.argtypes = [p, p, i64]
         L.oracle_residual_f64.argtypes = [p, p, i64, i64, i64, d, p, p, i32]
         L.oracle_advect_uvw.argtypes = [p, p, p, p, p, p, p, p, d, d, i64, i64, i64, i32]
-        L.oracle_refine.argtypes = [p, p, i64, i64, i64, d, d, i32, i64, i64, d, p, p, p, p]
+        L.oracle_refine.argtypes = [p, p, i64, i64, i64, d, d, i32, i64, i64, d, p, p, i64, p, p, p]
         L.oracle_refine.restype = i64
         L.oracle_num_threads.argtypes = [i32]
         L.oracle_num_threads.restype = i32
@@ -149,19 +149,25 @@ def advect_uvw(u, v, w, tzc1, tzc2, tcx, tcy, nthreads=1):
 INNER_CODES = {"f64": 0, "f32": 1, "bf16": 2}
 
 
-def refine(u0, f, h, rtol, inner="f32", m=100, max_cycles=10000, stall_ratio=0.999):
-    """Mixed-precision refinement (see oracle_refine).  Returns a dict."""
+def refine(u0, f, h, rtol, inner="f32", m=100, max_sweeps=10 ** 7, stall_ratio=0.9999):
+    """Mixed-precision refinement (see oracle_refine).  Returns a dict with
+    u, sweeps, cycles, hist (rel of each residual evaluated), rel (final),
+    final_inner and status (0 converged, -7 not converged / stalled,
+    -6 non-finite)."""
     u = np.array(u0, dtype=np.float64, order="C", copy=True)
     f = _c64(f)
     nx, ny, nz = _dims(u)
-    hist = np.zeros(max_cycles + 1, dtype=np.float64)
+    hist_len = 100000
+    hist = np.zeros(hist_len, dtype=np.float64)
     cycles = np.zeros(1, dtype=np.int64)
     fin = np.zeros(1, dtype=np.int32)
+    status = np.zeros(1, dtype=np.int32)
     work = np.zeros(6 * u.size, dtype=np.float64)
     sweeps = lib().oracle_refine(_ptr(u), _ptr(f), nx, ny, nz, h, rtol, INNER_CODES[inner], m,
-                                 max_cycles, stall_ratio, _ptr(cycles), _ptr(hist), _ptr(fin),
-                                 _ptr(work))
+                                 max_sweeps, stall_ratio, _ptr(cycles), _ptr(hist), hist_len,
+                                 _ptr(fin), _ptr(status), _ptr(work))
     c = int(cycles[0])
     inv = {v: k for k, v in INNER_CODES.items()}
-    return {"u": u, "sweeps": int(sweeps), "cycles": c, "hist": hist[: c + 1].copy(),
-            "final_inner": inv[int(fin[0])], "rel": float(hist[c])}
+    n_hist = min(c + 1, hist_len)
+    return {"u": u, "sweeps": int(sweeps), "cycles": c, "hist": hist[:n_hist].copy(),
+            "final_inner": inv[int(fin[0])], "rel": float(hist[n_hist - 1]), "status": int(status[0])}

@@ -255,20 +255,23 @@ void oracle_advect_uvw(const double* u, const double* v, const double* w,
 
 /*
  * Mixed-precision iterative refinement of A u = f (the FP32/BF16 storage
- * pattern; the paper itself iterates in FP64 only).  Each cycle:
- *   1. r = f - A u and rel = ||r||_2 / ||f||_2, in FP64;  stop if rel <= rtol;
- *   2. r_lo = r rounded to the inner storage type (RNE);
- *   3. e = 0, then m Jacobi sweeps of A e = r_lo with inner storage and FP32
- *      arithmetic (the sweep above with f := r_lo);
- *   4. u += e in FP64 (interior only).
- * If a cycle reduces rel by less than the factor stall_ratio (rel_new >
- * stall_ratio * rel_old) the inner storage is escalated BF16 -> FP32 -> FP64
- * (an FP64 inner solve is the plain FP64 sweep).  inner: 0 = F64, 1 = F32,
- * 2 = BF16 (the library's dtype codes).  The zero start is the caller's
- * (u's interior set to 0).  u's halo is the Dirichlet value of u; e's halo is
- * zero.  Returns the number of sweeps done; *cycles, hist[0..cycles] (the rel
- * of every residual evaluated, the last one being the final) and
- * *final_inner are written.  Returns -1 on a non-finite residual.
+ * pattern; the paper itself iterates in FP64 only).  Cycle c = 0, 1, ...:
+ *   1. r = f - A u and rel_c = ||r||_2 / ||f||_2, in FP64;
+ *   2. stop with status 0 if rel_c <= rtol, with status -7 if sweeps >=
+ *      max_sweeps, with status -6 if rel_c is not finite;
+ *   3. if c > 0 and rel_c > stall_ratio * rel_{c-1}: BF16 inner storage
+ *      escalates to FP32; FP32 inner storage stops with status -7 (stalled);
+ *      FP64 inner storage is never checked;
+ *   4. r_lo = r rounded to the inner storage type (FP64 -> FP32 round to
+ *      nearest even, then FP32 -> BF16 round to nearest even for BF16);
+ *   5. e = 0, then m Jacobi sweeps of A e = r_lo with inner storage and FP32
+ *      arithmetic (the sweep above with f := r_lo; FP64 for inner = F64);
+ *   6. u += e in FP64 (interior only); sweeps += m.
+ * inner: 0 = F64, 1 = F32, 2 = BF16 (the library's dtype codes).  The zero
+ * start is the caller's (u's interior set to 0).  u's halo is the Dirichlet
+ * value; e's halo is zero.  Writes *cycles (corrections applied),
+ * hist[0..cycles] (rel of every residual evaluated, the last one final),
+ * *final_inner and *status; returns the number of sweeps done.
  */
 static void add_correction_f64(double* u, const double* e, int64_t nx,
                                int64_t ny, int64_t nz) {
@@ -279,9 +282,9 @@ static void add_correction_f64(double* u, const double* e, int64_t nx,
 
 int64_t oracle_refine(double* u, const double* f, int64_t nx, int64_t ny,
                       int64_t nz, double h, double rtol, int inner,
-                      int64_t m, int64_t max_cycles, double stall_ratio,
-                      int64_t* cycles, double* hist, int* final_inner,
-                      double* work) {
+                      int64_t m, int64_t max_sweeps, double stall_ratio,
+                      int64_t* cycles, double* hist, int64_t hist_len,
+                      int* final_inner, int* status, double* work) {
   /* work: 6 fields' worth of FP64 storage */
   const size_t len = field_len(nx, ny, nz);
   double* r = work;
@@ -298,15 +301,24 @@ int64_t oracle_refine(double* u, const double* f, int64_t nx, int64_t ny,
   int cur = inner;
   double prev = INFINITY;
   int64_t c = 0;
+  *status = 0;
   memset(r, 0, len * sizeof(double));
   for (;; ++c) {
     double norms[2];
     oracle_residual_f64(u, f, nx, ny, nz, h, r, norms, 1);
     double rel = norms[1] > 0.0 ? norms[0] / norms[1] : norms[0];
-    hist[c] = rel;
-    if (!isfinite(rel)) { *cycles = c; *final_inner = cur; return -1; }
-    if (rel <= rtol || c >= max_cycles) break;
-    if (c > 0 && rel > stall_ratio * prev && cur != 0) cur = (cur == 2) ? 1 : 0;
+    if (c < hist_len) hist[c] = rel;
+    if (!isfinite(rel)) { *status = -6; break; }
+    if (rel <= rtol) break;
+    if (sweeps >= max_sweeps) { *status = -7; break; }
+    if (c > 0 && cur != 0 && rel > stall_ratio * prev) {
+      if (cur == 2) {
+        cur = 1;
+      } else {
+        *status = -7;
+        break;
+      }
+    }
     prev = rel;
     if (cur == 0) {
       memset(e64, 0, len * sizeof(double));

@@ -16,8 +16,8 @@ def test_f64_inner_equals_plain_jacobi():
     n = 10
     f = inputs.grf(n, seed=21)
     h = 1.0 / (n + 1)
-    res = oracle.refine(np.zeros_like(f), f, h, rtol=0.0, inner="f64", m=7, max_cycles=9)
-    assert res["sweeps"] == 63 and res["cycles"] == 9
+    res = oracle.refine(np.zeros_like(f), f, h, rtol=0.0, inner="f64", m=7, max_sweeps=63)
+    assert res["sweeps"] == 63 and res["cycles"] == 9 and res["status"] == -7
     plain = oracle.jacobi(np.zeros_like(f), f, h, 63)
     assert np.max(np.abs(res["u"] - plain)) <= 1e-13 * np.max(np.abs(plain))
     nr, nf = oracle.residual(plain, f, h)
@@ -29,6 +29,7 @@ def test_f32_inner_reaches_target():
     f = inputs.grf(n, seed=22)
     h = 1.0 / (n + 1)
     res = oracle.refine(np.zeros_like(f), f, h, rtol=1e-8, inner="f32", m=50)
+    assert res["status"] == 0
     nr, nf = oracle.residual(res["u"], f, h)
     assert nr / nf <= 1e-8 and abs(res["rel"] - nr / nf) <= 1e-12
     ud = exact.solve(f, h)
@@ -61,16 +62,21 @@ def test_bf16_inner_converges():
     assert np.max(rates) <= 1.2 * mu ** 100
 
 
-def test_stall_escalates_storage():
-    """A cycle that reduces rel by less than stall_ratio escalates the inner
-    storage bf16 -> f32 -> f64; the solve still reaches the target."""
+def test_stall_escalates_then_stops():
+    """A cycle that reduces rel by less than stall_ratio escalates BF16 storage
+    to FP32; a further stall in FP32 stops the solve (status -7), at a
+    residual no worse than the last one evaluated."""
     n = 16
     f = inputs.grf(n, seed=25)
     h = 1.0 / (n + 1)
     res = oracle.refine(np.zeros_like(f), f, h, rtol=1e-8, inner="bf16", m=20, stall_ratio=0.2)
-    assert res["final_inner"] == "f64"
+    assert res["final_inner"] == "f32" and res["status"] == -7
+    hist = res["hist"]
+    # the first stall is where the reduction fell short of 0.2
+    k = next(i for i in range(1, len(hist)) if hist[i] > 0.2 * hist[i - 1])
+    assert len(hist) > k + 1
     nr, nf = oracle.residual(res["u"], f, h)
-    assert nr / nf <= 1e-8
+    assert abs(nr / nf - res["rel"]) <= 1e-12 * res["rel"]
 
 
 def test_nonfinite_source_reported():
@@ -78,4 +84,4 @@ def test_nonfinite_source_reported():
     f = inputs.grf(n, seed=24)
     f[3, 3, 3] = np.nan
     res = oracle.refine(np.zeros_like(f), f, 1.0 / 7, rtol=1e-8)
-    assert res["sweeps"] == -1
+    assert res["status"] == -6 and res["sweeps"] == 0
