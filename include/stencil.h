@@ -90,7 +90,8 @@ STENCIL_API const char* stencil_last_error(void);
 
 /*
  * Create a context bound to CUDA device `device`: allocates the scratch
- * memory the routines below use (a few KB of reduction space).  *out
+ * memory the routines below use (a few KB of reduction space on the device
+ * and one pinned host word).  *out
  * receives the handle.  Not to be called while a stream capture is active.
  */
 STENCIL_API int stencil_ctx_create(int device, stencil_ctx** out);
@@ -173,6 +174,74 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
 STENCIL_API int stencil_residual(stencil_ctx* ctx, const stencil_grid* u,
                      const stencil_grid* f, double h, const stencil_grid* r,
                      double* norms_dev, void* stream);
+
+/* One Poisson instance of a batch. */
+typedef struct {
+  stencil_grid u;   /* F64 iterate: start on entry, solution on return (halo = Dirichlet values) */
+  stencil_grid f;   /* F64 source, same extents */
+  double h;         /* grid spacing */
+} stencil_problem;
+
+/* Options of stencil_batch_solve (zero-initialise, then set rtol etc.). */
+typedef struct {
+  double rtol;               /* target ||f - A u||_2 / ||f||_2, e.g. 1e-8 */
+  int64_t max_sweeps;        /* inner sweeps per instance before giving up (0 = 10^7) */
+  int32_t inner_dtype;       /* STENCIL_F32 or STENCIL_BF16 storage of the correction */
+  int32_t sweeps_per_cycle;  /* inner sweeps per refinement cycle (0 = 100) */
+  int32_t sweeps_per_pass;   /* sweeps fused per pass of the inner solve (0 = autotuned) */
+  int32_t reserved;
+  double stall_ratio;        /* a cycle with rel > stall_ratio * previous rel escalates
+                                BF16 -> F32 storage (0 = 0.9999); F32 stalls end the
+                                instance with STENCIL_ERR_NOT_CONVERGED */
+} stencil_batch_opts;
+
+/* Per-instance outcome of stencil_batch_solve. */
+typedef struct {
+  int64_t sweeps;            /* inner sweeps done */
+  int32_t cycles;            /* refinement cycles (corrections applied) */
+  int32_t status;            /* STENCIL_OK, STENCIL_ERR_NOT_CONVERGED, STENCIL_ERR_NONFINITE */
+  double rel_residual;       /* final ||f - A u||_2 / ||f||_2, binary64 */
+  int32_t final_dtype;       /* inner storage used by the last cycle */
+  int32_t reserved;
+} stencil_result;
+
+/*
+ * stencil_batch_workspace_size -- device workspace bytes stencil_batch_solve
+ * needs for these n problems (written to *bytes).  Host-only, no GPU work.
+ */
+STENCIL_API int stencil_batch_workspace_size(const stencil_problem* probs, int32_t n,
+                                             size_t* bytes);
+
+/*
+ * stencil_batch_solve -- solve n independent Poisson problems A u = f (the
+ * 7-point operator of stencil_residual, Dirichlet halos) to a relative
+ * residual rtol by mixed-precision iterative refinement: each cycle computes
+ * r = f - A u and its norm in binary64 (bitwise the stencil_residual values),
+ * stops an instance when ||r||/||f|| <= rtol, otherwise rounds r to the inner
+ * storage type (round-to-nearest-even), runs sweeps_per_cycle Jacobi sweeps
+ * of A e = r from e = 0 with binary32 arithmetic, and adds e to u in binary64.
+ * All active instances advance together: every pass of the inner solve is
+ * one persistent launch over the tiles of all of them, and one cycle is one
+ * CUDA graph (residual, check, cast, passes, update) that is replayed until
+ * every instance has finished; the host reads one counter per cycle.
+ *
+ *   probs      host array of n problem descriptors (device grids; u's must
+ *              satisfy the alignment rules of stencil_grid).
+ *   opts       see stencil_batch_opts.
+ *   workspace  device memory of at least stencil_batch_workspace_size bytes,
+ *              256-byte aligned; owned by the caller, clobbered.
+ *   results    host array of n results.
+ * Synchronous: starts after the work already queued on `stream` and returns
+ * when every instance has finished (converged, hit max_sweeps, stalled in
+ * F32, or met a non-finite residual); the work itself runs on the context's
+ * own stream.  Instances' outcomes are in results[i].status; the return
+ * value reports only argument and CUDA errors.  Not to be called during a
+ * stream capture.
+ */
+STENCIL_API int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* probs, int32_t n,
+                                    const stencil_batch_opts* opts, void* workspace,
+                                    size_t workspace_bytes, stencil_result* results,
+                                    void* stream);
 
 /*
  * stencil_residual_noalloc -- the same residual and norms as

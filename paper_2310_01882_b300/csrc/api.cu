@@ -155,6 +155,13 @@ int stencil_ctx_create(int device, stencil_ctx** out) {
   c->scratch = static_cast<unsigned char*>(p);
   rc = check_cuda(cudaMemset(p, 0, c->scratch_bytes), "cudaMemset(ctx scratch)");
   if (rc) { cudaFree(p); delete c; return rc; }
+  void* hw = nullptr;
+  rc = check_cuda(cudaHostAlloc(&hw, 64, cudaHostAllocDefault), "cudaHostAlloc(ctx host word)");
+  if (rc) { cudaFree(p); delete c; return rc; }
+  c->host_word = static_cast<unsigned long long*>(hw);
+  rc = check_cuda(cudaStreamCreateWithFlags(&c->solve_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&c->solve_event, cudaEventDisableTiming), "cudaEventCreate");
+  if (rc) { cudaFreeHost(hw); cudaFree(p); delete c; return rc; }
   *out = c;
   return STENCIL_OK;
 }
@@ -164,6 +171,9 @@ int stencil_ctx_destroy(stencil_ctx* ctx) {
   DeviceGuard dg(ctx->device);
   int rc = check_cuda(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
   cudaFree(ctx->scratch);
+  cudaFreeHost(ctx->host_word);
+  cudaEventDestroy(ctx->solve_event);
+  cudaStreamDestroy(ctx->solve_stream);
   delete ctx;
   return rc;
 }

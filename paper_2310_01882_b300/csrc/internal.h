@@ -12,6 +12,9 @@ struct stencil_ctx {
   int num_sms;
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
+  unsigned long long* host_word;  // pinned host word (batch solve progress)
+  cudaStream_t solve_stream;      // private stream the batch solve captures and replays on
+  cudaEvent_t solve_event;
 };
 
 namespace stencil {

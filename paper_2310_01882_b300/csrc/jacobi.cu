@@ -1,265 +1,14 @@
-// jacobi.cu -- the 7-point Jacobi sweep (Section 4.1's relaxation in the
-// Poisson form, applied out of place as a stencil apply is, Section 2.2),
-// with temporal blocking: T sweeps per pass over HBM.
-//
-// One kernel template, jacobi_tb<Policy, T, R, WY, S>, for every storage /
-// arithmetic policy (policies.cuh).  A persistent CTA owns a tile of the xy
-// plane and marches through a chunk of z planes (2.5D blocking).  A producer
-// warp streams each z plane of u and f, with the halo the T sweeps need,
-// into a ring of S shared-memory stages by TMA tile loads.  Each consumer
-// warp owns 32 x-columns and R rows of the tile and keeps everything else in
-// registers:
-//   * lane l converts its column of each staged u plane once (rows -T..R+T-1);
-//   * x neighbours come from lanes l-1, l+1 by warp shuffle, y neighbours
-//     from the lane's own rows, z neighbours from the registers of the
-//     previous and next planes (three planes per sweep stage, rotated by a
-//     three-way unrolled loop, so no register moves);
-//   * sweep stage t (1..T) updates plane p - t when raw plane p arrives, on
-//     lanes t..31-t and rows -(T-t)..R-1+(T-t), from stage t-1's planes; its
-//     source term is read from the staged f plane, which is held until the
-//     last stage has used it;
-//   * cells that are not interior (the Dirichlet halo) keep their value
-//     through every stage, so the T sweeps equal T separate sweeps exactly.
-// Lanes T..31-T of stage T write the result: a tile is (32-2T) x (R*WY).
-// No CTA barrier and no shared-memory exchange between warps.
+// jacobi.cu -- host side of stencil_jacobi_sweep: per-call conversions
+// (fixed-point scale, pack/unpack), halo copies, and the choice of kernel
+// configuration for each pass (sweep_kernel.cuh holds the kernel).
 #include <stdlib.h>
 
 #include <algorithm>
 
-#include "common.cuh"
 #include "internal.h"
-#include "policies.cuh"
+#include "sweep_kernel.cuh"
 
 namespace stencil {
-
-struct SweepGeom {
-  int64_t nx, ny, nz, sy, sz;
-  int tiles_x, tiles_y, zc;  // zc: planes per z chunk
-  int bxo, byo;              // output tile extents
-  int64_t items;             // tiles_x * tiles_y * z chunks
-};
-
-struct Item {
-  int xo, yo;  // halo index of the tile's first output column / row
-  int zs, ze;  // output planes [zs, ze]
-};
-
-__device__ __forceinline__ Item decode_item(const SweepGeom& g, int64_t item) {
-  Item t;
-  const int64_t txy = static_cast<int64_t>(g.tiles_x) * g.tiles_y;
-  const int zci = static_cast<int>(item / txy);
-  const int64_t r = item - static_cast<int64_t>(zci) * txy;
-  const int ty = static_cast<int>(r / g.tiles_x);
-  const int tx = static_cast<int>(r - static_cast<int64_t>(ty) * g.tiles_x);
-  t.xo = 1 + tx * g.bxo;
-  t.yo = 1 + ty * g.byo;
-  t.zs = zci * g.zc + 1;
-  t.ze = min(t.zs + g.zc - 1, static_cast<int>(g.nz));
-  return t;
-}
-
-template <class Pol, int T_, int R_, int WY_, int S_, int MINB_>
-struct TbCfg {
-  static constexpr int T = T_, R = R_, WY = WY_, S = S_, MINB = MINB_;
-  static constexpr int A = 16 / Pol::kElem;      // TMA x granule in elements
-  static constexpr int BOXW = 32 + A;            // staged columns (any 0 <= off < A)
-  static constexpr int BXO = 32 - 2 * T;         // output columns per tile
-  static constexpr int BYO = R * WY;             // output rows per tile
-  static constexpr int NROW = R + 2 * T;         // rows a warp converts per plane
-  static constexpr int UROWS = BYO + 2 * T;
-  static constexpr int FROWS = BYO + 2 * T - 2;
-  static constexpr int UBYTES = BOXW * UROWS * Pol::kElem;
-  static constexpr int FBYTES = BOXW * FROWS * Pol::kElem;
-  static constexpr int UB = (UBYTES + 127) / 128 * 128;
-  static constexpr int FB = (FBYTES + 127) / 128 * 128;
-  static constexpr int STAGE = UB + FB;
-  static constexpr int RING = S * STAGE;
-  static constexpr int CONSUMERS = 32 * WY;
-  static constexpr int THREADS = CONSUMERS + 32;
-  static constexpr int SMEM = 128 + RING + 128;
-  static_assert(S >= T + 2, "each warp holds T+1 staged planes");
-  static_assert(NROW <= 32, "row mask");
-};
-
-__device__ __forceinline__ int align_down(int x, int a) { return x >= 0 ? x - x % a : -((-x + a - 1) / a) * a; }
-
-// Producer (lane 0 of the last warp): for every item of this CTA, the u
-// boxes of planes zs-T .. ze+T and the f boxes of the same planes.
-template <class Cfg>
-__device__ __forceinline__ void produce(const CUtensorMap* tm_u, const CUtensorMap* tm_f,
-                                        const SweepGeom& g, uint32_t bar_full, uint32_t bar_empty,
-                                        uint32_t ring, uint32_t* status, volatile int* abort_flag) {
-  constexpr int S = Cfg::S, T = Cfg::T;
-  prefetch_tensormap(tm_u);
-  prefetch_tensormap(tm_f);
-  uint32_t it = 0;
-  for (int64_t item = blockIdx.x; item < g.items; item += gridDim.x) {
-    const Item t = decode_item(g, item);
-    const int xa = align_down(t.xo - T, Cfg::A);
-    for (int p = t.zs - T; p <= t.ze + T; ++p, ++it) {
-      const uint32_t s = it % S;
-      if (*abort_flag || !mbar_wait_bounded(bar_empty + 8 * s, ((it / S) & 1u) ^ 1u, status)) {
-        *abort_flag = 1;
-        goto drain;
-      }
-      mbar_arrive_expect_tx(bar_full + 8 * s, Cfg::UBYTES + Cfg::FBYTES);
-      tma_load_3d(ring + s * Cfg::STAGE, tm_u, xa, t.yo - T, p, bar_full + 8 * s);
-      tma_load_3d(ring + s * Cfg::STAGE + Cfg::UB, tm_f, xa, t.yo - T + 1, p, bar_full + 8 * s);
-    }
-  }
-drain:
-  // Do not leave the CTA with copies in flight into its shared memory.
-  for (uint32_t q = (it > S ? it - S : 0); q < it; ++q)
-    if (!mbar_wait_bounded(bar_full + 8 * (q % S), (q / S) & 1u, status)) break;
-}
-
-// Register state of one consumer lane.
-template <class Pol, class Cfg>
-struct LaneState {
-  using C = typename Pol::C;
-  C W[Cfg::T][3][Cfg::NROW];  // stage t's three planes (stage 0 = converted input)
-};
-
-// One z step with the three plane slots rotated by ROT: raw plane p (sequence
-// number seq) has arrived in stage slot `slot`.
-template <class Pol, class Cfg, int ROT>
-__device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename Pol::K& k,
-                                        const unsigned char* ring, int slot, uint32_t seq, int j,
-                                        int p, int row0, int lane, int off, bool xin, uint32_t ymask,
-                                        typename Pol::T* orow0, int64_t sy, int64_t sz, int nz) {
-  using T = typename Pol::T;
-  using C = typename Pol::C;
-  constexpr int TT = Cfg::T, S = Cfg::S;
-  constexpr int OLD = (0 + ROT) % 3, MID = (1 + ROT) % 3, NEW = (2 + ROT) % 3;
-  {
-    const T* U = reinterpret_cast<const T*>(ring + slot * Cfg::STAGE);
-    const bool zin_p = (p >= 1 && p <= nz);
-#pragma unroll
-    for (int q = 0; q < Cfg::NROW; ++q) st.W[0][NEW][q] = Pol::in(U[(row0 + q) * Cfg::BOXW + off + lane], k);
-    // Cells outside the interior (Dirichlet halo, or beyond the grid) may be
-    // stored in a different form (PolResident keeps them binary64); only
-    // warps that touch one take this branch.
-    const uint32_t halo_rows = (xin && zin_p) ? ~ymask : 0xffffffffu;
-    if (__any_sync(0xffffffffu, (halo_rows & ((1u << Cfg::NROW) - 1u)) != 0u)) {
-#pragma unroll
-      for (int q = 0; q < Cfg::NROW; ++q)
-        if ((halo_rows >> q) & 1u) st.W[0][NEW][q] = Pol::in_halo(U[(row0 + q) * Cfg::BOXW + off + lane], k);
-    }
-  }
-#pragma unroll
-  for (int t = 1; t <= TT; ++t) {
-    if (j < 2 * t) break;  // stage t has no complete input yet
-    const int q = p - t;   // plane this stage updates
-    const bool zin = (q >= 1 && q <= nz);
-    const T* F = reinterpret_cast<const T*>(ring + ((seq - t) % S) * Cfg::STAGE + Cfg::UB);
-    constexpr int dummy = 0;
-    (void)dummy;
-    const int nr = Cfg::R + 2 * (TT - t);  // rows this stage updates
-#pragma unroll
-    for (int rr = 0; rr < Cfg::R + 2 * (TT - 1); ++rr) {
-      if (rr >= nr) break;
-      const C c = st.W[t - 1][MID][rr + 1];
-      const C xm = __shfl_up_sync(0xffffffffu, c, 1);
-      const C xp = __shfl_down_sync(0xffffffffu, c, 1);
-      const int w = rr - (TT - t);  // warp row, -T..R+T-1
-      const bool in = xin && zin && ((ymask >> (w + TT)) & 1u);
-      C v = c;
-      if (in) {
-        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + lane];
-        v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2],
-                        st.W[t - 1][OLD][rr + 1], st.W[t - 1][NEW][rr + 1], fv, k);
-      }
-      if (t < TT) {
-        st.W[t][NEW][rr] = v;
-      } else if (in && lane >= TT && lane < 32 - TT) {
-        orow0[static_cast<int64_t>(q) * sz + rr * sy] = Pol::out(v, k);
-      }
-    }
-  }
-}
-
-template <class Pol, class Cfg>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
-    jacobi_tb(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_f,
-              typename Pol::T* __restrict__ out, const SweepGeom g, const SweepArgs args) {
-  constexpr int S = Cfg::S, TT = Cfg::T, WY = Cfg::WY;
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ int abort_flag;
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  const uint32_t bar_full = smem_addr(base);
-  const uint32_t bar_empty = bar_full + 8 * S;
-  unsigned char* ring = base + 128;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, WY);
-    }
-    abort_flag = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  if (warp == WY) {
-    if (lane == 0)
-      produce<Cfg>(&tm_u, &tm_f, g, bar_full, bar_empty, smem_addr(ring), args.status, &abort_flag);
-    return;
-  }
-  const typename Pol::K k = Pol::make(args);
-  const int row0 = warp * Cfg::R;
-  LaneState<Pol, Cfg> st;
-  uint32_t it = 0;
-  for (int64_t item = blockIdx.x; item < g.items; item += gridDim.x) {
-    const Item t = decode_item(g, item);
-    const int xa = align_down(t.xo - TT, Cfg::A);
-    const int off = t.xo - TT - xa;
-    const int64_t x = t.xo - TT + lane;  // halo index of this lane's column
-    const bool xin = (x >= 1 && x <= g.nx);
-    uint32_t ymask = 0;                  // bit w+T: warp row w is interior
-#pragma unroll
-    for (int w = -TT; w < Cfg::R + TT; ++w) {
-      const int64_t y = t.yo + row0 + w;
-      ymask |= (y >= 1 && y <= g.ny) ? (1u << (w + TT)) : 0u;
-    }
-    typename Pol::T* orow0 = out + x + (t.yo + row0) * g.sy;
-    const int steps = (t.ze - t.zs + 1) + 2 * TT;
-    const uint32_t seq0 = it;
-    int j = 0;
-    auto wait = [&](int jj) -> int {
-      const uint32_t seq = seq0 + jj;
-      const uint32_t s = seq % S;
-      if (!mbar_wait_bounded(bar_full + 8 * s, (seq / S) & 1u, args.status)) {
-        abort_flag = 1;
-        return -1;
-      }
-      return static_cast<int>(s);
-    };
-    auto release = [&](uint32_t seq) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar_empty + 8 * (seq % S));
-    };
-    for (;;) {
-#define STENCIL_TB_STEP(ROT)                                                                    \
-  {                                                                                             \
-    const int slot = wait(j);                                                                   \
-    if (slot < 0) return;                                                                       \
-    tb_step<Pol, Cfg, ROT>(st, k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off, xin, \
-                           ymask, orow0, g.sy, g.sz, static_cast<int>(g.nz));                   \
-    if (j >= TT) release(seq0 + j - TT);                                                        \
-    if (++j >= steps) break;                                                                    \
-  }
-      STENCIL_TB_STEP(0)
-      STENCIL_TB_STEP(1)
-      STENCIL_TB_STEP(2)
-#undef STENCIL_TB_STEP
-    }
-    for (int q = steps - TT; q < steps; ++q)
-      if (q >= 0) release(seq0 + q);
-    it = seq0 + steps;
-  }
-}
 
 // max|u| over every cell (halo included) and max|f| over the interior, as
 // the bit patterns of non-negative doubles (their integer order is their
@@ -428,20 +177,22 @@ int grid_for(K kernel, int threads, int smem, int64_t items, int num_sms, int* g
 template <class Pol, class Cfg>
 int run_tb(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, const SweepArgs& a,
            cudaStream_t st) {
-  auto kern = jacobi_tb<Pol, Cfg>;
-  CUtensorMap tu, tf;
-  int rc = make_tensor_map(&tu, in, Cfg::BOXW, Cfg::UROWS);
+  auto kern = jacobi_tb<Pol, Cfg, SrcGrid<Pol>>;
+  SingleParams<Pol> prm;
+  int rc = make_tensor_map(&prm.tm_u, in, Cfg::BOXW, Cfg::UROWS);
   if (rc) return rc;
-  rc = make_tensor_map(&tf, f, Cfg::BOXW, Cfg::FROWS);
+  rc = make_tensor_map(&prm.tm_f, f, Cfg::BOXW, Cfg::FROWS);
   if (rc) return rc;
   int grid = 0, per_sm = 0;
   const int64_t txy = ((in.nx + Cfg::BXO - 1) / Cfg::BXO) * ((in.ny + Cfg::BYO - 1) / Cfg::BYO);
   rc = grid_for(kern, Cfg::THREADS, Cfg::SMEM, txy * in.nz, ctx->num_sms, &grid, &per_sm);
   if (rc) return rc;
   const int zc = pick_zc(txy, in.nz, per_sm * ctx->num_sms, Cfg::T);
-  const SweepGeom g = make_geom<Cfg>(in, zc);
-  grid = static_cast<int>(std::min<int64_t>(g.items, static_cast<int64_t>(per_sm) * ctx->num_sms));
-  kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(tu, tf, static_cast<typename Pol::T*>(out.data), g, a);
+  prm.g = make_geom<Cfg>(in, zc);
+  prm.out = static_cast<typename Pol::T*>(out.data);
+  prm.a = a;
+  grid = static_cast<int>(std::min<int64_t>(prm.g.items, static_cast<int64_t>(per_sm) * ctx->num_sms));
+  kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(prm);
   return check_cuda(cudaGetLastError(), "jacobi_tb launch");
 }
 

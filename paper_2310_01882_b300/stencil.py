@@ -38,6 +38,21 @@ class stencil_grid(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class stencil_problem(ctypes.Structure):
+    _fields_ = [("u", stencil_grid), ("f", stencil_grid), ("h", ctypes.c_double)]
+
+
+class stencil_batch_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_sweeps", ctypes.c_int64), ("inner_dtype", ctypes.c_int32),
+                ("sweeps_per_cycle", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
+
+
+class stencil_result(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("cycles", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("final_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 
 # Every exported symbol of include/stencil.h, with its ctypes signature.
@@ -55,6 +70,11 @@ SIGNATURES = {
     "stencil_advect_uvw": ([_P, _G, _G, _G, _G, _G, _G, _P, _P, ctypes.c_double, ctypes.c_double, _P],
                            ctypes.c_int),
     "stencil_residual_noalloc": ([_G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
+    "stencil_batch_workspace_size": ([ctypes.POINTER(stencil_problem), ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "stencil_batch_solve": ([_P, ctypes.POINTER(stencil_problem), ctypes.c_int32,
+                             ctypes.POINTER(stencil_batch_opts), _P, ctypes.c_size_t,
+                             ctypes.POINTER(stencil_result), _P], ctypes.c_int),
 }
 
 
@@ -200,3 +220,40 @@ def stencil_advect_uvw(ctx, u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, stream=No
     return _check(lib().stencil_advect_uvw(ctx.handle, *[ctypes.byref(g) for g in gs],
                                            ctypes.c_void_p(tzc1.data_ptr()), ctypes.c_void_p(tzc2.data_ptr()),
                                            float(tcx), float(tcy), _stream(stream)))
+
+
+def _problems(us, fs, hs):
+    arr = (stencil_problem * len(us))()
+    for i, (u, f, h) in enumerate(zip(us, fs, hs)):
+        arr[i].u = u.grid()
+        arr[i].f = f.grid()
+        arr[i].h = float(h)
+    return arr
+
+
+def stencil_batch_workspace_size(us, fs, hs):
+    arr = _problems(us, fs, hs)
+    n = ctypes.c_size_t()
+    _check(lib().stencil_batch_workspace_size(arr, len(us), ctypes.byref(n)))
+    return n.value
+
+
+def stencil_batch_solve(ctx, us, fs, hs, rtol, inner_dtype=F32, max_sweeps=0, sweeps_per_cycle=0,
+                        sweeps_per_pass=0, stall_ratio=0.0, workspace=None, stream=None):
+    """Solve the instances (F64 Fields us, fs; spacings hs) in place.
+    workspace: a CUDA tensor of >= stencil_batch_workspace_size bytes (one is
+    allocated if None).  Returns a list of dicts (sweeps, cycles, status,
+    rel_residual, final_dtype)."""
+    import torch
+    arr = _problems(us, fs, hs)
+    need = stencil_batch_workspace_size(us, fs, hs)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=us[0].storage.device)
+    assert workspace.numel() * workspace.element_size() >= need
+    opts = stencil_batch_opts(float(rtol), int(max_sweeps), int(inner_dtype), int(sweeps_per_cycle),
+                              int(sweeps_per_pass), 0, float(stall_ratio))
+    res = (stencil_result * len(us))()
+    _check(lib().stencil_batch_solve(ctx.handle, arr, len(us), ctypes.byref(opts),
+                                     ctypes.c_void_p(workspace.data_ptr()), need, res, _stream(stream)))
+    return [{"sweeps": r.sweeps, "cycles": r.cycles, "status": r.status, "rel_residual": r.rel_residual,
+             "final_dtype": r.final_dtype} for r in res]
