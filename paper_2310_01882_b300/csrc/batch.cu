@@ -374,8 +374,9 @@ int launch_pass(int di, int c, const InstDesc* desc, const InstState* state, con
                 : launch_pass_cfg<PolBF16, BB16b, 1>(p, num_sms, st);
 }
 
-// Geometry and tensor maps of instance i for storage di under configuration c.
-int describe(InstDesc& d, int di, const CfgInfo& ci, int elem) {
+// Geometry and tensor maps of instance i for storage di under configuration
+// c, with z chunks of zc planes.
+int describe(InstDesc& d, int di, const CfgInfo& ci, int elem, int zc) {
   Grid e0, e1, r;
   for (Grid* g : {&e0, &e1, &r}) {
     g->nx = d.nx; g->ny = d.ny; g->nz = d.nz;
@@ -396,7 +397,7 @@ int describe(InstDesc& d, int di, const CfgInfo& ci, int elem) {
   g.byo = ci.BYO;
   g.tiles_x = static_cast<int>((d.nx + ci.BXO - 1) / ci.BXO);
   g.tiles_y = static_cast<int>((d.ny + ci.BYO - 1) / ci.BYO);
-  g.zc = static_cast<int>(std::min<int64_t>(d.nz, 32));
+  g.zc = static_cast<int>(std::min<int64_t>(d.nz, zc));
   g.items = static_cast<int64_t>(g.tiles_x) * g.tiles_y * ((d.nz + g.zc - 1) / g.zc);
   return STENCIL_OK;
 }
@@ -426,9 +427,19 @@ struct Solver {
   int configure(int di, int c) {
     const CfgInfo ci = cfg_info(di, c);
     const int elem = di == 0 ? 4 : 2;
+    // z chunk: the longest (fewest re-read planes) that still gives the
+    // resident CTAs (about 3 per SM) four items each over the whole batch.
+    int zc = 64;
+    for (; zc > 8; zc /= 2) {
+      int64_t items = 0;
+      for (int i = 0; i < n; ++i)
+        items += ((desc[i].nx + ci.BXO - 1) / ci.BXO) * ((desc[i].ny + ci.BYO - 1) / ci.BYO) *
+                 ((desc[i].nz + zc - 1) / zc);
+      if (items >= 12 * static_cast<int64_t>(ctx->num_sms)) break;
+    }
     int64_t acc = 0;
     for (int i = 0; i < n; ++i) {
-      int rc = describe(desc[i], di, ci, elem);
+      int rc = describe(desc[i], di, ci, elem, zc);
       if (rc) return rc;
       sbase[di * (n + 1) + i] = acc;
       acc += desc[i].g[di].items;
