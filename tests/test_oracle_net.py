@@ -1,0 +1,92 @@
+"""Pins for the warm-start network oracle (oracle/net.py): the convolution
+against a delta kernel, scipy's correlate and a brute-force voxel; adjoint
+identities of every linear step; and the whole network's analytic gradient
+against central finite differences."""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+from oracle import net
+
+
+def test_delta_kernel_is_identity():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((5, 6, 7, 3))
+    W = np.zeros((3, 3, 3, 3, 3))
+    W[1, 1, 1] = np.eye(3)
+    b = np.array([0.5, -1.0, 2.0])
+    assert np.array_equal(net.conv3(x, W, b), x + b)
+
+
+def test_single_channel_matches_scipy_correlate():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((6, 5, 7))
+    w = rng.standard_normal((3, 3, 3))
+    ref = ndimage.correlate(x, w, mode="constant", cval=0.0)
+    got = net.conv3(x[..., None], w[..., None, None], np.zeros(1))[..., 0]
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_brute_force_voxel():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((4, 4, 4, 2))
+    W = rng.standard_normal((3, 3, 3, 2, 3))
+    b = rng.standard_normal(3)
+    out = net.conv3(x, W, b)
+    for (z, y, xx) in [(0, 0, 0), (1, 2, 3), (3, 3, 3), (2, 0, 1)]:
+        acc = b.copy()
+        for dz in range(3):
+            for dy in range(3):
+                for dx in range(3):
+                    zz, yy, xi = z + dz - 1, y + dy - 1, xx + dx - 1
+                    if 0 <= zz < 4 and 0 <= yy < 4 and 0 <= xi < 4:
+                        for ci in range(2):
+                            for co in range(3):
+                                acc[co] += x[zz, yy, xi, ci] * W[dz, dy, dx, ci, co]
+        np.testing.assert_allclose(out[z, y, xx], acc, rtol=1e-12)
+
+
+def test_adjoint_identities():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((4, 6, 8, 3))
+    y = rng.standard_normal((2, 3, 4, 3))
+    assert abs(np.sum(net.pool2(x) * y) - np.sum(x * net.pool2_bwd(y))) <= 1e-12
+    z = rng.standard_normal((8, 12, 16, 3))
+    assert abs(np.sum(net.up2(x) * z) - np.sum(x * net.up2_bwd(z))) <= 1e-11
+    W = rng.standard_normal((3, 3, 3, 3, 5))
+    g = rng.standard_normal((4, 6, 8, 5))
+    out = net.conv3(x, W, np.zeros(5))
+    dx, dW, db = net.conv3_bwd(x, W, g)
+    ip = np.sum(out * g)
+    assert abs(ip - np.sum(x * dx)) <= 1e-10 * abs(ip)
+    assert abs(ip - np.sum(W * dW)) <= 1e-10 * abs(ip)
+    np.testing.assert_allclose(db, g.sum(axis=(0, 1, 2)))
+
+
+@pytest.mark.parametrize("channels", [[4, 6], [3, 4, 5]])
+def test_network_gradient_finite_differences(channels):
+    rng = np.random.default_rng(4)
+    n = 8
+    x = rng.standard_normal((n, n, n, 1))
+    t = rng.standard_normal((n, n, n, 1)) * 0.1
+    p = net.init_params(channels, seed=5)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.1
+    loss, grads, _ = net.loss_and_grads(p, x, t, channels)
+    eps = 1e-6
+    checked = 0
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(3, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp = net.loss_and_grads(p, x, t, channels)[0]
+            flat[idx] = old - eps
+            lm = net.loss_and_grads(p, x, t, channels)[0]
+            flat[idx] = old
+            fd = (lp - lm) / (2 * eps)
+            an = grads[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-4), (name, idx, fd, an)
+            checked += 1
+    assert checked >= 20
