@@ -244,6 +244,59 @@ STENCIL_API int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* pro
                                     void* stream);
 
 /*
+ * Learned warm start (wsnet_*).  A small 3D U-Net maps the source f of a
+ * Poisson problem on an n^3 grid to a starting iterate u0 for the Jacobi
+ * solve; the solve (plain Jacobi or stencil_batch_solve) then removes the
+ * remaining error, and its residual judges the result.  The paper has no
+ * learned component: this is the warm-start pattern layered on the solver.
+ * Architecture (levels L <= 4 with per-level channels in {16, 32, 64}): two
+ * 3x3x3 convolutions with ReLU per level, 2x2x2 average pooling between
+ * encoder levels, nearest 2x upsampling between decoder levels whose first
+ * convolution adds the encoder feature of the same level before its ReLU,
+ * and a 1x1x1 output layer.  Input f / rms(f) over the interior; output
+ * u0 = y * rms(f) / (3 pi^2) on the interior (the halo of u is untouched).
+ * Activations and gradients are bfloat16, products accumulate in binary32 on
+ * the tensor cores; parameters are binary32 (Adam).  Parameter vector layout
+ * (wsnet_get_params): per 3x3x3 layer, in forward order (encoder levels
+ * 0..L-1 with layers a, b; decoder levels L-2..0 with layers a, b), weights
+ * W[co][tap*cin + ci] (tap = 9 dz + 3 dy + dx over offsets -1..1) then
+ * biases b[co]; then the output layer's C0 weights and its bias.
+ * A net owns its device memory (parameters and the activations of one n^3
+ * sample); one net per host thread.
+ */
+typedef struct wsnet wsnet;
+
+/* Create a net for n^3 grids (n a multiple of 2^(levels-1)); He-normal
+ * weights from `seed` (deterministic), zero biases.  Allocates. */
+STENCIL_API int wsnet_create(int device, int32_t levels, const int32_t* channels,
+                             int32_t n, uint64_t seed, wsnet** out);
+/* Free the net and its device memory (synchronises the device). */
+STENCIL_API int wsnet_destroy(wsnet* net);
+/* Number of binary32 parameters. */
+STENCIL_API int wsnet_num_params(const wsnet* net, int64_t* count);
+/* Copy the parameters to / from a host array of wsnet_num_params floats. */
+STENCIL_API int wsnet_get_params(wsnet* net, float* host, int64_t count);
+STENCIL_API int wsnet_set_params(wsnet* net, const float* host, int64_t count);
+/* u0 on the interior of u (F64 n^3 grid) from the source f (F64 n^3 grid),
+ * enqueued on `stream`. */
+STENCIL_API int wsnet_infer(wsnet* net, const stencil_grid* f,
+                            const stencil_grid* u, void* stream);
+/* One Adam step (lr; betas 0.9, 0.999; eps 1e-8) on the mean squared error
+ * between the normalised output and the normalised targets u[s] over
+ * `count` samples (host arrays of F64 n^3 grids f[s], u[s]); *loss receives
+ * the mean loss.  Synchronises `stream`. */
+STENCIL_API int wsnet_train_step(wsnet* net, const stencil_grid* f,
+                                 const stencil_grid* u, int32_t count,
+                                 float lr, double* loss, void* stream);
+/* One forward and backward pass on a given normalised input x and target t
+ * (DEVICE binary32 arrays of n^3 values, z slowest, x fastest); y (device,
+ * nullable) receives the output, grads (host, nullable) the gradients, in
+ * the parameter layout.  For checking the kernels against a reference. */
+STENCIL_API int wsnet_loss_grad(wsnet* net, const float* x, const float* t,
+                                float* y, float* grads, double* loss,
+                                void* stream);
+
+/*
  * stencil_residual_noalloc -- the same residual and norms as
  * stencil_residual, for callers that cannot allocate device memory: code
  * running where allocation is forbidden or unavailable (a host application

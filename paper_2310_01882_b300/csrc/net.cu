@@ -1,0 +1,989 @@
+// net.cu -- the learned warm start: a small 3D U-Net that maps the source f of
+// a Poisson problem to a starting iterate u0, trained on (f, converged u)
+// pairs, with its own BF16 tensor-core kernels (FP32 accumulation) for
+// inference and training.  The paper has no learned component; this is the
+// warm-start pattern layered on its Jacobi solver.
+//
+// Architecture (per-level channels C[0..L-1], L <= 4): per level two 3x3x3
+// convolutions with ReLU; 2x2x2 average pooling between encoder levels;
+// nearest 2x upsampling between decoder levels, whose first convolution adds
+// the encoder feature of the same level before its ReLU; a 1x1x1 output layer.
+// Activations and gradients are bfloat16, channels-last [z][y][x][c]; weights
+// are kept in FP32 (Adam) and mirrored to bfloat16 in two layouts: W[co][k]
+// with k = tap*Cin + ci (forward) and Wt[ci][k'] with k' = (26-tap)*Cout + co
+// (the input gradient is the forward convolution with flipped, transposed
+// weights).  The convolutions are implicit GEMMs on mma.sync m16n8k16 BF16.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace stencil {
+namespace net {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kMaxLevels = 4;
+
+__host__ __device__ constexpr int kpad(int cin) { return (27 * cin + 15) / 16 * 16; }
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return static_cast<uint32_t>(__bfloat16_as_ushort(lo)) |
+         (static_cast<uint32_t>(__bfloat16_as_ushort(hi)) << 16);
+}
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct Vox {
+  int z, y, x;
+  bool ok;
+};
+
+__device__ __forceinline__ Vox vox_of(int64_t v, int D, int H, int W) {
+  Vox r;
+  r.ok = v < static_cast<int64_t>(D) * H * W;
+  const int64_t hw = static_cast<int64_t>(H) * W;
+  r.z = static_cast<int>(v / hw);
+  const int64_t rem = v - static_cast<int64_t>(r.z) * hw;
+  r.y = static_cast<int>(rem / W);
+  r.x = static_cast<int>(rem - static_cast<int64_t>(r.y) * W);
+  return r;
+}
+
+// Index of the neighbour of p at tap (dz,dy,dx) = (tap/9-1, tap/3%3-1, tap%3-1),
+// or -1 outside the grid (zero padding).
+__device__ __forceinline__ int64_t nbr(const Vox& p, int tap, int D, int H, int W) {
+  const int z = p.z + tap / 9 - 1, y = p.y + (tap / 3) % 3 - 1, x = p.x + tap % 3 - 1;
+  if (!p.ok || tap >= 27 || z < 0 || z >= D || y < 0 || y >= H || x < 0 || x >= W) return -1;
+  return (static_cast<int64_t>(z) * H + y) * W + x;
+}
+
+// Two consecutive K entries (k, k+1) of the implicit-GEMM A row of voxel p.
+template <int CIN>
+__device__ __forceinline__ uint32_t a_pair(const bf16* __restrict__ in, const Vox& p, int k, int D, int H,
+                                           int W) {
+  if (CIN >= 2) {
+    const int tap = k / CIN, ci = k - (k / CIN) * CIN;
+    const int64_t q = nbr(p, tap, D, H, W);
+    return q < 0 ? 0u : *reinterpret_cast<const uint32_t*>(in + q * CIN + ci);
+  } else {
+    const int64_t q0 = nbr(p, k, D, H, W), q1 = nbr(p, k + 1, D, H, W);
+    const bf16 z = __float2bfloat16_rn(0.0f);
+    return pack2(q0 < 0 ? z : in[q0], q1 < 0 ? z : in[q1]);
+  }
+}
+
+// out[v, co] = epilogue( bias[co] + sum_k A[v, k] W[co, k] ), 64 voxels per
+// CTA, 16 per warp, all COUT channels per warp.  Epilogue: + skip (bf16),
+// ReLU, store bf16 (out) and/or FP32 (out32).
+template <int CIN, int COUT, bool RELU, bool SKIP>
+__global__ void __launch_bounds__(128)
+    conv3_fwd_kernel(const bf16* __restrict__ in, const bf16* __restrict__ Wk, const float* __restrict__ bias,
+                     const bf16* __restrict__ skip, bf16* __restrict__ out, float* __restrict__ out32, int D, int H,
+                     int W) {
+  constexpr int KP = kpad(CIN);
+  constexpr int NT = COUT / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t vb = static_cast<int64_t>(blockIdx.x) * 64 + warp * 16;
+  const Vox p0 = vox_of(vb + g, D, H, W), p1 = vox_of(vb + g + 8, D, H, W);
+  float acc[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+  for (int k0 = 0; k0 < KP; k0 += 16) {
+    uint32_t a[4];
+    a[0] = a_pair<CIN>(in, p0, k0 + 2 * t, D, H, W);
+    a[1] = a_pair<CIN>(in, p1, k0 + 2 * t, D, H, W);
+    a[2] = a_pair<CIN>(in, p0, k0 + 2 * t + 8, D, H, W);
+    a[3] = a_pair<CIN>(in, p1, k0 + 2 * t + 8, D, H, W);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const bf16* wr = Wk + static_cast<int64_t>(j * 8 + g) * KP + k0 + 2 * t;
+      mma16816(acc[j], a, *reinterpret_cast<const uint32_t*>(wr), *reinterpret_cast<const uint32_t*>(wr + 8));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int co = j * 8 + 2 * t;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t v = vb + g + 8 * h;
+      if (!(h ? p1.ok : p0.ok)) continue;
+      float v0 = acc[j][2 * h] + bias[co], v1 = acc[j][2 * h + 1] + bias[co + 1];
+      if (SKIP) {
+        v0 += __bfloat162float(skip[v * COUT + co]);
+        v1 += __bfloat162float(skip[v * COUT + co + 1]);
+      }
+      if (RELU) {
+        v0 = fmaxf(v0, 0.0f);
+        v1 = fmaxf(v1, 0.0f);
+      }
+      if (out) *reinterpret_cast<uint32_t*>(out + v * COUT + co) = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+      if (out32) {
+        out32[v * COUT + co] = v0;
+        out32[v * COUT + co + 1] = v1;
+      }
+    }
+  }
+}
+
+// Weight-gradient partials of one tap over one chunk of voxels:
+//   P[chunk][co][tap*CIN + ci] = sum_{v in chunk} g[v, co] * in[v + tap, ci].
+// GEMM with M = COUT, N = CIN, K = voxels; four warps split the chunk and
+// their tiles are summed in warp order.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+    conv3_wgrad_kernel(const bf16* __restrict__ in, const bf16* __restrict__ gr, float* __restrict__ part,
+                       int D, int H, int W, int chunk) {
+  constexpr int KP = kpad(CIN);
+  constexpr int MT = COUT / 16;
+  constexpr int NT = (CIN + 7) / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int tap = blockIdx.y;
+  const int64_t V = static_cast<int64_t>(D) * H * W;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t c1 = min(c0 + chunk, V);
+  const int per_warp = (chunk + 3) / 4;
+  const int64_t w0 = c0 + static_cast<int64_t>(warp) * per_warp;
+  const int64_t w1 = min(w0 + per_warp, c1);
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
+  const bf16 zero = __float2bfloat16_rn(0.0f);
+  for (int64_t vb = w0; vb < w1; vb += 16) {
+    int64_t vv[4];
+    vv[0] = vb + 2 * t; vv[1] = vv[0] + 1; vv[2] = vv[0] + 8; vv[3] = vv[0] + 9;
+    int64_t q[4];
+    bool ok[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ok[e] = vv[e] < w1;
+      const Vox p = vox_of(ok[e] ? vv[e] : 0, D, H, W);
+      q[e] = ok[e] ? nbr(p, tap, D, H, W) : -1;
+    }
+    uint32_t a[MT][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      const int co = i * 16 + g;
+      bf16 x[8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        x[e] = ok[e] ? gr[vv[e] * COUT + co] : zero;
+        x[4 + e] = ok[e] ? gr[vv[e] * COUT + co + 8] : zero;
+      }
+      a[i][0] = pack2(x[0], x[1]);   // (co, v0..v1)
+      a[i][1] = pack2(x[4], x[5]);   // (co+8, v0..v1)
+      a[i][2] = pack2(x[2], x[3]);   // (co, v0+8..)
+      a[i][3] = pack2(x[6], x[7]);   // (co+8, v0+8..)
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int ci = j * 8 + g;
+      bf16 y[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) y[e] = (q[e] >= 0 && ci < CIN) ? in[q[e] * CIN + ci] : zero;
+      const uint32_t b0 = pack2(y[0], y[1]), b1 = pack2(y[2], y[3]);
+#pragma unroll
+      for (int i = 0; i < MT; ++i) mma16816(acc[i][j], a[i], b0, b1);
+    }
+  }
+  // sum the four warps' tiles in warp order through shared memory
+  __shared__ float red[COUT * NT * 8];
+  for (int w = 0; w < 4; ++w) {
+    if (warp == w) {
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int co = i * 16 + g + ((e & 2) ? 8 : 0);
+            const int ci = j * 8 + 2 * t + (e & 1);
+            const int idx = co * (NT * 8) + ci;
+            red[idx] = (w == 0 ? 0.0f : red[idx]) + acc[i][j][e];
+          }
+    }
+    __syncthreads();
+  }
+  float* P = part + static_cast<int64_t>(blockIdx.x) * COUT * KP;
+  for (int idx = threadIdx.x; idx < COUT * NT * 8; idx += 128) {
+    const int co = idx / (NT * 8), ci = idx - co * (NT * 8);
+    if (ci >= CIN) continue;
+    P[co * KP + tap * CIN + ci] = red[idx];
+  }
+}
+
+// dW[co][k] += sum over chunks (in chunk order) of P[chunk][co][k], for
+// k < kvalid = 27*CIN (P rows are kp long, dW rows kvalid long).
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, float* __restrict__ dW, int cout, int kp,
+                                    int kvalid, int chunks) {
+  const int64_t n = static_cast<int64_t>(cout) * kp;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t co = i / kp, k = i - co * kp;
+    if (k >= kvalid) continue;
+    float s = 0.0f;
+    for (int c = 0; c < chunks; ++c) s += part[static_cast<int64_t>(c) * n + i];
+    dW[co * kvalid + k] += s;
+  }
+}
+
+// Per-channel sums over voxels (bias gradients): part[b][c] for blocks of
+// `chunk` voxels, then db[c] += sum over blocks in order.
+template <class T>
+__global__ void chan_sum_kernel(const T* __restrict__ x, float* __restrict__ part, int64_t V, int C, int chunk) {
+  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t v1 = min(v0 + chunk, V);
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float s = 0.0f;
+    for (int64_t v = v0; v < v1; ++v) s += static_cast<float>(x[v * C + c]);
+    part[static_cast<int64_t>(blockIdx.x) * C + c] = s;
+  }
+}
+
+__global__ void chan_sum_reduce_kernel(const float* __restrict__ part, float* __restrict__ db, int C, int blocks) {
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float s = 0.0f;
+    for (int b = 0; b < blocks; ++b) s += part[static_cast<int64_t>(b) * C + c];
+    db[c] += s;
+  }
+}
+
+__global__ void pool2_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int D, int H, int W, int C) {
+  const int d = D / 2, h = H / 2, w = W / 2;
+  const int64_t n = static_cast<int64_t>(d) * h * w * C;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(i % C);
+    const int64_t v = i / C;
+    const int x = static_cast<int>(v % w), y = static_cast<int>((v / w) % h), z = static_cast<int>(v / (w * h));
+    float s = 0.0f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          s += __bfloat162float(in[((static_cast<int64_t>(2 * z + dz) * H + 2 * y + dy) * W + 2 * x + dx) * C + c]);
+    out[i] = __float2bfloat16_rn(s * 0.125f);
+  }
+}
+
+// Adjoint of pool2: every fine voxel gets g/8 of its block.
+__global__ void pool2_bwd_kernel(const bf16* __restrict__ g, bf16* __restrict__ out, int D, int H, int W, int C) {
+  const int64_t n = static_cast<int64_t>(D) * H * W * C;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(i % C);
+    const int64_t v = i / C;
+    const int x = static_cast<int>(v % W), y = static_cast<int>((v / W) % H), z = static_cast<int>(v / (W * H));
+    const int64_t q = ((static_cast<int64_t>(z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c;
+    out[i] = __float2bfloat16_rn(__bfloat162float(g[q]) * 0.125f);
+  }
+}
+
+// Nearest 2x upsampling: fine grid (D, H, W) from the coarse one.
+__global__ void up2_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int D, int H, int W, int C) {
+  const int64_t n = static_cast<int64_t>(D) * H * W * C;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(i % C);
+    const int64_t v = i / C;
+    const int x = static_cast<int>(v % W), y = static_cast<int>((v / W) % H), z = static_cast<int>(v / (W * H));
+    out[i] = in[((static_cast<int64_t>(z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+  }
+}
+
+// Adjoint of up2: coarse voxel gets the sum of its 8 fine gradients.
+__global__ void up2_bwd_kernel(const bf16* __restrict__ g, bf16* __restrict__ out, int d, int h, int w, int C) {
+  const int H = 2 * h, W = 2 * w;
+  const int64_t n = static_cast<int64_t>(d) * h * w * C;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(i % C);
+    const int64_t v = i / C;
+    const int x = static_cast<int>(v % w), y = static_cast<int>((v / w) % h), z = static_cast<int>(v / (w * h));
+    float s = 0.0f;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+          s += __bfloat162float(g[((static_cast<int64_t>(2 * z + dz) * H + 2 * y + dy) * W + 2 * x + dx) * C + c]);
+    out[i] = __float2bfloat16_rn(s);
+  }
+}
+
+// g_out = (g + addend) * (act > 0), bf16 (addend may be null).
+__global__ void relu_bwd_kernel(const bf16* __restrict__ g, const bf16* __restrict__ addend,
+                                const bf16* __restrict__ act, bf16* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    float v = __bfloat162float(g[i]);
+    if (addend) v += __bfloat162float(addend[i]);
+    out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? v : 0.0f);
+  }
+}
+
+// Output layer: y[v] = b + sum_c h[v][c] w[c]  (FP32).
+__global__ void out_fwd_kernel(const bf16* __restrict__ h, const float* __restrict__ w, const float* __restrict__ b,
+                               float* __restrict__ y, int64_t V, int C) {
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x) {
+    float s = b[0];
+    for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(h[v * C + c]), w[c], s);
+    y[v] = s;
+  }
+}
+
+// gy = 2 (y - t) / V, the loss partials per block, and g_h = gy * w (bf16).
+__global__ void mse_bwd_kernel(const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ w,
+                               float* __restrict__ gy, bf16* __restrict__ gh, float* __restrict__ loss_part,
+                               int64_t V, int C, int chunk) {
+  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t v1 = min(v0 + chunk, V);
+  float s = 0.0f;
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const float d = y[v] - t[v];
+    s = fmaf(d, d, s);
+    const float gv = 2.0f * d / static_cast<float>(V);
+    gy[v] = gv;
+    for (int c = 0; c < C; ++c) gh[v * C + c] = __float2bfloat16_rn(gv * w[c]);
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// Output-layer weight gradients: part[b][c] = sum_{v in block} h[v][c] gy[v],
+// part[b][C] = sum gy.
+__global__ void out_wgrad_kernel(const bf16* __restrict__ h, const float* __restrict__ gy, float* __restrict__ part,
+                                 int64_t V, int C, int chunk) {
+  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * chunk;
+  const int64_t v1 = min(v0 + chunk, V);
+  for (int c = threadIdx.x; c <= C; c += blockDim.x) {
+    float s = 0.0f;
+    for (int64_t v = v0; v < v1; ++v) s += c < C ? __bfloat162float(h[v * C + c]) * gy[v] : gy[v];
+    part[static_cast<int64_t>(blockIdx.x) * (C + 1) + c] = s;
+  }
+}
+
+// Adam on the FP32 master parameters, then the bf16 mirrors in both layouts.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2, float gscale) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float gr = grad[i] * gscale;
+    const float mi = b1 * m[i] + (1.0f - b1) * gr;
+    const float vi = b2 * v[i] + (1.0f - b2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// bf16 mirrors of a 3x3x3 layer: Wf[co][k] (k = tap*cin + ci, zero past 27 cin)
+// and Wt[ci][k'] (k' = (26-tap)*cout + co) from the FP32 W[co][tap*cin+ci].
+__global__ void mirror_kernel(const float* __restrict__ w, bf16* __restrict__ wf, bf16* __restrict__ wt, int cin,
+                              int cout) {
+  const int kpf = kpad(cin), kpt = kpad(cout);
+  const int64_t nf = static_cast<int64_t>(cout) * kpf;
+  const int64_t nt = static_cast<int64_t>(cin) * kpt;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < nf + nt; i += int64_t(gridDim.x) * blockDim.x) {
+    if (i < nf) {
+      const int co = static_cast<int>(i / kpf), k = static_cast<int>(i % kpf);
+      wf[i] = __float2bfloat16_rn(k < 27 * cin ? w[static_cast<int64_t>(co) * 27 * cin + k] : 0.0f);
+    } else if (wt) {
+      const int64_t j = i - nf;
+      const int ci = static_cast<int>(j / kpt), k = static_cast<int>(j % kpt);
+      float val = 0.0f;
+      if (k < 27 * cout) {
+        const int tap = 26 - k / cout, co = k % cout;
+        val = w[static_cast<int64_t>(co) * 27 * cin + tap * cin + ci];
+      }
+      wt[j] = __float2bfloat16_rn(val);
+    }
+  }
+}
+
+// x0 = bf16(f / s) on the interior of an F64 halo grid (channels-last, C=1),
+// and u[interior] = y * scale (halo untouched).
+__global__ void input_kernel(const double* __restrict__ f, int64_t sy, int64_t sz, int n,
+                             const double* __restrict__ rms, bf16* __restrict__ x) {
+  const int64_t V = static_cast<int64_t>(n) * n * n;
+  const double inv = rms[0] > 0.0 ? 1.0 / rms[0] : 0.0;
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(v % n), j = static_cast<int>((v / n) % n), k = static_cast<int>(v / (int64_t(n) * n));
+    x[v] = __float2bfloat16_rn(static_cast<float>(f[(i + 1) + (j + 1) * sy + (k + 1) * sz] * inv));
+  }
+}
+
+__global__ void output_kernel(const float* __restrict__ y, double* __restrict__ u, int64_t sy, int64_t sz, int n,
+                              const double* __restrict__ rms, double s0) {
+  const int64_t V = static_cast<int64_t>(n) * n * n;
+  const double scale = rms[0] * s0;
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(v % n), j = static_cast<int>((v / n) % n), k = static_cast<int>(v / (int64_t(n) * n));
+    u[(i + 1) + (j + 1) * sy + (k + 1) * sz] = static_cast<double>(y[v]) * scale;
+  }
+}
+
+// Normalised target t = u / scale (FP32, channels-last).
+__global__ void target_kernel(const double* __restrict__ u, int64_t sy, int64_t sz, int n,
+                              const double* __restrict__ rms, double s0, float* __restrict__ t) {
+  const int64_t V = static_cast<int64_t>(n) * n * n;
+  const double inv = rms[0] > 0.0 ? 1.0 / (rms[0] * s0) : 0.0;
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(v % n), j = static_cast<int>((v / n) % n), k = static_cast<int>(v / (int64_t(n) * n));
+    t[v] = static_cast<float>(u[(i + 1) + (j + 1) * sy + (k + 1) * sz] * inv);
+  }
+}
+
+// Sum of squares of the interior of an F64 grid: per-block partials.
+__global__ void sumsq_kernel(const double* __restrict__ f, int64_t sy, int64_t sz, int n, double* __restrict__ part) {
+  const int64_t V = static_cast<int64_t>(n) * n * n;
+  double s = 0.0;
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(v % n), j = static_cast<int>((v / n) % n), k = static_cast<int>(v / (int64_t(n) * n));
+    const double a = f[(i + 1) + (j + 1) * sy + (k + 1) * sz];
+    s = fma(a, a, s);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// rms = sqrt(sum of part[0..blocks) / V), in block order (one thread).
+__global__ void rms_kernel(const double* __restrict__ part, int blocks, double V, double* __restrict__ rms) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < blocks; ++b) s += part[b];
+  rms[0] = sqrt(s / V);
+}
+
+}  // namespace net
+}  // namespace stencil
+
+// ---------------------------------------------------------------------------
+// Host side: the network object, its passes and the C ABI.
+// ---------------------------------------------------------------------------
+namespace stencil {
+namespace net {
+namespace {
+
+// Launch helpers with the (cin, cout) pairs the U-Nets here use.
+#define STENCIL_NET_PAIRS(X) \
+  X(1, 16) X(1, 32) X(16, 16) X(16, 32) X(16, 64) X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64)
+
+int blocks_for(int64_t n, int per = 256) {
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 8192)));
+}
+
+int launch_conv(int cin, int cout, bool relu, bool skip, const bf16* in, const bf16* w, const float* bias,
+                const bf16* sk, bf16* out, int D, int H, int W, cudaStream_t st) {
+  const int64_t V = static_cast<int64_t>(D) * H * W;
+  const int grid = static_cast<int>((V + 63) / 64);
+#define X(CI, CO)                                                                                           \
+  if (cin == CI && cout == CO) {                                                                           \
+    if (relu && skip)                                                                                      \
+      conv3_fwd_kernel<CI, CO, true, true><<<grid, 128, 0, st>>>(in, w, bias, sk, out, nullptr, D, H, W);  \
+    else if (relu)                                                                                         \
+      conv3_fwd_kernel<CI, CO, true, false><<<grid, 128, 0, st>>>(in, w, bias, sk, out, nullptr, D, H, W); \
+    else                                                                                                   \
+      conv3_fwd_kernel<CI, CO, false, false><<<grid, 128, 0, st>>>(in, w, bias, sk, out, nullptr, D, H, W); \
+    return check_cuda(cudaGetLastError(), "conv3 fwd");                                                    \
+  }
+  STENCIL_NET_PAIRS(X)
+#undef X
+  return set_error(STENCIL_ERR_ARG, "wsnet: no convolution kernel for %d -> %d channels", cin, cout);
+}
+
+constexpr int kWgradChunk = 8192;
+
+int launch_wgrad(int cin, int cout, const bf16* in, const bf16* g, float* part, float* dW, int D, int H, int W,
+                 cudaStream_t st) {
+  const int64_t V = static_cast<int64_t>(D) * H * W;
+  const int chunks = static_cast<int>((V + kWgradChunk - 1) / kWgradChunk);
+  const dim3 grid(chunks, 27);
+#define X(CI, CO)                                                                                   \
+  if (cin == CI && cout == CO) {                                                                   \
+    conv3_wgrad_kernel<CI, CO><<<grid, 128, 0, st>>>(in, g, part, D, H, W, kWgradChunk);           \
+    int rc = check_cuda(cudaGetLastError(), "conv3 wgrad");                                         \
+    if (rc) return rc;                                                                              \
+    wgrad_reduce_kernel<<<blocks_for(int64_t(CO) * kpad(CI)), 256, 0, st>>>(part, dW, CO, kpad(CI), \
+                                                                             27 * CI, chunks);      \
+    return check_cuda(cudaGetLastError(), "wgrad reduce");                                          \
+  }
+  STENCIL_NET_PAIRS(X)
+#undef X
+  return set_error(STENCIL_ERR_ARG, "wsnet: no weight-gradient kernel for %d -> %d channels", cin, cout);
+}
+
+uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Standard normal deviates by the Box-Muller transform of splitmix64 uniforms.
+double normal(uint64_t& s) {
+  const double u1 = (static_cast<double>(splitmix64(s) >> 11) + 0.5) / 9007199254740992.0;
+  const double u2 = (static_cast<double>(splitmix64(s) >> 11) + 0.5) / 9007199254740992.0;
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+}
+
+}  // namespace
+
+struct Layer {
+  int cin, cout, level;
+  int64_t woff, boff;  // offsets into the FP32 parameter vector
+  bf16* wf;            // [cout][kpad(cin)]
+  bf16* wt;            // [cin][kpad(cout)]
+};
+
+}  // namespace net
+}  // namespace stencil
+
+// Output scale: u0 = net(f / rms f) * rms(f) * kOutScale.  1/(3 pi^2) is the
+// solution of the lowest sine mode per unit of its source, so the network's
+// output is of order one.
+static const double kOutScale = 1.0 / (3.0 * 9.869604401089358);
+
+struct wsnet {
+  int device;
+  int L;
+  int C[stencil::net::kMaxLevels];
+  int n;  // interior extent of the grids it maps
+  std::vector<stencil::net::Layer> layers;
+  int64_t nparams;
+  int64_t out_w, out_b;
+  float *p, *g, *m, *v;  // device FP32: parameters, gradients, Adam moments
+  stencil::net::bf16* wbuf;
+  int64_t wbuf_elems;
+  float* zero_bias;
+  int64_t V[stencil::net::kMaxLevels];
+  int dim[stencil::net::kMaxLevels];
+  stencil::net::bf16 *x0, *a[4], *b[4], *pl[4], *u[4], *da[4], *db[4], *gA[4], *gB[4], *gs[4];
+  float *y, *t, *gy, *part, *misc;
+  double *rms_part, *rms;
+  int64_t part_elems;
+  int step;
+  std::vector<void*> allocs;
+};
+
+namespace stencil {
+namespace net {
+namespace {
+
+int dalloc(wsnet* w, void** p, size_t bytes) {
+  int rc = check_cuda(cudaMalloc(p, std::max<size_t>(bytes, 256)), "wsnet cudaMalloc");
+  if (!rc) {
+    w->allocs.push_back(*p);
+    rc = check_cuda(cudaMemset(*p, 0, std::max<size_t>(bytes, 256)), "wsnet cudaMemset");
+  }
+  return rc;
+}
+
+template <class T>
+int dalloc_t(wsnet* w, T** p, size_t count) {
+  void* q = nullptr;
+  int rc = dalloc(w, &q, count * sizeof(T));
+  *p = static_cast<T*>(q);
+  return rc;
+}
+
+int mirror(wsnet* w, cudaStream_t st) {
+  for (const Layer& ly : w->layers) {
+    const int64_t n = static_cast<int64_t>(ly.cout) * kpad(ly.cin) + static_cast<int64_t>(ly.cin) * kpad(ly.cout);
+    mirror_kernel<<<blocks_for(n), 256, 0, st>>>(w->p + ly.woff, ly.wf, ly.wt, ly.cin, ly.cout);
+  }
+  return check_cuda(cudaGetLastError(), "wsnet mirror");
+}
+
+int forward(wsnet* w, cudaStream_t st) {
+  const int L = w->L;
+  int li = 0;
+  for (int l = 0; l < L; ++l) {
+    const int d = w->dim[l];
+    const bf16* in = w->x0;
+    if (l > 0) {
+      pool2_kernel<<<blocks_for(w->V[l] * w->C[l - 1]), 256, 0, st>>>(w->b[l - 1], w->pl[l], 2 * d, 2 * d, 2 * d,
+                                                                      w->C[l - 1]);
+      in = w->pl[l];
+    }
+    const Layer& la = w->layers[li++];
+    int rc = launch_conv(la.cin, la.cout, true, false, in, la.wf, w->p + la.boff, nullptr, w->a[l], d, d, d, st);
+    if (rc) return rc;
+    const Layer& lb = w->layers[li++];
+    rc = launch_conv(lb.cin, lb.cout, true, false, w->a[l], lb.wf, w->p + lb.boff, nullptr, w->b[l], d, d, d, st);
+    if (rc) return rc;
+  }
+  const bf16* h = w->b[L - 1];
+  for (int l = L - 2; l >= 0; --l) {
+    const int d = w->dim[l];
+    up2_kernel<<<blocks_for(w->V[l] * w->C[l + 1]), 256, 0, st>>>(h, w->u[l], d, d, d, w->C[l + 1]);
+    const Layer& la = w->layers[li++];
+    int rc = launch_conv(la.cin, la.cout, true, true, w->u[l], la.wf, w->p + la.boff, w->b[l], w->da[l], d, d, d, st);
+    if (rc) return rc;
+    const Layer& lb = w->layers[li++];
+    rc = launch_conv(lb.cin, lb.cout, true, false, w->da[l], lb.wf, w->p + lb.boff, nullptr, w->db[l], d, d, d, st);
+    if (rc) return rc;
+    h = w->db[l];
+  }
+  const bf16* last = L > 1 ? w->db[0] : w->b[0];
+  out_fwd_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(last, w->p + w->out_w, w->p + w->out_b, w->y, w->V[0], w->C[0]);
+  return check_cuda(cudaGetLastError(), "wsnet forward");
+}
+
+// Accumulates dLoss/dtheta into w->g for the current y, t; loss partials in
+// w->misc (one per block of kLossChunk voxels).
+constexpr int kLossChunk = 16384;
+
+int bias_grad(wsnet* w, const bf16* g, int64_t V, int C, float* db, cudaStream_t st) {
+  const int chunk = 4096;
+  const int blocks = static_cast<int>((V + chunk - 1) / chunk);
+  chan_sum_kernel<bf16><<<blocks, 64, 0, st>>>(g, w->part, V, C, chunk);
+  chan_sum_reduce_kernel<<<1, 64, 0, st>>>(w->part, db, C, blocks);
+  return check_cuda(cudaGetLastError(), "bias grad");
+}
+
+int conv_backward(wsnet* w, const Layer& ly, const bf16* in, const bf16* g, bf16* gin, int d, cudaStream_t st) {
+  const int64_t V = static_cast<int64_t>(d) * d * d;
+  int rc = launch_wgrad(ly.cin, ly.cout, in, g, w->part, w->g + ly.woff, d, d, d, st);
+  if (!rc) rc = bias_grad(w, g, V, ly.cout, w->g + ly.boff, st);
+  if (!rc && gin) rc = launch_conv(ly.cout, ly.cin, false, false, g, ly.wt, w->zero_bias, nullptr, gin, d, d, d, st);
+  return rc;
+}
+
+int backward(wsnet* w, cudaStream_t st) {
+  const int L = w->L;
+  const int64_t V0 = w->V[0];
+  const bf16* last = L > 1 ? w->db[0] : w->b[0];
+  const int lblocks = static_cast<int>((V0 + kLossChunk - 1) / kLossChunk);
+  mse_bwd_kernel<<<lblocks, 256, 0, st>>>(w->y, w->t, w->p + w->out_w, w->gy, w->gA[0], w->misc, V0, w->C[0],
+                                          kLossChunk);
+  const int ochunk = 4096;
+  const int oblocks = static_cast<int>((V0 + ochunk - 1) / ochunk);
+  out_wgrad_kernel<<<oblocks, 64, 0, st>>>(last, w->gy, w->part, V0, w->C[0], ochunk);
+  chan_sum_reduce_kernel<<<1, 64, 0, st>>>(w->part, w->g + w->out_w, w->C[0] + 1, oblocks);
+  int rc = check_cuda(cudaGetLastError(), "output layer backward");
+  if (rc) return rc;
+  int li = static_cast<int>(w->layers.size()) - 1;  // layers in reverse forward order
+  for (int l = 0; l <= L - 2; ++l) {
+    const int d = w->dim[l];
+    const int64_t V = w->V[l];
+    const Layer& lb = w->layers[li--];
+    const Layer& la = w->layers[li--];
+    relu_bwd_kernel<<<blocks_for(V * lb.cout), 256, 0, st>>>(w->gA[l], nullptr, w->db[l], w->gB[l], V * lb.cout);
+    rc = conv_backward(w, lb, w->da[l], w->gB[l], w->gA[l], d, st);
+    if (rc) return rc;
+    relu_bwd_kernel<<<blocks_for(V * la.cout), 256, 0, st>>>(w->gA[l], nullptr, w->da[l], w->gs[l], V * la.cout);
+    rc = conv_backward(w, la, w->u[l], w->gs[l], w->gB[l], d, st);
+    if (rc) return rc;
+    up2_bwd_kernel<<<blocks_for(w->V[l + 1] * la.cin), 256, 0, st>>>(w->gB[l], w->gA[l + 1], w->dim[l + 1],
+                                                                     w->dim[l + 1], w->dim[l + 1], la.cin);
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const int d = w->dim[l];
+    const int64_t V = w->V[l];
+    const Layer& lb = w->layers[li--];
+    const Layer& la = w->layers[li--];
+    relu_bwd_kernel<<<blocks_for(V * lb.cout), 256, 0, st>>>(w->gA[l], l <= L - 2 ? w->gs[l] : nullptr, w->b[l],
+                                                             w->gB[l], V * lb.cout);
+    rc = conv_backward(w, lb, w->a[l], w->gB[l], w->gA[l], d, st);
+    if (rc) return rc;
+    relu_bwd_kernel<<<blocks_for(V * la.cout), 256, 0, st>>>(w->gA[l], nullptr, w->a[l], w->gB[l], V * la.cout);
+    rc = conv_backward(w, la, l > 0 ? w->pl[l] : w->x0, w->gB[l], l > 0 ? w->gA[l] : nullptr, d, st);
+    if (rc) return rc;
+    if (l > 0)
+      pool2_bwd_kernel<<<blocks_for(w->V[l - 1] * la.cin), 256, 0, st>>>(w->gA[l], w->gA[l - 1], 2 * d, 2 * d,
+                                                                         2 * d, la.cin);
+  }
+  return check_cuda(cudaGetLastError(), "wsnet backward");
+}
+
+int check_grid(const wsnet* w, const stencil_grid* g, const char* name, Grid* out) {
+  int rc = validate_grid(g, name, out, false);
+  if (rc) return rc;
+  if (out->dtype != STENCIL_F64) return set_error(STENCIL_ERR_DTYPE, "wsnet: %s must be F64", name);
+  if (out->nx != w->n || out->ny != w->n || out->nz != w->n)
+    return set_error(STENCIL_ERR_ARG, "wsnet: %s must be %d^3 (the size the net was created for)", name, w->n);
+  return STENCIL_OK;
+}
+
+// rms of f's interior into w->rms, then the normalised input x0.
+int load_input(wsnet* w, const Grid& f, cudaStream_t st) {
+  const int blocks = 256;
+  sumsq_kernel<<<blocks, 256, 0, st>>>(static_cast<const double*>(f.data), f.sy, f.sz, w->n, w->rms_part);
+  rms_kernel<<<1, 32, 0, st>>>(w->rms_part, blocks, static_cast<double>(w->V[0]), w->rms);
+  input_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(static_cast<const double*>(f.data), f.sy, f.sz, w->n, w->rms,
+                                                    w->x0);
+  return check_cuda(cudaGetLastError(), "wsnet input");
+}
+
+struct DevGuard {
+  int prev = -1;
+  int rc = STENCIL_OK;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) rc = check_cuda(cudaSetDevice(dev), "cudaSetDevice");
+  }
+  ~DevGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+}  // namespace net
+}  // namespace stencil
+
+using namespace stencil;
+using namespace stencil::net;
+
+extern "C" int wsnet_create(int device, int32_t levels, const int32_t* channels, int32_t n, uint64_t seed,
+                            wsnet** out) {
+  if (!out || !channels || levels < 1 || levels > kMaxLevels || n < 1)
+    return set_error(STENCIL_ERR_ARG, "wsnet_create: bad arguments");
+  *out = nullptr;
+  if (n % (1 << (levels - 1)) != 0)
+    return set_error(STENCIL_ERR_ARG, "wsnet_create: n must be a multiple of 2^(levels-1)");
+  for (int l = 0; l < levels; ++l)
+    if (channels[l] != 16 && channels[l] != 32 && channels[l] != 64)
+      return set_error(STENCIL_ERR_ARG, "wsnet_create: channels must be 16, 32 or 64");
+  DevGuard dg(device);
+  if (dg.rc) return dg.rc;
+  wsnet* w = new (std::nothrow) wsnet();
+  if (!w) return set_error(STENCIL_ERR_ARG, "wsnet_create: out of host memory");
+  w->device = device;
+  w->L = levels;
+  w->n = n;
+  for (int l = 0; l < levels; ++l) {
+    w->C[l] = channels[l];
+    w->dim[l] = n >> l;
+    w->V[l] = static_cast<int64_t>(w->dim[l]) * w->dim[l] * w->dim[l];
+  }
+  // parameter layout: per layer W[cout][27*cin] then b[cout]; then out.w, out.b
+  int64_t off = 0, welems = 0;
+  auto add = [&](int cin, int cout, int level) {
+    Layer ly;
+    ly.cin = cin; ly.cout = cout; ly.level = level;
+    ly.woff = off; off += static_cast<int64_t>(cout) * 27 * cin;
+    ly.boff = off; off += cout;
+    ly.wf = ly.wt = nullptr;
+    welems += static_cast<int64_t>(cout) * kpad(cin) + static_cast<int64_t>(cin) * kpad(cout);
+    w->layers.push_back(ly);
+  };
+  for (int l = 0; l < levels; ++l) {
+    add(l == 0 ? 1 : channels[l - 1], channels[l], l);
+    add(channels[l], channels[l], l);
+  }
+  for (int l = levels - 2; l >= 0; --l) {
+    add(channels[l + 1], channels[l], l);
+    add(channels[l], channels[l], l);
+  }
+  w->out_w = off; off += channels[0];
+  w->out_b = off; off += 1;
+  w->nparams = off;
+  int rc = STENCIL_OK;
+  auto A = [&](auto** p, size_t count) { if (!rc) rc = dalloc_t(w, p, count); };
+  A(&w->p, off); A(&w->g, off); A(&w->m, off); A(&w->v, off);
+  A(&w->wbuf, static_cast<size_t>(welems));
+  A(&w->zero_bias, 64);
+  A(&w->x0, static_cast<size_t>(w->V[0]));
+  int64_t part = 0;
+  for (int l = 0; l < levels; ++l) {
+    const size_t V = static_cast<size_t>(w->V[l]);
+    A(&w->a[l], V * channels[l]);
+    A(&w->b[l], V * channels[l]);
+    if (l > 0) A(&w->pl[l], V * channels[l - 1]);
+    if (l <= levels - 2) {
+      A(&w->u[l], V * channels[l + 1]);
+      A(&w->da[l], V * channels[l]);
+      A(&w->db[l], V * channels[l]);
+      A(&w->gs[l], V * channels[l]);
+    }
+    A(&w->gA[l], V * 64);
+    A(&w->gB[l], V * 64);
+  }
+  for (const Layer& ly : w->layers) {
+    const int64_t chunks = (w->V[ly.level] + kWgradChunk - 1) / kWgradChunk;
+    part = std::max(part, chunks * ly.cout * kpad(ly.cin));
+  }
+  part = std::max<int64_t>(part, (w->V[0] / 4096 + 2) * 65);
+  w->part_elems = part;
+  A(&w->part, static_cast<size_t>(part));
+  A(&w->y, static_cast<size_t>(w->V[0]));
+  A(&w->t, static_cast<size_t>(w->V[0]));
+  A(&w->gy, static_cast<size_t>(w->V[0]));
+  A(&w->misc, static_cast<size_t>(w->V[0] / kLossChunk + 16));
+  A(&w->rms_part, 256);
+  A(&w->rms, 4);
+  if (rc) {
+    wsnet_destroy(w);
+    return rc;
+  }
+  int64_t wo = 0;
+  for (Layer& ly : w->layers) {
+    ly.wf = w->wbuf + wo;
+    wo += static_cast<int64_t>(ly.cout) * kpad(ly.cin);
+    ly.wt = w->wbuf + wo;
+    wo += static_cast<int64_t>(ly.cin) * kpad(ly.cout);
+  }
+  // He-normal weights (std sqrt(2 / (27 cin))), zero biases; output layer
+  // std sqrt(1 / C0).
+  std::vector<float> hp(static_cast<size_t>(off), 0.0f);
+  uint64_t s = seed;
+  for (const Layer& ly : w->layers) {
+    const double sd = sqrt(2.0 / (27.0 * ly.cin));
+    for (int64_t i = 0; i < static_cast<int64_t>(ly.cout) * 27 * ly.cin; ++i)
+      hp[ly.woff + i] = static_cast<float>(normal(s) * sd);
+  }
+  for (int c = 0; c < channels[0]; ++c) hp[w->out_w + c] = static_cast<float>(normal(s) * sqrt(1.0 / channels[0]));
+  rc = check_cuda(cudaMemcpy(w->p, hp.data(), sizeof(float) * off, cudaMemcpyHostToDevice), "wsnet init");
+  if (!rc) rc = mirror(w, nullptr);
+  if (!rc) rc = check_cuda(cudaDeviceSynchronize(), "wsnet init sync");
+  if (rc) {
+    wsnet_destroy(w);
+    return rc;
+  }
+  *out = w;
+  return STENCIL_OK;
+}
+
+extern "C" int wsnet_destroy(wsnet* w) {
+  if (!w) return STENCIL_OK;
+  DevGuard dg(w->device);
+  cudaDeviceSynchronize();
+  for (void* p : w->allocs) cudaFree(p);
+  delete w;
+  return STENCIL_OK;
+}
+
+extern "C" int wsnet_num_params(const wsnet* w, int64_t* count) {
+  if (!w || !count) return set_error(STENCIL_ERR_ARG, "wsnet_num_params: null argument");
+  *count = w->nparams;
+  return STENCIL_OK;
+}
+
+extern "C" int wsnet_get_params(wsnet* w, float* host, int64_t count) {
+  if (!w || !host || count != w->nparams) return set_error(STENCIL_ERR_ARG, "wsnet_get_params: bad arguments");
+  DevGuard dg(w->device);
+  return check_cuda(cudaMemcpy(host, w->p, sizeof(float) * count, cudaMemcpyDeviceToHost), "wsnet_get_params");
+}
+
+extern "C" int wsnet_set_params(wsnet* w, const float* host, int64_t count) {
+  if (!w || !host || count != w->nparams) return set_error(STENCIL_ERR_ARG, "wsnet_set_params: bad arguments");
+  DevGuard dg(w->device);
+  int rc = check_cuda(cudaMemcpy(w->p, host, sizeof(float) * count, cudaMemcpyHostToDevice), "wsnet_set_params");
+  if (!rc) rc = mirror(w, nullptr);
+  if (!rc) rc = check_cuda(cudaDeviceSynchronize(), "wsnet_set_params sync");
+  return rc;
+}
+
+extern "C" int wsnet_infer(wsnet* w, const stencil_grid* f, const stencil_grid* u, void* stream) {
+  if (!w) return set_error(STENCIL_ERR_ARG, "wsnet_infer: null net");
+  Grid gf, gu;
+  int rc = check_grid(w, f, "f", &gf);
+  if (!rc) rc = check_grid(w, u, "u", &gu);
+  if (rc) return rc;
+  DevGuard dg(w->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = load_input(w, gf, st);
+  if (!rc) rc = forward(w, st);
+  if (rc) return rc;
+  output_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(w->y, static_cast<double*>(gu.data), gu.sy, gu.sz, w->n, w->rms,
+                                                     kOutScale);
+  return check_cuda(cudaGetLastError(), "wsnet output");
+}
+
+extern "C" int wsnet_train_step(wsnet* w, const stencil_grid* f, const stencil_grid* u, int32_t count, float lr,
+                                double* loss, void* stream) {
+  if (!w || !f || !u || count < 1) return set_error(STENCIL_ERR_ARG, "wsnet_train_step: bad arguments");
+  DevGuard dg(w->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = check_cuda(cudaMemsetAsync(w->g, 0, sizeof(float) * w->nparams, st), "zero grads");
+  if (rc) return rc;
+  const int lblocks = static_cast<int>((w->V[0] + kLossChunk - 1) / kLossChunk);
+  double total = 0.0;
+  std::vector<float> lp(static_cast<size_t>(lblocks));
+  for (int s = 0; s < count; ++s) {
+    Grid gf, gu;
+    rc = check_grid(w, &f[s], "f", &gf);
+    if (!rc) rc = check_grid(w, &u[s], "u", &gu);
+    if (!rc) rc = load_input(w, gf, st);
+    if (rc) return rc;
+    target_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(static_cast<const double*>(gu.data), gu.sy, gu.sz, w->n,
+                                                       w->rms, kOutScale, w->t);
+    rc = forward(w, st);
+    if (!rc) rc = backward(w, st);
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(lp.data(), w->misc, sizeof(float) * lblocks, cudaMemcpyDeviceToHost, st),
+                             "loss read");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "train sync");
+    if (rc) return rc;
+    double sl = 0.0;
+    for (float x : lp) sl += x;
+    total += sl / static_cast<double>(w->V[0]);
+  }
+  w->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - powf(b1, static_cast<float>(w->step));
+  const float c2 = 1.0f - powf(b2, static_cast<float>(w->step));
+  adam_kernel<<<blocks_for(w->nparams), 256, 0, st>>>(w->p, w->g, w->m, w->v, w->nparams, lr, b1, b2, 1e-8f, c1, c2,
+                                                      1.0f / static_cast<float>(count));
+  rc = check_cuda(cudaGetLastError(), "adam");
+  if (!rc) rc = mirror(w, st);
+  if (rc) return rc;
+  if (loss) *loss = total / count;
+  return STENCIL_OK;
+}
+
+// Test hook: for a normalised input x and target t (device FP32 arrays of
+// n^3 values, channels-last), run forward and backward once from zeroed
+// gradients; y (device, optional) receives the output, grads (host,
+// optional) the parameter gradients, *loss the mean squared error.
+extern "C" int wsnet_loss_grad(wsnet* w, const float* x, const float* t, float* y, float* grads, double* loss,
+                               void* stream) {
+  if (!w || !x || !t) return set_error(STENCIL_ERR_ARG, "wsnet_loss_grad: null argument");
+  DevGuard dg(w->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<float> hx(static_cast<size_t>(w->V[0]));
+  int rc = check_cuda(cudaMemcpyAsync(hx.data(), x, sizeof(float) * w->V[0], cudaMemcpyDeviceToHost, st), "x read");
+  if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "sync");
+  if (rc) return rc;
+  std::vector<bf16> hb(hx.size());
+  for (size_t i = 0; i < hx.size(); ++i) hb[i] = __float2bfloat16_rn(hx[i]);
+  rc = check_cuda(cudaMemcpyAsync(w->x0, hb.data(), sizeof(bf16) * hb.size(), cudaMemcpyHostToDevice, st), "x load");
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(w->t, t, sizeof(float) * w->V[0], cudaMemcpyDeviceToDevice, st), "t load");
+  if (!rc) rc = check_cuda(cudaMemsetAsync(w->g, 0, sizeof(float) * w->nparams, st), "zero grads");
+  if (!rc) rc = forward(w, st);
+  if (!rc) rc = backward(w, st);
+  if (rc) return rc;
+  if (y) rc = check_cuda(cudaMemcpyAsync(y, w->y, sizeof(float) * w->V[0], cudaMemcpyDeviceToDevice, st), "y copy");
+  const int lblocks = static_cast<int>((w->V[0] + kLossChunk - 1) / kLossChunk);
+  std::vector<float> lp(static_cast<size_t>(lblocks));
+  if (!rc) rc = check_cuda(cudaMemcpyAsync(lp.data(), w->misc, sizeof(float) * lblocks, cudaMemcpyDeviceToHost, st),
+                           "loss read");
+  if (!rc && grads)
+    rc = check_cuda(cudaMemcpyAsync(grads, w->g, sizeof(float) * w->nparams, cudaMemcpyDeviceToHost, st), "grads");
+  if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "sync");
+  if (rc) return rc;
+  double sl = 0.0;
+  for (float v : lp) sl += v;
+  if (loss) *loss = sl / static_cast<double>(w->V[0]);
+  return STENCIL_OK;
+}

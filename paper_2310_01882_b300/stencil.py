@@ -70,6 +70,16 @@ SIGNATURES = {
     "stencil_advect_uvw": ([_P, _G, _G, _G, _G, _G, _G, _P, _P, ctypes.c_double, ctypes.c_double, _P],
                            ctypes.c_int),
     "stencil_residual_noalloc": ([_G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
+    "wsnet_create": ([ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                      ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "wsnet_destroy": ([_P], ctypes.c_int),
+    "wsnet_num_params": ([_P, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "wsnet_get_params": ([_P, _P, ctypes.c_int64], ctypes.c_int),
+    "wsnet_set_params": ([_P, _P, ctypes.c_int64], ctypes.c_int),
+    "wsnet_infer": ([_P, _G, _G, _P], ctypes.c_int),
+    "wsnet_train_step": ([_P, _G, _G, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_double), _P],
+                         ctypes.c_int),
+    "wsnet_loss_grad": ([_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "stencil_batch_workspace_size": ([ctypes.POINTER(stencil_problem), ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "stencil_batch_solve": ([_P, ctypes.POINTER(stencil_problem), ctypes.c_int32,
@@ -257,3 +267,62 @@ def stencil_batch_solve(ctx, us, fs, hs, rtol, inner_dtype=F32, max_sweeps=0, sw
                                      ctypes.c_void_p(workspace.data_ptr()), need, res, _stream(stream)))
     return [{"sweeps": r.sweeps, "cycles": r.cycles, "status": r.status, "rel_residual": r.rel_residual,
              "final_dtype": r.final_dtype} for r in res]
+
+
+class WsNet:
+    """Owns a wsnet (the warm-start network; see include/stencil.h)."""
+
+    def __init__(self, levels, channels, n, seed=0, device=0):
+        h = ctypes.c_void_p()
+        ch = (ctypes.c_int32 * len(channels))(*channels)
+        _check(lib().wsnet_create(int(device), int(levels), ch, int(n), int(seed), ctypes.byref(h)))
+        self.handle, self.levels, self.channels, self.n = h, levels, list(channels), n
+        c = ctypes.c_int64()
+        _check(lib().wsnet_num_params(h, ctypes.byref(c)))
+        self.num_params = c.value
+
+    def get_params(self):
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().wsnet_get_params(self.handle, ctypes.c_void_p(out.ctypes.data), self.num_params))
+        return out
+
+    def set_params(self, arr):
+        arr = np.ascontiguousarray(arr, dtype=np.float32)
+        assert arr.size == self.num_params
+        _check(lib().wsnet_set_params(self.handle, ctypes.c_void_p(arr.ctypes.data), self.num_params))
+
+    def close(self):
+        if self.handle:
+            lib().wsnet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wsnet_infer(net, f, u, stream=None):
+    gf, gu = f.grid(), u.grid()
+    return _check(lib().wsnet_infer(net.handle, ctypes.byref(gf), ctypes.byref(gu), _stream(stream)))
+
+
+def wsnet_train_step(net, fs, us, lr, stream=None):
+    """One Adam step over the samples (lists of F64 Fields); returns the loss."""
+    af = (stencil_grid * len(fs))(*[f.grid() for f in fs])
+    au = (stencil_grid * len(us))(*[u.grid() for u in us])
+    loss = ctypes.c_double()
+    _check(lib().wsnet_train_step(net.handle, af, au, len(fs), float(lr), ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def wsnet_loss_grad(net, x, t, y=None, want_grads=True, stream=None):
+    """x, t, y: float32 CUDA tensors of n^3 values.  Returns (loss, grads)."""
+    grads = np.empty(net.num_params, dtype=np.float32) if want_grads else None
+    loss = ctypes.c_double()
+    _check(lib().wsnet_loss_grad(net.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                 ctypes.c_void_p(y.data_ptr()) if y is not None else None,
+                                 ctypes.c_void_p(grads.ctypes.data) if grads is not None else None,
+                                 ctypes.byref(loss), _stream(stream)))
+    return loss.value, grads

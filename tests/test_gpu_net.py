@@ -1,0 +1,134 @@
+"""GPU parity of the warm-start network kernels (BF16 tensor-core 3x3x3
+convolutions, pooling, upsampling, ReLU, output layer, loss and gradients)
+against the FP64 network oracle run on the same bf16-rounded weights and
+inputs with bf16 rounding of every stored activation."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import net as onet
+from paper_2310_01882_b300 import inputs
+from paper_2310_01882_b300 import stencil as S
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16(a):
+    return oracle.from_bf16(oracle.to_bf16(np.asarray(a, dtype=np.float32))).astype(np.float64)
+
+
+def to_oracle_params(flat, channels, round_weights=True):
+    """Device parameter vector -> oracle dict (weights (3,3,3,cin,cout))."""
+    L = len(channels)
+    p = {}
+    off = 0
+    names = onet.layer_names(L)
+    dims = []
+    for l in range(L):
+        dims += [(1 if l == 0 else channels[l - 1], channels[l]), (channels[l], channels[l])]
+    for l in range(L - 2, -1, -1):
+        dims += [(channels[l + 1], channels[l]), (channels[l], channels[l])]
+    for name, (ci, co) in zip(names, dims):
+        w = flat[off:off + co * 27 * ci].astype(np.float64).reshape(co, 27, ci)
+        off += co * 27 * ci
+        w = w.transpose(1, 2, 0).reshape(3, 3, 3, ci, co)
+        p[name + ".w"] = bf16(w) if round_weights else w
+        p[name + ".b"] = flat[off:off + co].astype(np.float64)
+        off += co
+    p["out.w"] = flat[off:off + channels[0]].astype(np.float64).reshape(channels[0], 1)
+    off += channels[0]
+    p["out.b"] = flat[off:off + 1].astype(np.float64)
+    off += 1
+    assert off == flat.size
+    return p, names, dims
+
+
+def from_oracle_grads(g, channels):
+    L = len(channels)
+    parts = []
+    for name in onet.layer_names(L):
+        w = g[name + ".w"]
+        ci, co = w.shape[3], w.shape[4]
+        parts.append(w.reshape(27, ci, co).transpose(2, 0, 1).reshape(-1))
+        parts.append(g[name + ".b"])
+    parts.append(g["out.w"].reshape(-1))
+    parts.append(g["out.b"].reshape(-1))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("levels,channels,n", [(2, [16, 32], 16), (3, [16, 32, 64], 16)])
+def test_forward_backward_match_oracle(levels, channels, n):
+    import torch
+    net = S.WsNet(levels, channels, n, seed=3)
+    flat = net.get_params()
+    rng = np.random.default_rng(7)
+    # nonzero biases so every bias path is exercised
+    flat = flat.copy()
+    p0, names, dims = to_oracle_params(flat, channels, round_weights=False)
+    off = 0
+    for (ci, co) in dims:
+        off += co * 27 * ci
+        flat[off:off + co] = rng.standard_normal(co).astype(np.float32) * 0.05
+        off += co
+    net.set_params(flat)
+    p, _, _ = to_oracle_params(flat, channels)
+    x = rng.standard_normal((n, n, n)).astype(np.float32)
+    t = (rng.standard_normal((n, n, n)) * 0.3).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    td = torch.from_numpy(t).cuda()
+    yd = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+    loss, grads = S.wsnet_loss_grad(net, xd, td, yd)
+    y_ref, cache = onet.forward(p, bf16(x)[..., None], channels, act_round=bf16)
+    l_ref, gy = onet.mse(y_ref, t.astype(np.float64)[..., None])
+    y = yd.cpu().numpy().reshape(n, n, n)
+    assert np.max(np.abs(y - y_ref[..., 0])) <= 1e-2 * np.max(np.abs(y_ref)), np.max(np.abs(y - y_ref[..., 0]))
+    assert abs(loss - l_ref) <= 1e-2 * l_ref
+    g_ref = from_oracle_grads(onet.backward(p, cache, gy, channels), channels)
+    # per layer, normwise relative error of the gradient
+    off = 0
+    for name, (ci, co) in zip(names, dims):
+        for part, size in (("w", co * 27 * ci), ("b", co)):
+            a, b = grads[off:off + size], g_ref[off:off + size]
+            err = np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30)
+            assert err <= 3e-2, (name, part, err)
+            off += size
+    a, b = grads[off:], g_ref[off:]
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 3e-2
+    net.close()
+
+
+def test_infer_scaling_and_halo():
+    """wsnet_infer writes y * rms(f) / (3 pi^2) on the interior, halo kept."""
+    import torch
+    n = 16
+    net = S.WsNet(2, [16, 32], n, seed=4)
+    f = inputs.grf(n, seed=9) * 3.0
+    u0 = np.zeros_like(f)
+    u0[0] = 5.0
+    fd, ud = S.Field.from_numpy(f), S.Field.from_numpy(u0)
+    S.wsnet_infer(net, fd, ud)
+    torch.cuda.synchronize()
+    got = ud.to_numpy()
+    rms = np.sqrt(np.mean(f[1:-1, 1:-1, 1:-1] ** 2))
+    p, _, _ = to_oracle_params(net.get_params(), [16, 32])
+    x = bf16(f[1:-1, 1:-1, 1:-1] / rms)[..., None]
+    y, _ = onet.forward(p, x, [16, 32], act_round=bf16)
+    ref = y[..., 0] * rms / (3 * np.pi ** 2)
+    assert np.max(np.abs(got[1:-1, 1:-1, 1:-1] - ref)) <= 1e-2 * np.max(np.abs(ref))
+    assert np.all(got[0] == 5.0) and np.all(got[-1] == 0.0)
+    net.close()
+
+
+def test_training_reduces_loss():
+    """Adam on 4 fixed (source, solution) pairs of 16^3: the loss falls."""
+    from oracle import exact
+    n = 16
+    net = S.WsNet(2, [16, 32], n, seed=5)
+    fs, us = [], []
+    for q in range(4):
+        f = inputs.grf(n, seed=300 + q)
+        fs.append(S.Field.from_numpy(f))
+        us.append(S.Field.from_numpy(exact.solve(f, 1.0 / (n + 1))))
+    losses = [S.wsnet_train_step(net, fs, us, 2e-3) for _ in range(40)]
+    assert losses[-1] < 0.3 * losses[0], losses[::8]
+    net.close()
