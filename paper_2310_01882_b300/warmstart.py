@@ -1,0 +1,224 @@
+"""Learned warm start for the Jacobi Poisson solve: data, training, evaluation.
+
+    python -m paper_2310_01882_b300.warmstart [--n 128] [--train 200] [--test 20]
+        [--epochs 30] [--batch 4] [--lr 1e-3] [--out DIR]
+
+Pairs (f, u*): f a k^-3 Gaussian random field (seeds 10000+i for training,
+20000+i held out), u* from plain FP64 Jacobi (stencil_jacobi_sweep) from zero
+until the FP64 relative residual (stencil_residual) is at most 1e-8.  The
+net (wsnet_*, 4 levels 16-32-64-64) is trained with Adam and a cosine
+learning-rate decay; on the held-out fields the sweeps and wall time to
+relative residual 1e-8 are measured for a zero start and for the warm start,
+with plain FP64 Jacobi and with the mixed-precision solve
+(stencil_batch_solve, FP32 inner storage).  The residual computed in FP64 is
+the judge throughout.  The warm start's own residual is recorded; the
+"selected" figures use it only when, after `judge_sweeps` plain sweeps from
+each start, its residual is below the zero start's (the fallback is plain
+Jacobi from zero).
+
+Host-side orchestration only: every step runs in the library's kernels.
+"""
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import inputs
+from . import stencil as S
+
+CHANNELS = [16, 32, 64, 64]
+RTOL = 1e-8
+
+
+class Solver:
+    """Plain FP64 Jacobi on one grid size, one context per stream."""
+
+    def __init__(self, n, streams=1):
+        import torch
+        self.n = n
+        self.h = 1.0 / (n + 1)
+        self.ctxs = [S.Context(0) for _ in range(streams)]
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.tmp = [S.Field(n, n, n) for _ in range(streams)]
+        self.work = [S.Field(n, n, n) for _ in range(streams)]
+        self.norms = torch.zeros((streams, 2), dtype=torch.float64, device="cuda")
+
+    def solve(self, us, fs, chunk=1000, max_sweeps=2_000_000):
+        """Sweep every u (F64 Fields, in place) until its relative residual is
+        <= RTOL, checking every `chunk` sweeps; up to len(streams) at once.
+        Returns per-instance (sweeps, rel)."""
+        import torch
+        out = [None] * len(us)
+        k = len(self.streams)
+        for base in range(0, len(us), k):
+            idx = list(range(base, min(base + k, len(us))))
+            sweeps = {i: 0 for i in idx}
+            active = set(idx)
+            while active:
+                for j, i in enumerate(idx):
+                    if i in active:
+                        S.stencil_residual(self.ctxs[j], us[i], fs[i], self.h, self.norms[j], stream=self.streams[j])
+                torch.cuda.synchronize()
+                nrm = self.norms.cpu().numpy()
+                for j, i in enumerate(idx):
+                    if i not in active:
+                        continue
+                    rel = nrm[j, 0] / nrm[j, 1]
+                    if rel <= RTOL or sweeps[i] >= max_sweeps:
+                        out[i] = (sweeps[i], float(rel))
+                        active.discard(i)
+                for j, i in enumerate(idx):
+                    if i in active:
+                        S.stencil_jacobi_sweep(self.ctxs[j], us[i], self.tmp[j], fs[i], self.work[j], self.h, chunk,
+                                               0, S.SWEEP_AUTO, stream=self.streams[j])
+                        sweeps[i] += chunk
+        return out
+
+
+def generate_pairs(solver, seeds):
+    """(f, u*) Field pairs for the given GRF seeds (u* from plain FP64 Jacobi)."""
+    n = solver.n
+    fs = [S.Field.from_numpy(inputs.grf(n, seed=s)) for s in seeds]
+    us = [S.Field(n, n, n) for _ in seeds]
+    info = solver.solve(us, fs)
+    return fs, us, info
+
+
+def train(net, fs, us, epochs, batch, lr0, seed=0, log=None):
+    """Adam with a cosine decay from lr0 to lr0/20 over all steps."""
+    rng = np.random.default_rng(seed)
+    steps = epochs * max(1, len(fs) // batch)
+    hist = []
+    step = 0
+    for ep in range(epochs):
+        order = rng.permutation(len(fs))
+        losses = []
+        for b in range(0, len(fs) - batch + 1, batch):
+            lr = lr0 * (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * step / max(1, steps))))
+            sel = order[b:b + batch]
+            losses.append(S.wsnet_train_step(net, [fs[i] for i in sel], [us[i] for i in sel], lr))
+            step += 1
+        hist.append(float(np.mean(losses)))
+        if log:
+            log(f"epoch {ep}: loss {hist[-1]:.4e}")
+    return hist
+
+
+def evaluate(net, solver, seeds, chunk=200, judge_sweeps=50):
+    """Sweeps / seconds to RTOL from a zero start and from the warm start,
+    with plain FP64 Jacobi and with the mixed-precision batch solve."""
+    import torch
+    n, h = solver.n, solver.h
+    ctx = solver.ctxs[0]
+    rows = []
+    for s in seeds:
+        f_np = inputs.grf(n, seed=s)
+        f = S.Field.from_numpy(f_np)
+        r = {"seed": s}
+        # warm start (inference timed), judged by its FP64 residual
+        u_w = S.Field(n, n, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.wsnet_infer(net, f, u_w)
+        S.stencil_residual(ctx, u_w, f, h, solver.norms[0])
+        torch.cuda.synchronize()
+        r["infer_s"] = time.perf_counter() - t0
+        nrm = solver.norms[0].cpu().numpy()
+        r["warm_rel0"] = float(nrm[0] / nrm[1])
+        warm0 = u_w.storage.clone()
+        for name, start in (("zero", None), ("warm", warm0)):
+            u = S.Field(n, n, n)
+            if start is not None:
+                u.storage.copy_(start)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            (sw, rel), = solver.solve([u], [f], chunk=chunk)
+            torch.cuda.synchronize()
+            r[f"fp64_{name}"] = {"sweeps": sw, "seconds": time.perf_counter() - t0, "rel": rel}
+            u = S.Field(n, n, n)
+            if start is not None:
+                u.storage.copy_(start)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = S.stencil_batch_solve(ctx, [u], [f], [h], RTOL, inner_dtype=S.F32, sweeps_per_cycle=400)
+            torch.cuda.synchronize()
+            r[f"mixed_{name}"] = {"sweeps": res[0]["sweeps"], "seconds": time.perf_counter() - t0,
+                                  "rel": res[0]["rel_residual"], "status": res[0]["status"]}
+        # judge: residual after judge_sweeps plain sweeps from each start
+        rels = {}
+        for name, start in (("zero", None), ("warm", warm0)):
+            u = S.Field(n, n, n)
+            if start is not None:
+                u.storage.copy_(start)
+            S.stencil_jacobi_sweep(ctx, u, solver.tmp[0], f, None, h, judge_sweeps, 0, S.SWEEP_AUTO)
+            S.stencil_residual(ctx, u, f, h, solver.norms[0])
+            nrm = solver.norms[0].cpu().numpy()
+            rels[name] = float(nrm[0] / nrm[1])
+        r["judge_rel"] = rels
+        r["fallback"] = not (rels["warm"] < rels["zero"])
+        rows.append(r)
+    return rows
+
+
+def summarise(rows):
+    def med(key, field):
+        return float(np.median([r[key][field] for r in rows]))
+    out = {k: {"sweeps_median": med(k, "sweeps"), "seconds_median": med(k, "seconds")}
+           for k in ("fp64_zero", "fp64_warm", "mixed_zero", "mixed_warm")}
+    inf = float(np.median([r["infer_s"] for r in rows]))
+    base = out["fp64_zero"]["seconds_median"]
+    out["infer_seconds_median"] = inf
+    out["speedup_vs_fp64_zero"] = {k: base / (out[k]["seconds_median"] + (inf if "warm" in k else 0.0))
+                                   for k in ("fp64_warm", "mixed_zero", "mixed_warm")}
+    out["warm_rel0_median"] = float(np.median([r["warm_rel0"] for r in rows]))
+    out["fallbacks"] = int(sum(1 for r in rows if r.get("fallback")))
+    # with the fallback applied: the warm start only where the judge accepted it
+    sel = []
+    for r in rows:
+        k = "mixed_zero" if r.get("fallback") else "mixed_warm"
+        sel.append(r[k]["seconds"] + (0.0 if r.get("fallback") else r["infer_s"]))
+    out["selected_mixed_seconds_median"] = float(np.median(sel))
+    out["speedup_selected_mixed_vs_fp64_zero"] = base / float(np.median(sel))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--test", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--out", default=".")
+    args = ap.parse_args()
+    import torch
+    log = lambda m: print(m, flush=True)  # noqa: E731
+    solver = Solver(args.n, streams=args.streams)
+    t0 = time.perf_counter()
+    fs, us, info = generate_pairs(solver, [10000 + i for i in range(args.train)])
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    log(f"generated {args.train} pairs in {gen_s:.1f} s; sweeps median {np.median([s for s, _ in info])}")
+    net = S.WsNet(len(CHANNELS), CHANNELS, args.n, seed=1)
+    t0 = time.perf_counter()
+    hist = train(net, fs, us, args.epochs, args.batch, args.lr, log=log)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    np.save(os.path.join(args.out, "wsnet_params.npy"), net.get_params())
+    rows = evaluate(net, solver, [20000 + i for i in range(args.test)])
+    summary = summarise(rows)
+    result = {"n": args.n, "train_pairs": args.train, "test_fields": args.test, "epochs": args.epochs,
+              "batch": args.batch, "lr": args.lr, "gen_seconds": gen_s, "train_seconds": train_s,
+              "loss_history": hist, "summary": summary, "rows": rows}
+    with open(os.path.join(args.out, "warmstart.json"), "w") as fh:
+        json.dump(result, fh, indent=1)
+    log(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()
