@@ -44,6 +44,7 @@
 #ifndef STENCIL_H_
 #define STENCIL_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -156,6 +157,41 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
                          const stencil_grid* u_tmp, const stencil_grid* f,
                          const stencil_grid* work, double h, int64_t nsweeps,
                          int32_t sweeps_per_pass, int32_t flags, void* stream);
+
+/*
+ * stencil_autotune_sweep -- the project's autotuner for stencil_jacobi_sweep.
+ * For the storage / arithmetic that (u dtype, flags, work) selects, time
+ * every compiled configuration of the sweep kernel (sweeps fused per pass,
+ * rows per warp, warps per CTA, shared-memory stages, CTAs per SM) on these
+ * grids, keep the fastest per pass length in ctx, and make the pass length
+ * with the fastest time per sweep the ctx's default (sweeps_per_pass = 0).
+ * Arguments as for stencil_jacobi_sweep; trial passes read u and write
+ * u_tmp's interior only (u is not changed).  report (nullable): a text line
+ * per configuration timed.  Synchronous; not to be called during a stream
+ * capture.  No counterpart in the paper (its tile sizes were fixed by hand).
+ */
+STENCIL_API int stencil_autotune_sweep(stencil_ctx* ctx, const stencil_grid* u,
+                                       const stencil_grid* u_tmp,
+                                       const stencil_grid* f,
+                                       const stencil_grid* work, double h,
+                                       int32_t flags, char* report,
+                                       size_t report_len, void* stream);
+
+/*
+ * Inspect or pin the sweep configuration (for reproducible runs and tests).
+ * (dtype, flags, with_work) select the storage / arithmetic exactly as in
+ * stencil_jacobi_sweep (with_work != 0: a work grid is passed; F64 fixed
+ * point with a work grid and 4 or more sweeps keeps the iterate resident).
+ * stencil_sweep_config_count writes the number of compiled configurations
+ * for pass length T (0 if none); stencil_sweep_config_select makes
+ * configuration `index` the one ctx uses for that pass length.
+ */
+STENCIL_API int stencil_sweep_config_count(int32_t dtype, int32_t flags,
+                                           int32_t with_work, int32_t T,
+                                           int32_t* count);
+STENCIL_API int stencil_sweep_config_select(stencil_ctx* ctx, int32_t dtype,
+                                            int32_t flags, int32_t with_work,
+                                            int32_t T, int32_t index);
 
 /*
  * stencil_residual -- the residual of A u = f for the 7-point operator

@@ -148,6 +148,10 @@ int stencil_ctx_create(int device, stencil_ctx** out) {
   if (!c) return set_error(STENCIL_ERR_ARG, "ctx_create: out of host memory");
   c->device = device;
   c->num_sms = prop.multiProcessorCount;
+  for (int p = 0; p < kNumPolicies; ++p) {
+    for (int t = 0; t <= kMaxPass; ++t) c->sweep_choice[p][t] = 0;
+    c->best_pass[p] = (p == kPolF32 || p == kPolBF16) ? 4 : 1;
+  }
   c->scratch_bytes = kScratchBytes;
   void* p = nullptr;
   rc = check_cuda(cudaMalloc(&p, c->scratch_bytes), "cudaMalloc(ctx scratch)");
@@ -230,6 +234,70 @@ int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_
   const bool use_work = work && gu.dtype == STENCIL_F64;
   return launch_jacobi(ctx, gu, gt, gf, use_work ? &gw : nullptr, h, nsweeps, sweeps_per_pass, flags,
                        static_cast<cudaStream_t>(stream));
+}
+
+static int policy_for(int32_t dtype, int32_t flags, int32_t with_work, int* policy) {
+  if (dtype == STENCIL_F64) {
+    if (flags == STENCIL_SWEEP_FP64_NATIVE) *policy = kPolF64;
+    else *policy = with_work ? kPolResident : kPolFixed;
+  } else if (dtype == STENCIL_F32) {
+    *policy = kPolF32;
+  } else if (dtype == STENCIL_BF16) {
+    *policy = kPolBF16;
+  } else {
+    return set_error(STENCIL_ERR_DTYPE, "unknown dtype %d", dtype);
+  }
+  return STENCIL_OK;
+}
+
+int stencil_sweep_config_count(int32_t dtype, int32_t flags, int32_t with_work, int32_t T, int32_t* count) {
+  if (!count) return set_error(STENCIL_ERR_ARG, "sweep_config_count: null count");
+  int policy = 0;
+  int rc = policy_for(dtype, flags, with_work, &policy);
+  if (rc) return rc;
+  const SweepVariant* v;
+  *count = (T >= 1 && T <= kMaxPass) ? sweep_variants(policy, T, &v) : 0;
+  return STENCIL_OK;
+}
+
+int stencil_sweep_config_select(stencil_ctx* ctx, int32_t dtype, int32_t flags, int32_t with_work, int32_t T,
+                                int32_t index) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "sweep_config_select: null ctx");
+  int policy = 0;
+  int rc = policy_for(dtype, flags, with_work, &policy);
+  if (rc) return rc;
+  const SweepVariant* v;
+  const int n = (T >= 1 && T <= kMaxPass) ? sweep_variants(policy, T, &v) : 0;
+  if (index < 0 || index >= n)
+    return set_error(STENCIL_ERR_ARG, "sweep_config_select: index %d out of range (%d configurations)", index, n);
+  ctx->sweep_choice[policy][T] = index;
+  return STENCIL_OK;
+}
+
+int stencil_autotune_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
+                           const stencil_grid* f, const stencil_grid* work, double h, int32_t flags, char* report,
+                           size_t report_len, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "autotune_sweep: null ctx");
+  Grid gu, gt, gf, gw;
+  int rc = validate_grid(u, "u", &gu, true);
+  if (!rc) rc = validate_grid(u_tmp, "u_tmp", &gt, true);
+  if (!rc) rc = validate_grid(f, "f", &gf, true);
+  if (!rc && work) rc = validate_grid(work, "work", &gw, true);
+  if (rc) return rc;
+  if ((rc = same_extents(gu, gt, "u", "u_tmp")) || (rc = same_extents(gu, gf, "u", "f"))) return rc;
+  if (work && (rc = same_extents(gu, gw, "u", "work"))) return rc;
+  if (gu.dtype != gt.dtype || gu.dtype != gf.dtype || (work && gw.dtype != STENCIL_F64))
+    return set_error(STENCIL_ERR_DTYPE, "autotune_sweep: dtype mismatch");
+  if (gu.data == gt.data || gu.data == gf.data || gt.data == gf.data)
+    return set_error(STENCIL_ERR_ARG, "autotune_sweep: u, u_tmp and f must be distinct buffers");
+  if (flags < STENCIL_SWEEP_AUTO || flags > STENCIL_SWEEP_FP64_FIXED)
+    return set_error(STENCIL_ERR_ARG, "autotune_sweep: unknown flags %d", flags);
+  if (!(h > 0.0) || !(h < 1.0e150)) return set_error(STENCIL_ERR_ARG, "autotune_sweep: bad h");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  const bool use_work = work && gu.dtype == STENCIL_F64;
+  return autotune_sweep(ctx, gu, gt, gf, use_work ? &gw : nullptr, h, flags, report, report_len,
+                        static_cast<cudaStream_t>(stream));
 }
 
 int stencil_residual(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* f, double h,

@@ -7,9 +7,20 @@
 
 #include "../../include/stencil.h"
 
+namespace stencil {
+// Sweep policies (storage / arithmetic) and the registry of compiled
+// configurations of the sweep kernel, indexed by policy and pass length T.
+enum SweepPolicy { kPolResident = 0, kPolFixed = 1, kPolF64 = 2, kPolF32 = 3, kPolBF16 = 4, kNumPolicies = 5 };
+constexpr int kMaxPass = 8;
+}  // namespace stencil
+
 struct stencil_ctx {
   int device;
   int num_sms;
+  // autotuned choice per policy: configuration index per pass length, and
+  // the pass length used when the caller asks for the library's choice
+  int sweep_choice[stencil::kNumPolicies][stencil::kMaxPass + 1];
+  int best_pass[stencil::kNumPolicies];
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)
@@ -55,9 +66,24 @@ int same_extents(const Grid& a, const Grid& b, const char* an, const char* bn);
 // TMA descriptor of a 3D halo grid with box (bx, by, 1).
 int make_tensor_map(CUtensorMap* map, const Grid& g, int box_x, int box_y);
 
+struct SweepArgs;
+using PassFn = int (*)(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, const SweepArgs& a,
+                       cudaStream_t st);
+struct SweepVariant {
+  int T, R, WY, S, minb;  // sweeps per pass, rows per warp, warps, stages, CTAs per SM
+  PassFn fn;
+};
+// Compiled configurations for (policy, T); returns their count (0 if none).
+int sweep_variants(int policy, int T, const SweepVariant** out);
+int sweep_variants_f64(int policy, int T, const SweepVariant** out);
+int sweep_variants_f32(int T, const SweepVariant** out);
+int sweep_variants_bf16(int T, const SweepVariant** out);
+
 // Kernel launchers (jacobi.cu, residual.cu, advect.cu).
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
+int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,
+                   int flags, char* report, size_t report_len, cudaStream_t st);
 int launch_residual(stencil_ctx* ctx, const Grid& u, const Grid& f, double h, const Grid* r,
                     double* norms_dev, cudaStream_t st);
 int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w, const Grid& su,

@@ -4,6 +4,10 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <string>
+
+#include <stdio.h>
+#include <string.h>
 
 #include "internal.h"
 #include "sweep_kernel.cuh"
@@ -136,115 +140,6 @@ __global__ void fx_unpack_kernel(const unsigned long long* __restrict__ src, dou
 // ---------------------------------------------------------------------------
 namespace {
 
-template <class Cfg>
-SweepGeom make_geom(const Grid& u, int zc) {
-  SweepGeom g;
-  g.nx = u.nx; g.ny = u.ny; g.nz = u.nz; g.sy = u.sy; g.sz = u.sz;
-  g.bxo = Cfg::BXO;
-  g.byo = Cfg::BYO;
-  g.tiles_x = static_cast<int>((u.nx + Cfg::BXO - 1) / Cfg::BXO);
-  g.tiles_y = static_cast<int>((u.ny + Cfg::BYO - 1) / Cfg::BYO);
-  g.zc = zc;
-  const int64_t zch = (u.nz + zc - 1) / zc;
-  g.items = static_cast<int64_t>(g.tiles_x) * g.tiles_y * zch;
-  return g;
-}
-
-// z chunk length: the longest (fewest re-read planes, 2T per chunk) that
-// still gives every resident CTA about four items for load balance.
-int pick_zc(int64_t tiles_xy, int64_t nz, int slots, int T) {
-  int zc = 256;
-  while (zc > 4 * T + 4 && tiles_xy * ((nz + zc - 1) / zc) < 4 * static_cast<int64_t>(slots)) zc /= 2;
-  return static_cast<int>(std::min<int64_t>(zc, nz));
-}
-
-template <class K>
-int grid_for(K kernel, int threads, int smem, int64_t items, int num_sms, int* grid, int* per_sm_out) {
-  int per_sm = 0;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute");
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute(carveout)");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  if (e != cudaSuccess) return check_cuda(e, "occupancy");
-  if (per_sm < 1) return set_error(STENCIL_ERR_CUDA, "sweep kernel cannot be resident");
-  *grid = static_cast<int>(std::min<int64_t>(items, static_cast<int64_t>(per_sm) * num_sms));
-  if (per_sm_out) *per_sm_out = per_sm;
-  return STENCIL_OK;
-}
-
-template <class Pol, class Cfg>
-int run_tb(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, const SweepArgs& a,
-           cudaStream_t st) {
-  auto kern = jacobi_tb<Pol, Cfg, SrcGrid<Pol>>;
-  SingleParams<Pol> prm;
-  int rc = make_tensor_map(&prm.tm_u, in, Cfg::BOXW, Cfg::UROWS);
-  if (rc) return rc;
-  rc = make_tensor_map(&prm.tm_f, f, Cfg::BOXW, Cfg::FROWS);
-  if (rc) return rc;
-  int grid = 0, per_sm = 0;
-  const int64_t txy = ((in.nx + Cfg::BXO - 1) / Cfg::BXO) * ((in.ny + Cfg::BYO - 1) / Cfg::BYO);
-  rc = grid_for(kern, Cfg::THREADS, Cfg::SMEM, txy * in.nz, ctx->num_sms, &grid, &per_sm);
-  if (rc) return rc;
-  const int zc = pick_zc(txy, in.nz, per_sm * ctx->num_sms, Cfg::T);
-  prm.g = make_geom<Cfg>(in, zc);
-  prm.out = static_cast<typename Pol::T*>(out.data);
-  prm.a = a;
-  grid = static_cast<int>(std::min<int64_t>(prm.g.items, static_cast<int64_t>(per_sm) * ctx->num_sms));
-  kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(prm);
-  return check_cuda(cudaGetLastError(), "jacobi_tb launch");
-}
-
-// Compiled tile shapes: (policy, sweeps per pass T, rows per warp R, warps
-// WY, stages S, CTAs per SM the register budget targets).
-using FixT1 = TbCfg<PolFixed, 1, 8, 4, 4, 3>;
-using ResT1 = TbCfg<PolResident, 1, 8, 4, 4, 3>;
-using ResT2 = TbCfg<PolResident, 2, 4, 4, 5, 2>;
-using F64T1 = TbCfg<PolF64, 1, 8, 4, 4, 3>;
-using F32T1 = TbCfg<PolF32, 1, 8, 8, 4, 2>;
-using F32T2 = TbCfg<PolF32, 2, 8, 4, 5, 1>;
-using F32T4 = TbCfg<PolF32, 4, 4, 4, 7, 1>;
-using B16T1 = TbCfg<PolBF16, 1, 8, 8, 4, 2>;
-using B16T2 = TbCfg<PolBF16, 2, 8, 4, 5, 1>;
-using B16T4 = TbCfg<PolBF16, 4, 4, 4, 7, 1>;
-
-// One pass of T sweeps from `in` to `out`.
-int run_pass(stencil_ctx* ctx, int dtype, bool fixed, int T, const Grid& in, const Grid& out,
-             const Grid& f, const SweepArgs& a, cudaStream_t st) {
-  if (dtype == kDtypeU64) {
-    if (T >= 2) return run_tb<PolResident, ResT2>(ctx, in, out, f, a, st);
-    return run_tb<PolResident, ResT1>(ctx, in, out, f, a, st);
-  }
-  if (dtype == STENCIL_F64) {
-    if (!fixed) return run_tb<PolF64, F64T1>(ctx, in, out, f, a, st);
-    return run_tb<PolFixed, FixT1>(ctx, in, out, f, a, st);
-  }
-  if (dtype == STENCIL_F32) {
-    if (T >= 4) return run_tb<PolF32, F32T4>(ctx, in, out, f, a, st);
-    if (T >= 2) return run_tb<PolF32, F32T2>(ctx, in, out, f, a, st);
-    return run_tb<PolF32, F32T1>(ctx, in, out, f, a, st);
-  }
-  if (T >= 4) return run_tb<PolBF16, B16T4>(ctx, in, out, f, a, st);
-  if (T >= 2) return run_tb<PolBF16, B16T2>(ctx, in, out, f, a, st);
-  return run_tb<PolBF16, B16T1>(ctx, in, out, f, a, st);
-}
-
-// Sweeps per pass the library picks when the caller passes 0.
-int default_spp(int dtype, bool fixed) {
-  (void)fixed;
-  if (dtype == STENCIL_F64 || dtype == kDtypeU64) return 1;
-  return 4;
-}
-
-// Largest compiled T not above `want` for this policy.
-int supported_t(int dtype, bool fixed, int want) {
-  if (dtype == kDtypeU64) return want >= 2 ? 2 : 1;
-  if (dtype == STENCIL_F64) return 1;
-  (void)fixed;
-  return want >= 4 ? 4 : (want >= 2 ? 2 : 1);
-}
-
 template <class T>
 int copy_halo(const Grid& src, const Grid& dst, cudaStream_t st) {
   const int64_t total = 2 * (src.nx + 2) * (src.ny + 2) + 2 * (src.nx + 2) * src.nz + 2 * src.ny * src.nz;
@@ -276,16 +171,56 @@ int copy_interior_any(const Grid& src, const Grid& dst, cudaStream_t st) {
   return copy_interior<unsigned short>(src, dst, st);
 }
 
+int policy_of(int dtype, bool fixed, bool resident) {
+  if (dtype == STENCIL_F64) return resident ? kPolResident : (fixed ? kPolFixed : kPolF64);
+  return dtype == STENCIL_F32 ? kPolF32 : kPolBF16;
+}
+
+// Largest pass length with compiled configurations, not above `want`.
+int supported_t(int policy, int want) {
+  for (int T = std::min(want, kMaxPass); T > 1; --T) {
+    const SweepVariant* v;
+    if (sweep_variants(policy, T, &v) > 0) return T;
+  }
+  return 1;
+}
+
+int run_pass(stencil_ctx* ctx, int policy, int T, const Grid& in, const Grid& out, const Grid& f,
+             const SweepArgs& a, cudaStream_t st) {
+  const SweepVariant* vs;
+  const int nv = sweep_variants(policy, T, &vs);
+  if (nv < 1) return set_error(STENCIL_ERR_ARG, "no compiled sweep configuration for T=%d", T);
+  int c = ctx->sweep_choice[policy][T];
+  if (c < 0 || c >= nv) c = 0;
+  return vs[c].fn(ctx, in, out, f, a, st);
+}
+
 }  // namespace
 
-int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
-                  double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
-  if (nsweeps == 0) return STENCIL_OK;
+int sweep_variants(int policy, int T, const SweepVariant** out) {
+  if (policy == kPolF32) return sweep_variants_f32(T, out);
+  if (policy == kPolBF16) return sweep_variants_bf16(T, out);
+  return sweep_variants_f64(policy, T, out);
+}
+
+namespace {
+
+// Per-call set-up shared by the sweep and its autotuner: u_tmp's halo, the
+// fixed-point range, and (resident) the packed iterate and source.
+struct Prepared {
+  int policy;
+  Grid ui, ti, fi;
+  SweepArgs a;
+};
+
+int prepare(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,
+            int64_t nsweeps, int flags, bool pack, cudaStream_t st, Prepared* P) {
   const bool fixed = (u.dtype == STENCIL_F64) && (flags != STENCIL_SWEEP_FP64_NATIVE);
   const bool resident = fixed && work != nullptr && nsweeps >= kResidentMinSweeps;
+  P->policy = policy_of(u.dtype, fixed, resident);
   int rc = copy_halo_any(u, ut, st);
   if (rc) return rc;
-  SweepArgs a;
+  SweepArgs& a = P->a;
   a.hh = h * h;
   a.nsw = static_cast<double>(nsweeps);
   a.lmin = static_cast<double>(std::min(std::min(u.nx, u.ny), u.nz) + 1) * h;
@@ -302,39 +237,115 @@ int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f
     rc = check_cuda(cudaGetLastError(), "range kernel");
     if (rc) return rc;
   }
-  const int64_t rows = u.ny * u.nz;
-  const int cblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 16 * ctx->num_sms));
-  Grid ui = u, ti = ut, fi = f;
+  P->ui = u;
+  P->ti = ut;
+  P->fi = f;
   if (resident) {
-    fx_pack_kernel<<<cblocks, dim3(32, 8), 0, st>>>(
-        static_cast<double*>(u.data), static_cast<const double*>(f.data),
-        static_cast<unsigned long long*>(work->data), u.nx, u.ny, u.nz, u.sy, u.sz, f.sy, f.sz,
-        work->sy, work->sz, a);
-    rc = check_cuda(cudaGetLastError(), "pack kernel");
-    if (rc) return rc;
-    ui.dtype = ti.dtype = kDtypeU64;
-    fi = *work;
-    fi.dtype = kDtypeU64;
+    if (pack) {
+      const int64_t rows = u.ny * u.nz;
+      const int cblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 16 * ctx->num_sms));
+      fx_pack_kernel<<<cblocks, dim3(32, 8), 0, st>>>(
+          static_cast<double*>(u.data), static_cast<const double*>(f.data),
+          static_cast<unsigned long long*>(work->data), u.nx, u.ny, u.nz, u.sy, u.sz, f.sy, f.sz, work->sy,
+          work->sz, a);
+      rc = check_cuda(cudaGetLastError(), "pack kernel");
+      if (rc) return rc;
+    }
+    P->ui.dtype = P->ti.dtype = kDtypeU64;
+    P->fi = *work;
+    P->fi.dtype = kDtypeU64;
   }
-  const int want = spp > 0 ? spp : default_spp(resident ? kDtypeU64 : u.dtype, fixed);
-  const Grid* a_in = &ui;
-  const Grid* b_out = &ti;
+  return STENCIL_OK;
+}
+
+}  // namespace
+
+int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
+                  double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
+  if (nsweeps == 0) return STENCIL_OK;
+  Prepared P;
+  int rc = prepare(ctx, u, ut, f, work, h, nsweeps, flags, true, st, &P);
+  if (rc) return rc;
+  const int want = spp > 0 ? spp : ctx->best_pass[P.policy];
+  const Grid* a_in = &P.ui;
+  const Grid* b_out = &P.ti;
   int64_t left = nsweeps;
   while (left > 0) {
-    const int T = supported_t(ui.dtype, fixed, static_cast<int>(std::min<int64_t>(left, want)));
-    rc = run_pass(ctx, ui.dtype, fixed, T, *a_in, *b_out, fi, a, st);
+    const int T = supported_t(P.policy, static_cast<int>(std::min<int64_t>(left, want)));
+    rc = run_pass(ctx, P.policy, T, *a_in, *b_out, P.fi, P.a, st);
     if (rc) return rc;
     std::swap(a_in, b_out);
     left -= T;
   }
-  if (resident) {
+  if (P.policy == kPolResident) {
+    const int64_t rows = u.ny * u.nz;
+    const int cblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 16 * ctx->num_sms));
     fx_unpack_kernel<<<cblocks, dim3(32, 8), 0, st>>>(
         static_cast<const unsigned long long*>(a_in->data), static_cast<double*>(u.data), u.nx, u.ny,
-        u.nz, a_in->sy, a_in->sz, u.sy, u.sz, a);
+        u.nz, a_in->sy, a_in->sz, u.sy, u.sz, P.a);
     return check_cuda(cudaGetLastError(), "unpack kernel");
   }
-  if (a_in != &ui) rc = copy_interior_any(*a_in, u, st);
+  if (a_in != &P.ui) rc = copy_interior_any(*a_in, u, st);
   return rc;
+}
+
+int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,
+                   int flags, char* report, size_t report_len, cudaStream_t st) {
+  // Trial passes read u and write u_tmp only (u's contents are never
+  // changed; the resident policy's trials read u's binary64 interior as if
+  // it were packed, which costs the same).
+  Prepared P;
+  int rc = prepare(ctx, u, ut, f, work, h, 1000, flags, false, st, &P);
+  if (rc) return rc;
+  std::string rep;
+  char line[256];
+  cudaEvent_t e0, e1;
+  rc = check_cuda(cudaEventCreate(&e0), "event");
+  if (!rc) rc = check_cuda(cudaEventCreate(&e1), "event");
+  if (rc) return rc;
+  double best_rate = 1e300;
+  int best_T = 1;
+  for (int T = 1; T <= kMaxPass && !rc; ++T) {
+    const SweepVariant* vs;
+    const int nv = sweep_variants(P.policy, T, &vs);
+    if (nv < 1) continue;
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int c = 0; c < nv && !rc; ++c) {
+      const int reps = 4;
+      rc = vs[c].fn(ctx, P.ui, P.ti, P.fi, P.a, st);  // warm-up
+      if (!rc) rc = check_cuda(cudaEventRecord(e0, st), "event record");
+      for (int r = 0; r < reps && !rc; ++r) rc = vs[c].fn(ctx, P.ui, P.ti, P.fi, P.a, st);
+      if (!rc) rc = check_cuda(cudaEventRecord(e1, st), "event record");
+      if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "event sync");
+      float ms = 0.0f;
+      if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+      const float per_sweep = ms / (reps * T);
+      snprintf(line, sizeof(line), "policy %d T=%d R=%d WY=%d S=%d minb=%d: %.4f ms/sweep\n", P.policy, T,
+               vs[c].R, vs[c].WY, vs[c].S, vs[c].minb, per_sweep);
+      rep += line;
+      if (per_sweep < best_ms) {
+        best_ms = per_sweep;
+        best = c;
+      }
+    }
+    ctx->sweep_choice[P.policy][T] = best;
+    if (best_ms < best_rate) {
+      best_rate = best_ms;
+      best_T = T;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  ctx->best_pass[P.policy] = best_T;
+  snprintf(line, sizeof(line), "chosen: T=%d\n", best_T);
+  rep += line;
+  if (report && report_len > 0) {
+    strncpy(report, rep.c_str(), report_len - 1);
+    report[report_len - 1] = 0;
+  }
+  return STENCIL_OK;
 }
 
 }  // namespace stencil

@@ -1,0 +1,30 @@
+// sweep_f64.cu -- compiled configurations of the sweep kernel for binary64
+// storage: fixed point resident for the call, fixed point per pass, and
+// binary64 arithmetic.  TbCfg<policy, T, R, WY, S, CTAs per SM>.
+#include "sweep_launch.cuh"
+
+namespace stencil {
+
+int sweep_variants_f64(int policy, int T, const SweepVariant** out) {
+  static const SweepVariant res1[] = {
+      variant<PolResident, TbCfg<PolResident, 1, 8, 4, 4, 3>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 4, 8, 5, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 8, 4, 6, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 4, 4, 6, 4>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 8, 8, 4, 1>>(),
+  };
+  static const SweepVariant res2[] = {
+      variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 2, 2, 4, 6, 3>>(),
+  };
+  static const SweepVariant fix1[] = {variant<PolFixed, TbCfg<PolFixed, 1, 8, 4, 4, 3>>()};
+  static const SweepVariant f641[] = {variant<PolF64, TbCfg<PolF64, 1, 8, 4, 4, 3>>()};
+  if (policy == kPolResident && T == 1) { *out = res1; return sizeof(res1) / sizeof(res1[0]); }
+  if (policy == kPolResident && T == 2) { *out = res2; return sizeof(res2) / sizeof(res2[0]); }
+  if (policy == kPolFixed && T == 1) { *out = fix1; return 1; }
+  if (policy == kPolF64 && T == 1) { *out = f641; return 1; }
+  *out = nullptr;
+  return 0;
+}
+
+}  // namespace stencil

@@ -70,6 +70,12 @@ SIGNATURES = {
     "stencil_advect_uvw": ([_P, _G, _G, _G, _G, _G, _G, _P, _P, ctypes.c_double, ctypes.c_double, _P],
                            ctypes.c_int),
     "stencil_residual_noalloc": ([_G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
+    "stencil_autotune_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int32, ctypes.c_char_p, ctypes.c_size_t,
+                                _P], ctypes.c_int),
+    "stencil_sweep_config_count": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "stencil_sweep_config_select": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32], ctypes.c_int),
     "wsnet_create": ([ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "wsnet_destroy": ([_P], ctypes.c_int),
@@ -203,6 +209,29 @@ def stencil_jacobi_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, 
                                              ctypes.byref(gw) if gw is not None else None,
                                              float(h), int(nsweeps), int(sweeps_per_pass), int(flags),
                                              _stream(stream)))
+
+
+def stencil_autotune_sweep(ctx, u, u_tmp, f, work, h, flags=SWEEP_AUTO, stream=None):
+    """Time every compiled sweep configuration on these grids and keep the
+    fastest in ctx (see include/stencil.h).  Returns the text report."""
+    gu, gt, gf = u.grid(), u_tmp.grid(), f.grid()
+    gw = work.grid() if work is not None else None
+    buf = ctypes.create_string_buffer(8192)
+    _check(lib().stencil_autotune_sweep(ctx.handle, ctypes.byref(gu), ctypes.byref(gt), ctypes.byref(gf),
+                                        ctypes.byref(gw) if gw is not None else None, float(h), int(flags),
+                                        buf, len(buf), _stream(stream)))
+    return buf.value.decode()
+
+
+def stencil_sweep_config_count(dtype, flags, with_work, T):
+    c = ctypes.c_int32()
+    _check(lib().stencil_sweep_config_count(int(dtype), int(flags), int(bool(with_work)), int(T), ctypes.byref(c)))
+    return c.value
+
+
+def stencil_sweep_config_select(ctx, dtype, flags, with_work, T, index):
+    return _check(lib().stencil_sweep_config_select(ctx.handle, int(dtype), int(flags), int(bool(with_work)),
+                                                    int(T), int(index)))
 
 
 def stencil_residual(ctx, u, f, h, norms_dev, r=None, stream=None):

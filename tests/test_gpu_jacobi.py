@@ -231,3 +231,57 @@ def test_argument_errors():
     rc = S.lib().stencil_jacobi_sweep(ctx().handle, ctypes.byref(gu), ctypes.byref(g), ctypes.byref(gf),
                                       None, 0.1, 1, 0, 0, None)
     assert rc == -2
+
+
+CONFIG_CASES = [(S.F64, S.SWEEP_FP64_FIXED, True), (S.F64, S.SWEEP_FP64_FIXED, False),
+                (S.F64, S.SWEEP_FP64_NATIVE, False), (S.F32, 0, False), (S.BF16, 0, False)]
+
+
+@pytest.mark.parametrize("dtype,flags,with_work", CONFIG_CASES)
+def test_every_compiled_configuration(dtype, flags, with_work):
+    """Each compiled tile configuration (pinned with sweep_config_select) of
+    each pass length gives the oracle's sweeps on a ragged grid."""
+    u, f, h = rand_problem(70, 45, 23, seed=41)
+    n = 8
+    if dtype == S.F64:
+        ref = oracle.jacobi(u, f, h, n)
+        tol = FP64_TOL
+        u_in, f_in = u, f
+    elif dtype == S.F32:
+        u_in, f_in = u.astype(np.float32).astype(np.float64), f.astype(np.float32).astype(np.float64)
+        a = u.astype(np.float32)
+        for _ in range(n):
+            a = oracle.jacobi_sweep_f32(a, f.astype(np.float32), h)
+        ref, tol = a.astype(np.float64), FP32_TOL
+    else:
+        u_in = oracle.from_bf16(oracle.to_bf16(u.astype(np.float32))).astype(np.float64)
+        f_in = oracle.from_bf16(oracle.to_bf16(f.astype(np.float32))).astype(np.float64)
+        ref, tol = oracle.jacobi(u_in, f_in, h, n), None
+    c = S.Context(0)
+    for T in range(1, 9):
+        count = S.stencil_sweep_config_count(dtype, flags, with_work, T)
+        for idx in range(count):
+            S.stencil_sweep_config_select(c, dtype, flags, with_work, T, idx)
+            uf, ff = S.Field.from_numpy(u_in, dtype), S.Field.from_numpy(f_in, dtype)
+            w = S.Field(uf.nx, uf.ny, uf.nz) if with_work else None
+            S.stencil_jacobi_sweep(c, uf, uf.like(), ff, w, h, n, T, flags)
+            S.stencil_ctx_status(c)
+            got = uf.to_numpy()
+            t = tol if tol is not None else (-(-n // T)) * 2.0 ** -8
+            assert rel_err(got, ref) <= t, (T, idx)
+            assert halo_equal(got, u_in)
+    c.close()
+
+
+def test_autotune_then_parity():
+    u, f, h = rand_problem(90, 61, 33, seed=42)
+    c = S.Context(0)
+    uf, ff = S.Field.from_numpy(u), S.Field.from_numpy(f)
+    t, w = uf.like(), S.Field(uf.nx, uf.ny, uf.nz)
+    rep = S.stencil_autotune_sweep(c, uf, t, ff, w, h)
+    assert "chosen" in rep and "ms/sweep" in rep
+    assert np.array_equal(uf.to_numpy(), u)  # the tuner does not change u
+    S.stencil_jacobi_sweep(c, uf, t, ff, w, h, 12, 0, 0)
+    S.stencil_ctx_status(c)
+    assert rel_err(uf.to_numpy(), oracle.jacobi(u, f, h, 12)) <= FP64_TOL
+    c.close()
