@@ -239,7 +239,9 @@ def run_ours(args, rank, world, local_rank):
     u, ut, f = fields(S.F64)
 
     tune_reports = {}
-    if not args.no_tune:
+    if args.f64_config is not None:
+        S.stencil_sweep_config_select(ctx, S.F64, S.SWEEP_AUTO, True, 1, args.f64_config)
+    elif not args.no_tune:
         tune_reports["f64"] = S.stencil_autotune_sweep(ctx, u, ut, f, work, h)
     # The headline runs one sweep per pass: the HBM-bound configuration the
     # roofline refers to (the fused two-sweep pass is reported as a variant).
@@ -374,6 +376,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--f64-config", type=int, default=None,
+                    help="pin the headline's FP64 one-sweep configuration (index; profiling runs)")
     ap.add_argument("--grid", type=int, default=None, help="grid extent (profiling runs; default 512)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step (profiling runs; default 1000)")
     ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16"],

@@ -289,7 +289,9 @@ STENCIL_API int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* pro
  * 3x3x3 convolutions with ReLU per level, 2x2x2 average pooling between
  * encoder levels, nearest 2x upsampling between decoder levels whose first
  * convolution adds the encoder feature of the same level before its ReLU,
- * and a 1x1x1 output layer.  Input f / rms(f) over the interior; output
+ * a 1x1x1 output layer and a fixed separable [1,2,1]/4 smoothing filter
+ * (it all but removes the checkerboard mode, which Jacobi damps as slowly as
+ * the smoothest mode).  Input f / rms(f) over the interior; output
  * u0 = y * rms(f) / (3 pi^2) on the interior (the halo of u is untouched).
  * Activations and gradients are bfloat16, products accumulate in binary32 on
  * the tensor cores; parameters are binary32 (Adam).  Parameter vector layout
@@ -324,6 +326,14 @@ STENCIL_API int wsnet_infer(wsnet* net, const stencil_grid* f,
 STENCIL_API int wsnet_train_step(wsnet* net, const stencil_grid* f,
                                  const stencil_grid* u, int32_t count,
                                  float lr, double* loss, void* stream);
+/* 1: the 3x3x3 convolutions with at least 16 input and output channels on
+ * grids whose rows divide 128 voxels run on the tcgen05 tensor cores
+ * (accumulators in tensor memory); 0 (the default): every convolution uses
+ * the warp-level mma.sync kernel. */
+STENCIL_API int wsnet_use_tcgen05(wsnet* net, int32_t enable);
+/* Read and clear the net's device status: STENCIL_ERR_TIMEOUT if a bounded
+ * wait inside a kernel expired (synchronises `stream`). */
+STENCIL_API int wsnet_status(wsnet* net, void* stream);
 /* One forward and backward pass on a given normalised input x and target t
  * (DEVICE binary32 arrays of n^3 values, z slowest, x fastest); y (device,
  * nullable) receives the output, grads (host, nullable) the gradients, in

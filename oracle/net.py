@@ -7,7 +7,11 @@ the configuration "3D conv encoder-decoder, 4 levels, 16-32-64-64 channels,
     followed by ReLU; 2x2x2 average pooling between encoder levels; nearest
     2x upsampling between decoder levels, whose first convolution adds the
     encoder feature of the same level before its ReLU; a final 1x1x1
-    convolution to one channel, no activation;
+    convolution to one channel, no activation, followed by a fixed low-pass
+    filter: the separable [1, 2, 1]/4 average along each axis (zero outside),
+    which scales the sine mode k of an axis with n points by
+    cos^2(pi k / (2 (n + 1))) and so all but removes the checkerboard mode --
+    the mode plain Jacobi damps as slowly as the smoothest one;
   * no normalisation layers.
 Fields are channels-last arrays (D, H, W, C).  Weights of a 3x3x3 layer are
 (3, 3, 3, Cin, Cout) plus a bias (Cout,); the output layer is (Cin, 1).
@@ -65,6 +69,19 @@ def up2(x):
 def up2_bwd(g):
     D, H, W, C = g.shape
     return g.reshape(D // 2, 2, H // 2, 2, W // 2, 2, C).sum(axis=(1, 3, 5))
+
+
+def smooth121(y):
+    """Separable [1,2,1]/4 filter along each of the three axes, zero padding
+    (the filter is symmetric, so it is also its own adjoint)."""
+    for ax in range(3):
+        pad = [(0, 0)] * y.ndim
+        pad[ax] = (1, 1)
+        p = np.pad(y, pad)
+        n = y.shape[ax]
+        sl = lambda a, b: tuple(slice(a, b) if d == ax else slice(None) for d in range(y.ndim))  # noqa: E731
+        y = 0.25 * p[sl(0, n)] + 0.5 * p[sl(1, n + 1)] + 0.25 * p[sl(2, n + 2)]
+    return y
 
 
 def relu(x):
@@ -126,7 +143,7 @@ def forward(p, x, channels, act_round=None):
         b = rd(relu(conv3(a, p[f"dec{l}b.w"], p[f"dec{l}b.b"])))
         cache[f"dec{l}b.in"], cache[f"dec{l}b.out"] = a, b
         h = b
-    y = h @ p["out.w"] + p["out.b"]
+    y = smooth121(h @ p["out.w"] + p["out.b"])
     cache["out.in"] = h
     return y, cache
 
@@ -141,6 +158,7 @@ def backward(p, cache, gy, channels):
     """Analytic gradients of every parameter given dLoss/dy."""
     L = len(channels)
     grads = {}
+    gy = smooth121(gy)
     h = cache["out.in"]
     grads["out.w"] = np.tensordot(h, gy, axes=([0, 1, 2], [0, 1, 2]))
     grads["out.b"] = gy.sum(axis=(0, 1, 2))

@@ -105,6 +105,24 @@ int make_tensor_map(CUtensorMap* map, const Grid& g, int box_x, int box_y) {
   return STENCIL_OK;
 }
 
+int encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* ptr, const uint64_t* dims,
+                 const uint64_t* strides, const uint32_t* box, CUtensorMapSwizzle swz) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(STENCIL_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t d[5], st[4];
+  cuuint32_t b[5], e[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    e[i] = 1;
+    if (i + 1 < rank) st[i] = strides[i];
+  }
+  CUresult r = fn(map, dt, rank, ptr, d, st, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(STENCIL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return STENCIL_OK;
+}
+
 // Make ctx's device current for the duration of a call.
 struct DeviceGuard {
   int prev = -1;

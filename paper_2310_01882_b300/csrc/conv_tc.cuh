@@ -1,0 +1,238 @@
+// conv_tc.cuh -- 3x3x3 convolution as an implicit GEMM on the 5th-generation
+// tensor cores (tcgen05, sm_100 family): M = 128 output voxels, N = COUT,
+// K = 27 taps x CIN channels.
+//
+// One CTA (4 warps) computes 128 consecutive voxels x COUT channels:
+//   * warp 0 lane 0 streams, per tap, the A tile (the 128 voxels' neighbours
+//     at that tap, CIN channels each: one box of the channels-last activation
+//     tensor, zero-filled outside the grid) and the B tile (the tap's
+//     COUT x CIN weights) with TMA into a ring of S stages, 128/64/32-byte
+//     swizzled to match the MMA operand layout (K-major);
+//   * warp 1 lane 0 issues tcgen05.mma (M=128, N=COUT, K=16, BF16 in, FP32
+//     accumulate in tensor memory) for each 16-channel chunk of each tap and
+//     releases the stage with tcgen05.commit;
+//   * after the last tap all 4 warps read the accumulator rows (one voxel per
+//     thread) with tcgen05.ld and apply bias, skip, ReLU, and store bf16.
+// Every wait is bounded; on expiry the status is set, the kernel still waits
+// (bounded) for outstanding MMAs, frees its tensor memory and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace stencil {
+namespace net {
+
+template <int CIN>
+struct TcSwz {
+  static constexpr int ROW = CIN * 2;  // bytes per K-major row (one voxel or one output channel)
+  // smem descriptor layout codes: 6 = 32B, 4 = 64B, 2 = 128B swizzle
+  static constexpr uint64_t LAYOUT = ROW == 32 ? 6 : (ROW == 64 ? 4 : 2);
+  static constexpr int ATOM = 8 * ROW;  // bytes of one 8-row swizzle atom (the stride between row groups)
+};
+
+template <int CIN, int COUT, int S>
+struct TcCfg {
+  static constexpr int ABYTES = 128 * CIN * 2;
+  static constexpr int BBYTES = COUT * CIN * 2;
+  static constexpr int STAGE = ((ABYTES + BBYTES) + 1023) / 1024 * 1024;
+  static constexpr int SMEM = 1024 /*align*/ + S * STAGE + 256 /*barriers, tmem slot*/;
+  static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+};
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint64_t layout, uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1u) << 16;                          // leading byte offset (unused for these swizzles)
+  d |= static_cast<uint64_t>((sbo_bytes >> 4) & 0x3FFFu) << 32;  // stride byte offset: 8-row groups
+  d |= static_cast<uint64_t>(1u) << 46;                          // descriptor version
+  d |= layout << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+struct TcParams {
+  CUtensorMap tm_in;   // activations [D][H][W][CIN] as (CIN, W, H, D), box (CIN, W, HB, ZB)
+  CUtensorMap tm_w;    // weights [COUT][27*CIN] as (27*CIN, COUT), box (CIN, COUT)
+  const float* bias;
+  const __nv_bfloat16* skip;
+  __nv_bfloat16* out;
+  int D, H, W, HB, ZB;  // tile = ZB planes x HB rows x W voxels = 128
+  uint32_t* status;
+};
+
+template <int CIN, int COUT, int S, bool RELU, bool SKIP>
+__global__ void __launch_bounds__(128, 1) conv3_tc_kernel(const __grid_constant__ TcParams p) {
+  using Cfg = TcCfg<CIN, COUT, S>;
+  using Sw = TcSwz<CIN>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* ring = base;
+  unsigned char* tail = base + S * Cfg::STAGE;
+  const uint32_t bar_full = smem_addr(tail);
+  const uint32_t bar_empty = bar_full + 8 * S;
+  const uint32_t bar_acc = bar_empty + 8 * S;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(tail + 8 * (2 * S + 1));
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    mbar_init(bar_acc, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(const_cast<uint32_t*>(tmem_slot))),
+                 "r"(Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  // tile origin: 128 consecutive voxels = ZB planes x HB rows x W
+  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * 128;
+  const int z0 = static_cast<int>(v0 / (static_cast<int64_t>(p.H) * p.W));
+  const int y0 = static_cast<int>((v0 / p.W) % p.H);
+  constexpr int KC = CIN / 16;  // MMAs per tap
+  bool ok = true;
+  if (warp == 0 && lane == 0) {
+    // producer
+    prefetch_tensormap(&p.tm_in);
+    prefetch_tensormap(&p.tm_w);
+    int issued = 0;
+    for (int tap = 0; tap < 27; ++tap) {
+      const int s = tap % S;
+      const uint32_t par = (tap / S) & 1u;
+      if (!mbar_wait_bounded(bar_empty + 8 * s, par ^ 1u, p.status)) { ok = false; abort_flag = 1; break; }
+      const uint32_t a = smem_addr(ring + s * Cfg::STAGE);
+      mbar_arrive_expect_tx(bar_full + 8 * s, Cfg::ABYTES + Cfg::BBYTES);
+      tma_load_4d(a, &p.tm_in, 0, tap % 3 - 1, y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1, bar_full + 8 * s);
+      tma_load_2d(a + Cfg::ABYTES, &p.tm_w, tap * CIN, 0, bar_full + 8 * s);
+      issued = tap + 1;
+    }
+    // no copy may still be landing in shared memory when the CTA exits: wait
+    // (bounded) for the last load issued to every stage
+    for (int s = 0; s < S && s < issued; ++s) {
+      const int last = s + (issued - 1 - s) / S * S;
+      mbar_wait_bounded(bar_full + 8 * s, (last / S) & 1u, p.status);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = tc_idesc(128, COUT);
+    for (int tap = 0; tap < 27; ++tap) {
+      const int s = tap % S;
+      const uint32_t par = (tap / S) & 1u;
+      if (*reinterpret_cast<volatile int*>(&abort_flag) ||
+          !mbar_wait_bounded(bar_full + 8 * s, par, p.status)) {
+        ok = false;
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = smem_addr(ring + s * Cfg::STAGE);
+      const uint32_t b = a + Cfg::ABYTES;
+#pragma unroll
+      for (int kc = 0; kc < KC; ++kc) {
+        const uint64_t ad = tc_smem_desc(a + 32 * kc, Sw::LAYOUT, Sw::ATOM);
+        const uint64_t bd = tc_smem_desc(b + 32 * kc, Sw::LAYOUT, Sw::ATOM);
+        const uint32_t acc = (tap > 0 || kc > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       bar_empty + 8 * s)
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_acc)
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: every thread owns one accumulator row (one voxel)
+  const bool acc_ok = mbar_wait_bounded(bar_acc, 0, p.status);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // warp-uniform decision: tcgen05.ld is a warp-wide (.sync.aligned) load
+  if (__all_sync(0xffffffffu, acc_ok && !*reinterpret_cast<volatile int*>(&abort_flag))) {
+    const int row = warp * 32 + lane;
+    const int64_t v = v0 + row;
+    float vals[COUT];
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) vals[c0 + j] = __uint_as_float(r[j]);
+    }
+    uint32_t packed[COUT / 2];
+#pragma unroll
+    for (int c = 0; c < COUT; c += 2) {
+      float a0 = vals[c] + p.bias[c], a1 = vals[c + 1] + p.bias[c + 1];
+      if (SKIP) {
+        a0 += __bfloat162float(p.skip[v * COUT + c]);
+        a1 += __bfloat162float(p.skip[v * COUT + c + 1]);
+      }
+      if (RELU) {
+        a0 = fmaxf(a0, 0.0f);
+        a1 = fmaxf(a1, 0.0f);
+      }
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+      packed[c / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(p.out + v * COUT);
+#pragma unroll
+    for (int q = 0; q < COUT / 8; ++q)
+      dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+  }
+  // bar_acc completing means every issued MMA has finished; free the
+  // tensor memory once all warps are past their loads
+  (void)ok;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace net
+}  // namespace stencil

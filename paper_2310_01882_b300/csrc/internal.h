@@ -65,6 +65,9 @@ int same_extents(const Grid& a, const Grid& b, const char* an, const char* bn);
 
 // TMA descriptor of a 3D halo grid with box (bx, by, 1).
 int make_tensor_map(CUtensorMap* map, const Grid& g, int box_x, int box_y);
+// General tiled TMA descriptor (rank <= 5; strides in bytes for dims 1..).
+int encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* ptr, const uint64_t* dims,
+                 const uint64_t* strides, const uint32_t* box, CUtensorMapSwizzle swz);
 
 struct SweepArgs;
 using PassFn = int (*)(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, const SweepArgs& a,

@@ -7,7 +7,9 @@
 // Architecture (per-level channels C[0..L-1], L <= 4): per level two 3x3x3
 // convolutions with ReLU; 2x2x2 average pooling between encoder levels;
 // nearest 2x upsampling between decoder levels, whose first convolution adds
-// the encoder feature of the same level before its ReLU; a 1x1x1 output layer.
+// the encoder feature of the same level before its ReLU; a 1x1x1 output layer
+// and a fixed separable [1,2,1]/4 filter (it all but removes the checkerboard
+// mode, which plain Jacobi damps as slowly as the smoothest one).
 // Activations and gradients are bfloat16, channels-last [z][y][x][c]; weights
 // are kept in FP32 (Adam) and mirrored to bfloat16 in two layouts: W[co][k]
 // with k = tap*Cin + ci (forward) and Wt[ci][k'] with k' = (26-tap)*Cout + co
@@ -22,6 +24,7 @@
 
 #include <cuda_bf16.h>
 
+#include "conv_tc.cuh"
 #include "internal.h"
 
 namespace stencil {
@@ -339,19 +342,16 @@ __global__ void out_fwd_kernel(const bf16* __restrict__ h, const float* __restri
   }
 }
 
-// gy = 2 (y - t) / V, the loss partials per block, and g_h = gy * w (bf16).
-__global__ void mse_bwd_kernel(const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ w,
-                               float* __restrict__ gy, bf16* __restrict__ gh, float* __restrict__ loss_part,
-                               int64_t V, int C, int chunk) {
+// gy = 2 (y - t) / V and the loss partials per block.
+__global__ void mse_bwd_kernel(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ gy,
+                               float* __restrict__ loss_part, int64_t V, int chunk) {
   const int64_t v0 = static_cast<int64_t>(blockIdx.x) * chunk;
   const int64_t v1 = min(v0 + chunk, V);
   float s = 0.0f;
   for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
     const float d = y[v] - t[v];
     s = fmaf(d, d, s);
-    const float gv = 2.0f * d / static_cast<float>(V);
-    gy[v] = gv;
-    for (int c = 0; c < C; ++c) gh[v * C + c] = __float2bfloat16_rn(gv * w[c]);
+    gy[v] = 2.0f * d / static_cast<float>(V);
   }
   __shared__ float red[256];
   red[threadIdx.x] = s;
@@ -361,6 +361,41 @@ __global__ void mse_bwd_kernel(const float* __restrict__ y, const float* __restr
     __syncthreads();
   }
   if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// g_h[v][c] = gy[v] * w[c] (bf16): the gradient entering the last 3x3x3 layer.
+__global__ void out_bwd_kernel(const float* __restrict__ gy, const float* __restrict__ w, bf16* __restrict__ gh,
+                               int64_t V, int C) {
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x)
+    for (int c = 0; c < C; ++c) gh[v * C + c] = __float2bfloat16_rn(gy[v] * w[c]);
+}
+
+// The network's fixed last layer: the separable [1,2,1]/4 filter along each
+// axis of an n^3 FP32 field, zero outside (27 taps, weights (a b c)/64 with
+// a, b, c in {1, 2}).  Symmetric, so the backward pass applies it too.
+__global__ void smooth121_kernel(const float* __restrict__ in, float* __restrict__ out, int n) {
+  const int64_t V = static_cast<int64_t>(n) * n * n;
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V; v += int64_t(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n), z = static_cast<int>(v / (int64_t(n) * n));
+    float s = 0.0f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = z + dz;
+      if (zz < 0 || zz >= n) continue;
+      const float wz = dz == 0 ? 2.0f : 1.0f;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= n) continue;
+        const float wy = dy == 0 ? 2.0f : 1.0f;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = x + dx;
+          if (xx < 0 || xx >= n) continue;
+          const float wx = dx == 0 ? 2.0f : 1.0f;
+          s = fmaf(wz * wy * wx, in[(static_cast<int64_t>(zz) * n + yy) * n + xx], s);
+        }
+      }
+    }
+    out[v] = s * (1.0f / 64.0f);
+  }
 }
 
 // Output-layer weight gradients: part[b][c] = sum_{v in block} h[v][c] gy[v],
@@ -492,9 +527,67 @@ int blocks_for(int64_t n, int per = 256) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, 8192)));
 }
 
-int launch_conv(int cin, int cout, bool relu, bool skip, const bf16* in, const bf16* w, const float* bias,
-                const bf16* sk, bf16* out, int D, int H, int W, cudaStream_t st) {
+// tcgen05 path: 128-voxel tiles of whole rows (W divides 128, 128/W rows of
+// one plane), CIN and COUT in {16, 32, 64}.
+bool tc_eligible(int cin, int cout, int D, int H, int W) {
+  (void)D;
+  if (cin < 16 || cout < 16) return false;
+  if (W < 16 || W > 128 || 128 % W != 0) return false;
+  const int hb = 128 / W;
+  return H % hb == 0;
+}
+
+template <int CIN, int COUT>
+int launch_conv_tc(bool relu, bool skip, const bf16* in, const bf16* w, const float* bias, const bf16* sk, bf16* out,
+                   int D, int H, int W, uint32_t* status, cudaStream_t st) {
+  constexpr int S = 4;
+  using Cfg = TcCfg<CIN, COUT, S>;
+  TcParams p;
+  const CUtensorMapSwizzle swz = CIN == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                 : CIN == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_128B;
+  const uint64_t dims_in[4] = {static_cast<uint64_t>(CIN), static_cast<uint64_t>(W), static_cast<uint64_t>(H),
+                               static_cast<uint64_t>(D)};
+  const uint64_t str_in[3] = {static_cast<uint64_t>(CIN) * 2, static_cast<uint64_t>(W) * CIN * 2,
+                              static_cast<uint64_t>(H) * W * CIN * 2};
+  const uint32_t box_in[4] = {static_cast<uint32_t>(CIN), static_cast<uint32_t>(W), static_cast<uint32_t>(128 / W), 1};
+  int rc = encode_tiled(&p.tm_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims_in, str_in, box_in,
+                        swz);
+  if (rc) return rc;
+  const uint64_t dims_w[2] = {static_cast<uint64_t>(27 * CIN), static_cast<uint64_t>(COUT)};
+  const uint64_t str_w[1] = {static_cast<uint64_t>(kpad(CIN)) * 2};
+  const uint32_t box_w[2] = {static_cast<uint32_t>(CIN), static_cast<uint32_t>(COUT)};
+  rc = encode_tiled(&p.tm_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(w), dims_w, str_w, box_w, swz);
+  if (rc) return rc;
+  p.bias = bias;
+  p.skip = sk;
+  p.out = out;
+  p.D = D; p.H = H; p.W = W; p.HB = 128 / W; p.ZB = 1;
+  p.status = status;
   const int64_t V = static_cast<int64_t>(D) * H * W;
+  const int grid = static_cast<int>(V / 128);
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return check_cuda(e, "conv tc attribute");
+    kern<<<grid, 128, Cfg::SMEM, st>>>(p);
+    return check_cuda(cudaGetLastError(), "conv tc launch");
+  };
+  if (relu && skip) return go(conv3_tc_kernel<CIN, COUT, S, true, true>);
+  if (relu) return go(conv3_tc_kernel<CIN, COUT, S, true, false>);
+  return go(conv3_tc_kernel<CIN, COUT, S, false, false>);
+}
+
+// tc_status: device status word of the tcgen05 path's bounded waits, or null
+// to use the mma.sync kernel for every layer.
+int launch_conv(int cin, int cout, bool relu, bool skip, const bf16* in, const bf16* w, const float* bias,
+                const bf16* sk, bf16* out, int D, int H, int W, uint32_t* tc_status, cudaStream_t st) {
+  const int64_t V = static_cast<int64_t>(D) * H * W;
+  if (tc_status && tc_eligible(cin, cout, D, H, W)) {
+#define X(CI, CO) \
+    if (cin == CI && cout == CO) return launch_conv_tc<CI, CO>(relu, skip, in, w, bias, sk, out, D, H, W, tc_status, st);
+    X(16, 16) X(16, 32) X(16, 64) X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64)
+#undef X
+  }
   const int grid = static_cast<int>((V + 63) / 64);
 #define X(CI, CO)                                                                                           \
   if (cin == CI && cout == CO) {                                                                           \
@@ -578,8 +671,10 @@ struct wsnet {
   int64_t V[stencil::net::kMaxLevels];
   int dim[stencil::net::kMaxLevels];
   stencil::net::bf16 *x0, *a[4], *b[4], *pl[4], *u[4], *da[4], *db[4], *gA[4], *gB[4], *gs[4];
-  float *y, *t, *gy, *part, *misc;
+  float *y, *yraw, *t, *gy, *gyf, *part, *misc;
   double *rms_part, *rms;
+  uint32_t* status;  // device status word (bounded waits of the tensor-core kernels)
+  int use_tc;        // 1: tcgen05 convolutions where eligible, 0: mma.sync everywhere
   int64_t part_elems;
   int step;
   std::vector<void*> allocs;
@@ -626,10 +721,11 @@ int forward(wsnet* w, cudaStream_t st) {
       in = w->pl[l];
     }
     const Layer& la = w->layers[li++];
-    int rc = launch_conv(la.cin, la.cout, true, false, in, la.wf, w->p + la.boff, nullptr, w->a[l], d, d, d, st);
+    uint32_t* tcs = w->use_tc ? w->status : nullptr;
+    int rc = launch_conv(la.cin, la.cout, true, false, in, la.wf, w->p + la.boff, nullptr, w->a[l], d, d, d, tcs, st);
     if (rc) return rc;
     const Layer& lb = w->layers[li++];
-    rc = launch_conv(lb.cin, lb.cout, true, false, w->a[l], lb.wf, w->p + lb.boff, nullptr, w->b[l], d, d, d, st);
+    rc = launch_conv(lb.cin, lb.cout, true, false, w->a[l], lb.wf, w->p + lb.boff, nullptr, w->b[l], d, d, d, tcs, st);
     if (rc) return rc;
   }
   const bf16* h = w->b[L - 1];
@@ -637,15 +733,20 @@ int forward(wsnet* w, cudaStream_t st) {
     const int d = w->dim[l];
     up2_kernel<<<blocks_for(w->V[l] * w->C[l + 1]), 256, 0, st>>>(h, w->u[l], d, d, d, w->C[l + 1]);
     const Layer& la = w->layers[li++];
-    int rc = launch_conv(la.cin, la.cout, true, true, w->u[l], la.wf, w->p + la.boff, w->b[l], w->da[l], d, d, d, st);
+    uint32_t* tcs = w->use_tc ? w->status : nullptr;
+    int rc = launch_conv(la.cin, la.cout, true, true, w->u[l], la.wf, w->p + la.boff, w->b[l], w->da[l], d, d, d, tcs,
+                         st);
     if (rc) return rc;
     const Layer& lb = w->layers[li++];
-    rc = launch_conv(lb.cin, lb.cout, true, false, w->da[l], lb.wf, w->p + lb.boff, nullptr, w->db[l], d, d, d, st);
+    rc = launch_conv(lb.cin, lb.cout, true, false, w->da[l], lb.wf, w->p + lb.boff, nullptr, w->db[l], d, d, d, tcs,
+                     st);
     if (rc) return rc;
     h = w->db[l];
   }
   const bf16* last = L > 1 ? w->db[0] : w->b[0];
-  out_fwd_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(last, w->p + w->out_w, w->p + w->out_b, w->y, w->V[0], w->C[0]);
+  out_fwd_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(last, w->p + w->out_w, w->p + w->out_b, w->yraw, w->V[0],
+                                                       w->C[0]);
+  smooth121_kernel<<<blocks_for(w->V[0]), 256, 0, st>>>(w->yraw, w->y, w->n);
   return check_cuda(cudaGetLastError(), "wsnet forward");
 }
 
@@ -665,7 +766,9 @@ int conv_backward(wsnet* w, const Layer& ly, const bf16* in, const bf16* g, bf16
   const int64_t V = static_cast<int64_t>(d) * d * d;
   int rc = launch_wgrad(ly.cin, ly.cout, in, g, w->part, w->g + ly.woff, d, d, d, st);
   if (!rc) rc = bias_grad(w, g, V, ly.cout, w->g + ly.boff, st);
-  if (!rc && gin) rc = launch_conv(ly.cout, ly.cin, false, false, g, ly.wt, w->zero_bias, nullptr, gin, d, d, d, st);
+  if (!rc && gin)
+    rc = launch_conv(ly.cout, ly.cin, false, false, g, ly.wt, w->zero_bias, nullptr, gin, d, d, d,
+                     w->use_tc ? w->status : nullptr, st);
   return rc;
 }
 
@@ -674,11 +777,12 @@ int backward(wsnet* w, cudaStream_t st) {
   const int64_t V0 = w->V[0];
   const bf16* last = L > 1 ? w->db[0] : w->b[0];
   const int lblocks = static_cast<int>((V0 + kLossChunk - 1) / kLossChunk);
-  mse_bwd_kernel<<<lblocks, 256, 0, st>>>(w->y, w->t, w->p + w->out_w, w->gy, w->gA[0], w->misc, V0, w->C[0],
-                                          kLossChunk);
+  mse_bwd_kernel<<<lblocks, 256, 0, st>>>(w->y, w->t, w->gy, w->misc, V0, kLossChunk);
+  smooth121_kernel<<<blocks_for(V0), 256, 0, st>>>(w->gy, w->gyf, w->n);
+  out_bwd_kernel<<<blocks_for(V0), 256, 0, st>>>(w->gyf, w->p + w->out_w, w->gA[0], V0, w->C[0]);
   const int ochunk = 4096;
   const int oblocks = static_cast<int>((V0 + ochunk - 1) / ochunk);
-  out_wgrad_kernel<<<oblocks, 64, 0, st>>>(last, w->gy, w->part, V0, w->C[0], ochunk);
+  out_wgrad_kernel<<<oblocks, 64, 0, st>>>(last, w->gyf, w->part, V0, w->C[0], ochunk);
   chan_sum_reduce_kernel<<<1, 64, 0, st>>>(w->part, w->g + w->out_w, w->C[0] + 1, oblocks);
   int rc = check_cuda(cudaGetLastError(), "output layer backward");
   if (rc) return rc;
@@ -828,11 +932,15 @@ extern "C" int wsnet_create(int device, int32_t levels, const int32_t* channels,
   w->part_elems = part;
   A(&w->part, static_cast<size_t>(part));
   A(&w->y, static_cast<size_t>(w->V[0]));
+  A(&w->yraw, static_cast<size_t>(w->V[0]));
+  A(&w->gyf, static_cast<size_t>(w->V[0]));
   A(&w->t, static_cast<size_t>(w->V[0]));
   A(&w->gy, static_cast<size_t>(w->V[0]));
   A(&w->misc, static_cast<size_t>(w->V[0] / kLossChunk + 16));
   A(&w->rms_part, 256);
   A(&w->rms, 4);
+  A(&w->status, 4);
+  w->use_tc = 0;
   if (rc) {
     wsnet_destroy(w);
     return rc;
@@ -985,5 +1093,28 @@ extern "C" int wsnet_loss_grad(wsnet* w, const float* x, const float* t, float* 
   double sl = 0.0;
   for (float v : lp) sl += v;
   if (loss) *loss = sl / static_cast<double>(w->V[0]);
+  return STENCIL_OK;
+}
+
+// Choose the convolution kernels: 1 = tcgen05 for eligible layers,
+// 0 (default) = mma.sync for every layer.
+extern "C" int wsnet_use_tcgen05(wsnet* w, int32_t enable) {
+  if (!w) return set_error(STENCIL_ERR_ARG, "wsnet_use_tcgen05: null net");
+  w->use_tc = enable ? 1 : 0;
+  return STENCIL_OK;
+}
+
+// Read and clear the net's device status (bounded waits of its kernels).
+extern "C" int wsnet_status(wsnet* w, void* stream) {
+  if (!w) return set_error(STENCIL_ERR_ARG, "wsnet_status: null net");
+  DevGuard dg(w->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t bits = 0;
+  int rc = check_cuda(cudaMemcpyAsync(&bits, w->status, 4, cudaMemcpyDeviceToHost, st), "status read");
+  if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "sync");
+  if (!rc) rc = check_cuda(cudaMemsetAsync(w->status, 0, 4, st), "status clear");
+  if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "sync");
+  if (rc) return rc;
+  if (bits & kStatusTimeout) return set_error(STENCIL_ERR_TIMEOUT, "a bounded device wait expired");
   return STENCIL_OK;
 }

@@ -85,6 +85,8 @@ SIGNATURES = {
     "wsnet_infer": ([_P, _G, _G, _P], ctypes.c_int),
     "wsnet_train_step": ([_P, _G, _G, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_double), _P],
                          ctypes.c_int),
+    "wsnet_use_tcgen05": ([_P, ctypes.c_int32], ctypes.c_int),
+    "wsnet_status": ([_P, _P], ctypes.c_int),
     "wsnet_loss_grad": ([_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "stencil_batch_workspace_size": ([ctypes.POINTER(stencil_problem), ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
@@ -330,6 +332,14 @@ class WsNet:
             self.close()
         except Exception:
             pass
+
+
+def wsnet_use_tcgen05(net, enable):
+    return _check(lib().wsnet_use_tcgen05(net.handle, int(bool(enable))))
+
+
+def wsnet_status(net, stream=None):
+    return _check(lib().wsnet_status(net.handle, _stream(stream)))
 
 
 def wsnet_infer(net, f, u, stream=None):

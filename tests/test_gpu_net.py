@@ -56,10 +56,14 @@ def from_oracle_grads(g, channels):
     return np.concatenate(parts)
 
 
-@pytest.mark.parametrize("levels,channels,n", [(2, [16, 32], 16), (3, [16, 32, 64], 16)])
-def test_forward_backward_match_oracle(levels, channels, n):
+@pytest.mark.parametrize("levels,channels,n,tc", [(2, [16, 32], 16, 1), (3, [16, 32, 64], 16, 1),
+                                                   (3, [16, 32, 64], 32, 1), (3, [16, 32, 64], 32, 0)])
+def test_forward_backward_match_oracle(levels, channels, n, tc):
+    """tc = 1: the tcgen05 convolutions run wherever they apply (rows of 16
+    to 128 voxels: levels 0 and 1 at n = 32); tc = 0: mma.sync everywhere."""
     import torch
     net = S.WsNet(levels, channels, n, seed=3)
+    S.wsnet_use_tcgen05(net, tc)
     flat = net.get_params()
     rng = np.random.default_rng(7)
     # nonzero biases so every bias path is exercised
@@ -94,6 +98,31 @@ def test_forward_backward_match_oracle(levels, channels, n):
             off += size
     a, b = grads[off:], g_ref[off:]
     assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 3e-2
+    S.wsnet_status(net)
+    net.close()
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_tcgen05_matches_mma_sync(n):
+    """The two convolution paths agree on the same net and data (both are
+    bf16 products with FP32 sums; only the summation order differs)."""
+    import torch
+    ch = [16, 32, 64, 64]
+    net = S.WsNet(4, ch, n, seed=11)
+    rng = np.random.default_rng(12)
+    x = torch.from_numpy(rng.standard_normal((n, n, n)).astype(np.float32)).cuda()
+    t = torch.from_numpy((rng.standard_normal((n, n, n)) * 0.3).astype(np.float32)).cuda()
+    out = []
+    for tc in (0, 1):
+        S.wsnet_use_tcgen05(net, tc)
+        y = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+        loss, g = S.wsnet_loss_grad(net, x, t, y)
+        S.wsnet_status(net)
+        out.append((loss, g, y.cpu().numpy()))
+    (l0, g0, y0), (l1, g1, y1) = out
+    assert np.max(np.abs(y0 - y1)) <= 1e-2 * np.max(np.abs(y0))
+    assert abs(l0 - l1) <= 1e-2 * l0
+    assert np.max(np.abs(g0 - g1)) <= 3e-2 * np.max(np.abs(g0))
     net.close()
 
 

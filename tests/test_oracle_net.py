@@ -53,6 +53,9 @@ def test_adjoint_identities():
     assert abs(np.sum(net.pool2(x) * y) - np.sum(x * net.pool2_bwd(y))) <= 1e-12
     z = rng.standard_normal((8, 12, 16, 3))
     assert abs(np.sum(net.up2(x) * z) - np.sum(x * net.up2_bwd(z))) <= 1e-11
+    a = rng.standard_normal((5, 6, 7, 1))
+    b = rng.standard_normal((5, 6, 7, 1))
+    assert abs(np.sum(net.smooth121(a) * b) - np.sum(a * net.smooth121(b))) <= 1e-12
     W = rng.standard_normal((3, 3, 3, 3, 5))
     g = rng.standard_normal((4, 6, 8, 5))
     out = net.conv3(x, W, np.zeros(5))
@@ -61,6 +64,20 @@ def test_adjoint_identities():
     assert abs(ip - np.sum(x * dx)) <= 1e-10 * abs(ip)
     assert abs(ip - np.sum(W * dW)) <= 1e-10 * abs(ip)
     np.testing.assert_allclose(db, g.sum(axis=(0, 1, 2)))
+
+
+def test_smoothing_filter_modes():
+    """On sine modes sin(pi k i/(n+1)) (zero outside) the [1,2,1]/4 filter is
+    diagonal with factor cos^2(pi k/(2(n+1))) per axis: the checkerboard
+    mode k = n is multiplied by cos^2(pi n/(2(n+1))) ~ 1e-2 per axis and
+    the smoothest mode by nearly 1."""
+    n = 12
+    i = np.arange(1, n + 1)
+    for k in (1, 5, n):
+        s = np.sin(np.pi * k * i / (n + 1))
+        mode = s[:, None, None] * s[None, :, None] * s[None, None, :]
+        fac = np.cos(np.pi * k / (2 * (n + 1))) ** 6
+        np.testing.assert_allclose(net.smooth121(mode[..., None])[..., 0], fac * mode, atol=1e-14)
 
 
 @pytest.mark.parametrize("channels", [[4, 6], [3, 4, 5]])
