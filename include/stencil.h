@@ -326,10 +326,12 @@ STENCIL_API int wsnet_infer(wsnet* net, const stencil_grid* f,
 STENCIL_API int wsnet_train_step(wsnet* net, const stencil_grid* f,
                                  const stencil_grid* u, int32_t count,
                                  float lr, double* loss, void* stream);
-/* 1: the 3x3x3 convolutions with at least 16 input and output channels on
- * grids whose rows divide 128 voxels run on the tcgen05 tensor cores
- * (accumulators in tensor memory); 0 (the default): every convolution uses
- * the warp-level mma.sync kernel. */
+/* 1 (the default): the 3x3x3 convolutions with at least 16 input and output
+ * channels on grids whose rows of 16 to 128 voxels divide 128 run on the
+ * tcgen05 tensor cores (accumulators in tensor memory); 0: every
+ * convolution uses the warp-level mma.sync kernel.  Both paths sum the
+ * bf16 products in binary32 in the same order (taps, then 16-channel
+ * chunks). */
 STENCIL_API int wsnet_use_tcgen05(wsnet* net, int32_t enable);
 /* Read and clear the net's device status: STENCIL_ERR_TIMEOUT if a bounded
  * wait inside a kernel expired (synchronises `stream`). */

@@ -245,16 +245,51 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, float* __res
   }
 }
 
-// Per-channel sums over voxels (bias gradients): part[b][c] for blocks of
-// `chunk` voxels, then db[c] += sum over blocks in order.
-template <class T>
-__global__ void chan_sum_kernel(const T* __restrict__ x, float* __restrict__ part, int64_t V, int C, int chunk) {
-  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * chunk;
-  const int64_t v1 = min(v0 + chunk, V);
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    float s = 0.0f;
-    for (int64_t v = v0; v < v1; ++v) s += static_cast<float>(x[v * C + c]);
-    part[static_cast<int64_t>(blockIdx.x) * C + c] = s;
+// Per-channel sums over voxels of a channels-last bf16 tensor, for the bias
+// gradients (GY = false: part[b][c] = sum_v x[v][c]) and the output layer's
+// weight gradient (GY = true: part[b][c] = sum_v x[v][c] gy[v] for c < C and
+// part[b][C] = sum_v gy[v]).  Block b covers voxels [b, b+1) * kSumChunk;
+// its 256 threads are (voxel lane, channel pair), so one pass of the block
+// reads 256 consecutive bf16 pairs; the lanes are then added in lane order
+// (deterministic).  db[c] += sum over blocks in order (chan_sum_reduce).
+constexpr int kSumChunk = 2048;
+
+template <int C, bool GY>
+__global__ void __launch_bounds__(256)
+    chan_sum_kernel(const bf16* __restrict__ x, const float* __restrict__ gy, float* __restrict__ part, int64_t V) {
+  constexpr int P = C / 2, LANES = 256 / P, OUT = GY ? C + 1 : C;
+  __shared__ float red[3][256];
+  const int cp = threadIdx.x % P, vl = threadIdx.x / P;
+  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * kSumChunk;
+  const int64_t v1 = min(v0 + kSumChunk, V);
+  float s0 = 0.0f, s1 = 0.0f, sg = 0.0f;
+  for (int64_t v = v0 + vl; v < v1; v += LANES) {
+    const __nv_bfloat162 b = reinterpret_cast<const __nv_bfloat162*>(x + v * C)[cp];
+    if (GY) {
+      const float g = gy[v];
+      s0 += __low2float(b) * g;
+      s1 += __high2float(b) * g;
+      sg += g;
+    } else {
+      s0 += __low2float(b);
+      s1 += __high2float(b);
+    }
+  }
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = s1;
+  red[2][threadIdx.x] = sg;
+  __syncthreads();
+  if (threadIdx.x < P) {
+    float t0 = 0.0f, t1 = 0.0f, tg = 0.0f;
+    for (int l = 0; l < LANES; ++l) {
+      t0 += red[0][l * P + threadIdx.x];
+      t1 += red[1][l * P + threadIdx.x];
+      tg += red[2][l * P + threadIdx.x];
+    }
+    float* o = part + static_cast<int64_t>(blockIdx.x) * OUT;
+    o[2 * threadIdx.x] = t0;
+    o[2 * threadIdx.x + 1] = t1;
+    if (GY && threadIdx.x == 0) o[C] = tg;
   }
 }
 
@@ -395,19 +430,6 @@ __global__ void smooth121_kernel(const float* __restrict__ in, float* __restrict
       }
     }
     out[v] = s * (1.0f / 64.0f);
-  }
-}
-
-// Output-layer weight gradients: part[b][c] = sum_{v in block} h[v][c] gy[v],
-// part[b][C] = sum gy.
-__global__ void out_wgrad_kernel(const bf16* __restrict__ h, const float* __restrict__ gy, float* __restrict__ part,
-                                 int64_t V, int C, int chunk) {
-  const int64_t v0 = static_cast<int64_t>(blockIdx.x) * chunk;
-  const int64_t v1 = min(v0 + chunk, V);
-  for (int c = threadIdx.x; c <= C; c += blockDim.x) {
-    float s = 0.0f;
-    for (int64_t v = v0; v < v1; ++v) s += c < C ? __bfloat162float(h[v * C + c]) * gy[v] : gy[v];
-    part[static_cast<int64_t>(blockIdx.x) * (C + 1) + c] = s;
   }
 }
 
@@ -755,9 +777,11 @@ int forward(wsnet* w, cudaStream_t st) {
 constexpr int kLossChunk = 16384;
 
 int bias_grad(wsnet* w, const bf16* g, int64_t V, int C, float* db, cudaStream_t st) {
-  const int chunk = 4096;
-  const int blocks = static_cast<int>((V + chunk - 1) / chunk);
-  chan_sum_kernel<bf16><<<blocks, 64, 0, st>>>(g, w->part, V, C, chunk);
+  const int blocks = static_cast<int>((V + kSumChunk - 1) / kSumChunk);
+  if (C == 16) chan_sum_kernel<16, false><<<blocks, 256, 0, st>>>(g, nullptr, w->part, V);
+  else if (C == 32) chan_sum_kernel<32, false><<<blocks, 256, 0, st>>>(g, nullptr, w->part, V);
+  else if (C == 64) chan_sum_kernel<64, false><<<blocks, 256, 0, st>>>(g, nullptr, w->part, V);
+  else return set_error(STENCIL_ERR_ARG, "wsnet: no bias-gradient kernel for %d channels", C);
   chan_sum_reduce_kernel<<<1, 64, 0, st>>>(w->part, db, C, blocks);
   return check_cuda(cudaGetLastError(), "bias grad");
 }
@@ -780,10 +804,12 @@ int backward(wsnet* w, cudaStream_t st) {
   mse_bwd_kernel<<<lblocks, 256, 0, st>>>(w->y, w->t, w->gy, w->misc, V0, kLossChunk);
   smooth121_kernel<<<blocks_for(V0), 256, 0, st>>>(w->gy, w->gyf, w->n);
   out_bwd_kernel<<<blocks_for(V0), 256, 0, st>>>(w->gyf, w->p + w->out_w, w->gA[0], V0, w->C[0]);
-  const int ochunk = 4096;
-  const int oblocks = static_cast<int>((V0 + ochunk - 1) / ochunk);
-  out_wgrad_kernel<<<oblocks, 64, 0, st>>>(last, w->gyf, w->part, V0, w->C[0], ochunk);
-  chan_sum_reduce_kernel<<<1, 64, 0, st>>>(w->part, w->g + w->out_w, w->C[0] + 1, oblocks);
+  const int oblocks = static_cast<int>((V0 + kSumChunk - 1) / kSumChunk);
+  const int C0 = w->C[0];
+  if (C0 == 16) chan_sum_kernel<16, true><<<oblocks, 256, 0, st>>>(last, w->gyf, w->part, V0);
+  else if (C0 == 32) chan_sum_kernel<32, true><<<oblocks, 256, 0, st>>>(last, w->gyf, w->part, V0);
+  else chan_sum_kernel<64, true><<<oblocks, 256, 0, st>>>(last, w->gyf, w->part, V0);
+  chan_sum_reduce_kernel<<<1, 64, 0, st>>>(w->part, w->g + w->out_w, C0 + 1, oblocks);
   int rc = check_cuda(cudaGetLastError(), "output layer backward");
   if (rc) return rc;
   int li = static_cast<int>(w->layers.size()) - 1;  // layers in reverse forward order
@@ -928,7 +954,7 @@ extern "C" int wsnet_create(int device, int32_t levels, const int32_t* channels,
     const int64_t chunks = (w->V[ly.level] + kWgradChunk - 1) / kWgradChunk;
     part = std::max(part, chunks * ly.cout * kpad(ly.cin));
   }
-  part = std::max<int64_t>(part, (w->V[0] / 4096 + 2) * 65);
+  part = std::max<int64_t>(part, (w->V[0] / kSumChunk + 2) * 65);
   w->part_elems = part;
   A(&w->part, static_cast<size_t>(part));
   A(&w->y, static_cast<size_t>(w->V[0]));
@@ -940,7 +966,7 @@ extern "C" int wsnet_create(int device, int32_t levels, const int32_t* channels,
   A(&w->rms_part, 256);
   A(&w->rms, 4);
   A(&w->status, 4);
-  w->use_tc = 0;
+  w->use_tc = 1;
   if (rc) {
     wsnet_destroy(w);
     return rc;
@@ -1096,8 +1122,8 @@ extern "C" int wsnet_loss_grad(wsnet* w, const float* x, const float* t, float* 
   return STENCIL_OK;
 }
 
-// Choose the convolution kernels: 1 = tcgen05 for eligible layers,
-// 0 (default) = mma.sync for every layer.
+// Choose the convolution kernels: 1 (default) = tcgen05 for eligible layers,
+// 0 = mma.sync for every layer.
 extern "C" int wsnet_use_tcgen05(wsnet* w, int32_t enable) {
   if (!w) return set_error(STENCIL_ERR_ARG, "wsnet_use_tcgen05: null net");
   w->use_tc = enable ? 1 : 0;
