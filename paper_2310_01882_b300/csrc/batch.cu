@@ -326,25 +326,33 @@ Layout plan(const stencil_problem* probs, int n) {
 
 // Compiled configurations of the inner sweep per storage type: (T, R, WY,
 // S, CTAs per SM).  The autotuner times each and keeps the fastest per sweep.
-using BF32a = TbCfg<PolF32, 1, 8, 4, 4, 3>;
-using BF32b = TbCfg<PolF32, 2, 4, 4, 5, 2>;
-using BB16a = TbCfg<PolBF16, 1, 8, 4, 4, 3>;
-using BB16b = TbCfg<PolBF16, 2, 4, 4, 5, 2>;
+template <class... Cs>
+struct CfgList {};
+template <class P>
+using BatchCfgs = CfgList<TbCfg<P, 1, 8, 4, 4, 3>, TbCfg<P, 1, 8, 8, 4, 2>, TbCfg<P, 1, 4, 8, 6, 3>,
+                          TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>, TbCfg<P, 2, 4, 8, 6, 2>>;
+constexpr int kNumCfg = 6;
+
+// Calls f(Cfg{}) for the c-th configuration of the list.
+template <class F, class... Cs>
+void with_cfg(int c, CfgList<Cs...>, F&& f) {
+  int i = 0;
+  ((i++ == c ? (f(Cs{}), 0) : 0), ...);
+}
 
 struct CfgInfo {
   int T, BXO, BYO, BOXW, UROWS, FROWS, THREADS, SMEM;
 };
 
-template <class Cfg>
-CfgInfo info() {
-  return CfgInfo{Cfg::T, Cfg::BXO, Cfg::BYO, Cfg::BOXW, Cfg::UROWS, Cfg::FROWS, Cfg::THREADS, Cfg::SMEM};
-}
-
-constexpr int kNumCfg = 2;
-
 CfgInfo cfg_info(int di, int c) {
-  if (di == 0) return c == 0 ? info<BF32a>() : info<BF32b>();
-  return c == 0 ? info<BB16a>() : info<BB16b>();
+  CfgInfo out{};
+  auto get = [&](auto cfg) {
+    using C = decltype(cfg);
+    out = CfgInfo{C::T, C::BXO, C::BYO, C::BOXW, C::UROWS, C::FROWS, C::THREADS, C::SMEM};
+  };
+  if (di == 0) with_cfg(c, BatchCfgs<PolF32>{}, get);
+  else with_cfg(c, BatchCfgs<PolBF16>{}, get);
+  return out;
 }
 
 template <class Pol, class Cfg, int DT>
@@ -364,14 +372,17 @@ int launch_pass_cfg(const typename SrcBatch<Pol, DT>::Params& prm, int num_sms, 
 
 int launch_pass(int di, int c, const InstDesc* desc, const InstState* state, const int64_t* base, int n,
                 int parity, uint32_t* status, int num_sms, cudaStream_t st) {
+  int rc = 1;  // not a status: set when the configuration index matches
   if (di == 0) {
     typename SrcBatch<PolF32, 0>::Params p{desc, state, base, n, parity, status};
-    return c == 0 ? launch_pass_cfg<PolF32, BF32a, 0>(p, num_sms, st)
-                  : launch_pass_cfg<PolF32, BF32b, 0>(p, num_sms, st);
+    with_cfg(c, BatchCfgs<PolF32>{},
+             [&](auto cfg) { rc = launch_pass_cfg<PolF32, decltype(cfg), 0>(p, num_sms, st); });
+  } else {
+    typename SrcBatch<PolBF16, 1>::Params p{desc, state, base, n, parity, status};
+    with_cfg(c, BatchCfgs<PolBF16>{},
+             [&](auto cfg) { rc = launch_pass_cfg<PolBF16, decltype(cfg), 1>(p, num_sms, st); });
   }
-  typename SrcBatch<PolBF16, 1>::Params p{desc, state, base, n, parity, status};
-  return c == 0 ? launch_pass_cfg<PolBF16, BB16a, 1>(p, num_sms, st)
-                : launch_pass_cfg<PolBF16, BB16b, 1>(p, num_sms, st);
+  return rc == 1 ? set_error(STENCIL_ERR_ARG, "batch: no sweep configuration %d", c) : rc;
 }
 
 // Geometry and tensor maps of instance i for storage di under configuration

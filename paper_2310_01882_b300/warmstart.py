@@ -1,7 +1,7 @@
 """Learned warm start for the Jacobi Poisson solve: data, training, evaluation.
 
     python -m paper_2310_01882_b300.warmstart [--n 128] [--train 200] [--test 20]
-        [--epochs 30] [--batch 4] [--lr 1e-3] [--out DIR]
+        [--epochs 30] [--batch 4] [--lr 1e-3] [--together K] [--out DIR]
 
 Pairs (f, u*): f a k^-3 Gaussian random field (seeds 10000+i for training,
 20000+i held out), u* from plain FP64 Jacobi (stencil_jacobi_sweep) from zero
@@ -14,7 +14,9 @@ with plain FP64 Jacobi and with the mixed-precision solve
 the judge throughout.  The warm start's own residual is recorded; the
 "selected" figures use it only when, after `judge_sweeps` plain sweeps from
 each start, its residual is below the zero start's (the fallback is plain
-Jacobi from zero).
+Jacobi from zero).  With --together K, K held-out fields are also solved as
+one job (throughput): plain FP64 Jacobi over several streams against the
+batch solve with FP32 and BF16 inner storage, from zero and warm starts.
 
 Host-side orchestration only: every step runs in the library's kernels.
 """
@@ -48,34 +50,37 @@ class Solver:
 
     def solve(self, us, fs, chunk=1000, max_sweeps=2_000_000):
         """Sweep every u (F64 Fields, in place) until its relative residual is
-        <= RTOL, checking every `chunk` sweeps; up to len(streams) at once.
-        Returns per-instance (sweeps, rel)."""
+        <= RTOL, checking every `chunk` sweeps.  The streams work through the
+        instances as a queue: a stream whose instance has finished takes the
+        next one.  Returns per-instance (sweeps, rel)."""
         import torch
         out = [None] * len(us)
         k = len(self.streams)
-        for base in range(0, len(us), k):
-            idx = list(range(base, min(base + k, len(us))))
-            sweeps = {i: 0 for i in idx}
-            active = set(idx)
-            while active:
-                for j, i in enumerate(idx):
-                    if i in active:
-                        S.stencil_residual(self.ctxs[j], us[i], fs[i], self.h, self.norms[j], stream=self.streams[j])
-                torch.cuda.synchronize()
-                nrm = self.norms.cpu().numpy()
-                for j, i in enumerate(idx):
-                    if i not in active:
-                        continue
-                    rel = nrm[j, 0] / nrm[j, 1]
-                    if rel <= RTOL or sweeps[i] >= max_sweeps:
-                        out[i] = (sweeps[i], float(rel))
-                        active.discard(i)
-                for j, i in enumerate(idx):
-                    if i in active:
-                        S.stencil_jacobi_sweep(self.ctxs[j], us[i], self.tmp[j], fs[i], self.work[j], self.h, chunk,
-                                               0, S.SWEEP_AUTO, stream=self.streams[j])
-                        sweeps[i] += chunk
-        return out
+        queue = list(range(len(us)))[::-1]
+        slot = [None] * k
+        sweeps = [0] * len(us)
+        while True:
+            for j in range(k):
+                if slot[j] is None and queue:
+                    slot[j] = queue.pop()
+            if all(i is None for i in slot):
+                return out
+            for j, i in enumerate(slot):
+                if i is not None:
+                    S.stencil_residual(self.ctxs[j], us[i], fs[i], self.h, self.norms[j], stream=self.streams[j])
+            torch.cuda.synchronize()
+            nrm = self.norms.cpu().numpy()
+            for j, i in enumerate(slot):
+                if i is None:
+                    continue
+                rel = nrm[j, 0] / nrm[j, 1]
+                if rel <= RTOL or sweeps[i] >= max_sweeps:
+                    out[i] = (sweeps[i], float(rel))
+                    slot[j] = None
+                    continue
+                S.stencil_jacobi_sweep(self.ctxs[j], us[i], self.tmp[j], fs[i], self.work[j], self.h, chunk,
+                                       0, S.SWEEP_AUTO, stream=self.streams[j])
+                sweeps[i] += chunk
 
 
 def generate_pairs(solver, seeds):
@@ -163,6 +168,79 @@ def evaluate(net, solver, seeds, chunk=200, judge_sweeps=50):
     return rows
 
 
+def solve_together(solver, fs, starts, kind, chunk=200, sweeps_per_cycle=400):
+    """Bring every field to RTOL together (throughput: the fields are solved
+    as one job) and time it.  kind "fp64": plain FP64 Jacobi on the
+    solver's streams, residual checked every `chunk` sweeps; "f32"/"bf16":
+    stencil_batch_solve with that inner storage, every active instance in
+    one persistent launch per pass.  starts: list of None (zero) or F64
+    storage tensors to copy.  Returns (seconds, sweeps list, max rel, ok)."""
+    import torch
+    n, h = solver.n, solver.h
+    us = []
+    for st in starts:
+        u = S.Field(n, n, n)
+        if st is not None:
+            u.storage.copy_(st)
+        us.append(u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if kind == "fp64":
+        info = solver.solve(us, fs, chunk=chunk)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sweeps = [sw for sw, _ in info]
+        rels = [rel for _, rel in info]
+        ok = all(r <= RTOL for r in rels)
+    else:
+        inner = S.F32 if kind == "f32" else S.BF16
+        res = S.stencil_batch_solve(solver.ctxs[0], us, fs, [h] * len(us), RTOL, inner_dtype=inner,
+                                    sweeps_per_cycle=sweeps_per_cycle)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sweeps = [r["sweeps"] for r in res]
+        rels = [r["rel_residual"] for r in res]
+        ok = all(r["status"] == 0 and r["rel_residual"] <= RTOL for r in res)
+    # the FP64 residual of every returned u is the judge
+    worst = 0.0
+    for u, f in zip(us, fs):
+        S.stencil_residual(solver.ctxs[0], u, f, h, solver.norms[0])
+        nrm = solver.norms[0].cpu().numpy()
+        worst = max(worst, float(nrm[0] / nrm[1]))
+    return dt, sweeps, worst, ok and worst <= RTOL
+
+
+def evaluate_together(net, solver, seeds, kinds=("fp64", "f32", "bf16")):
+    """Time to bring ALL the held-out fields to RTOL as one job, from zero
+    starts and from warm starts (inference of every field included)."""
+    import torch
+    n = solver.n
+    fs = [S.Field.from_numpy(inputs.grf(n, seed=s)) for s in seeds]
+    warm = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if net is not None:
+        for f in fs:
+            u = S.Field(n, n, n)
+            S.wsnet_infer(net, f, u)
+            warm.append(u.storage)
+    torch.cuda.synchronize()
+    infer_s = time.perf_counter() - t0
+    out = {"fields": len(seeds), "infer_seconds": infer_s}
+    for start in (("zero", "warm") if net is not None else ("zero",)):
+        starts = [None] * len(fs) if start == "zero" else warm
+        for kind in kinds:
+            dt, sweeps, worst, ok = solve_together(solver, fs, starts, kind)
+            if start == "warm":
+                dt += infer_s
+            out[f"{kind}_{start}"] = {"seconds": dt, "sweeps_median": float(np.median(sweeps)),
+                                      "sweeps_total": int(np.sum(sweeps)), "worst_rel": worst, "ok": ok}
+    base = out["fp64_zero"]["seconds"]
+    out["speedup_vs_fp64_zero"] = {k: base / v["seconds"] for k, v in out.items()
+                                   if isinstance(v, dict) and "seconds" in v and k != "fp64_zero"}
+    return out
+
+
 def summarise(rows):
     def med(key, field):
         return float(np.median([r[key][field] for r in rows]))
@@ -194,30 +272,44 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--load", default=None, help="evaluate saved parameters (.npy) instead of training")
+    ap.add_argument("--together", type=int, default=0,
+                    help="also time solving this many held-out fields as one job")
     ap.add_argument("--out", default=".")
     args = ap.parse_args()
     import torch
     log = lambda m: print(m, flush=True)  # noqa: E731
     solver = Solver(args.n, streams=args.streams)
-    t0 = time.perf_counter()
-    fs, us, info = generate_pairs(solver, [10000 + i for i in range(args.train)])
-    torch.cuda.synchronize()
-    gen_s = time.perf_counter() - t0
-    log(f"generated {args.train} pairs in {gen_s:.1f} s; sweeps median {np.median([s for s, _ in info])}")
     net = S.WsNet(len(CHANNELS), CHANNELS, args.n, seed=1)
-    t0 = time.perf_counter()
-    hist = train(net, fs, us, args.epochs, args.batch, args.lr, log=log)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    np.save(os.path.join(args.out, "wsnet_params.npy"), net.get_params())
+    gen_s = train_s = 0.0
+    hist = []
+    if args.load:
+        net.set_params(np.load(args.load))
+        args.train = args.epochs = 0
+    else:
+        t0 = time.perf_counter()
+        fs, us, info = generate_pairs(solver, [10000 + i for i in range(args.train)])
+        torch.cuda.synchronize()
+        gen_s = time.perf_counter() - t0
+        log(f"generated {args.train} pairs in {gen_s:.1f} s; sweeps median {np.median([s for s, _ in info])}")
+        t0 = time.perf_counter()
+        hist = train(net, fs, us, args.epochs, args.batch, args.lr, log=log)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del fs, us
+        np.save(os.path.join(args.out, "wsnet_params.npy"), net.get_params())
     rows = evaluate(net, solver, [20000 + i for i in range(args.test)])
     summary = summarise(rows)
+    log(json.dumps(summary))
+    together = None
+    if args.together:
+        together = evaluate_together(net, solver, [20000 + i for i in range(args.together)])
+        log(json.dumps(together))
     result = {"n": args.n, "train_pairs": args.train, "test_fields": args.test, "epochs": args.epochs,
               "batch": args.batch, "lr": args.lr, "gen_seconds": gen_s, "train_seconds": train_s,
-              "loss_history": hist, "summary": summary, "rows": rows}
+              "loss_history": hist, "summary": summary, "rows": rows, "together": together}
     with open(os.path.join(args.out, "warmstart.json"), "w") as fh:
         json.dump(result, fh, indent=1)
-    log(json.dumps(summary))
 
 
 if __name__ == "__main__":
