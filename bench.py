@@ -10,8 +10,10 @@ updates per second) and the fraction of the measured HBM roofline.
 
 Side measurements on the same line: the same step with FP32 and BF16
 storage, the FP64 residual and the PW advection (512x512x256) throughput,
-an end-to-end run from pinned host buffers, and the CPU oracle on the
-host cores (a bounded sample).  Inputs (1.1 GB per FP64 field) are larger
+the time to relative residual 1e-8 of 16 Poisson problems of 128^3 (plain
+FP64 Jacobi against the mixed-precision batch solve), an end-to-end run
+from pinned host buffers, and the CPU oracle on the host cores (a bounded
+sample).  Inputs (1.1 GB per FP64 field) are larger
 than the 126 MB L2, so no flush is needed between timed iterations.
 
 Multi-GPU: one process per GPU (torchrun); the work is replicated, not
@@ -38,11 +40,21 @@ ALGO_BYTES = {"f64": 24, "f32": 12, "bf16": 6}   # read u, read f, write u' per 
 
 
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, measured on
-# a 320^3 launch and scaled by the lattice points to 512^3 (the traffic grows
-# with the points); keyed by the kernel configuration it was measured on.
-# Command: ncu --set full --clock-control none -k regex:jacobi_tb -s 3 -c 1
-#   python bench.py --grid 320 --sweeps 8 --only f64 --steps 1 --warmup 1 --no-cpu
-MEASURED_TRAFFIC = {"jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (617.844736e6 + 232.756480e6) * (512 / 320) ** 3}
+# a 320^3 launch of each one-sweep configuration and scaled by the lattice
+# points to 512^3 (the traffic grows with the points); keyed by the kernel
+# configuration the autotuner may keep.  Command, for index i = 0..4 of the
+# compiled one-sweep configurations:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:jacobi_tb -s 2 -c 1
+#   python bench.py --grid 320 --sweeps 8 --only f64 --steps 1 --warmup 1 --no-cpu --f64-config i
+_SCALE_320 = (512 / 320) ** 3
+MEASURED_TRAFFIC = {
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (613374976 + 231496704) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (565770496 + 231974656) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (570426880 + 234036224) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (596441344 + 234272768) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (575960320 + 235593728) * _SCALE_320,
+}
 
 
 def chosen_config(report, T, policy_name):
@@ -220,6 +232,30 @@ def run_ours(args, rank, world, local_rank):
             ms = float(t.item())
         return ms / steps
 
+    if args.only == "wsnet":
+        r = wsnet_perf(N, infer_reps=args.steps, grad_reps=args.steps)
+        if rank == 0:
+            print(json.dumps({"metric": "warm-start net (profiling run)", **r}))
+        ctx.close()
+        return
+
+    if args.only == "advect":
+        from paper_2310_01882_b300 import inputs
+        nz = N // 2
+        uw, vw, ww = inputs.winds(N, N, nz)
+        fu, fv, fw = (S.Field.from_numpy(a, S.F64, device=dev) for a in (uw, vw, ww))
+        su, sv, sw = fu.like(), fu.like(), fu.like()
+        t1 = torch.from_numpy(inputs.tzc(nz, 7)).to(dev)
+        t2 = torch.from_numpy(inputs.tzc(nz, 8)).to(dev)
+        ams = timed_steps(lambda: S.stencil_advect_uvw(ctx, fu, fv, fw, su, sv, sw, t1, t2, 0.25, 0.25),
+                          args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": "Gpt/s (profiling run, advection only)",
+                              "value": round(N * N * nz / (ams * 1e-3) / 1e9, 2), "unit": "Gpt/s",
+                              "grid": [N, N, nz], "ms_per_step": round(ams, 3)}))
+        ctx.close()
+        return
+
     if args.only in ("f32", "bf16"):
         dt = S.F32 if args.only == "f32" else S.BF16
         u, ut, f = fields(dt)
@@ -314,6 +350,18 @@ def run_ours(args, rank, world, local_rank):
     del fu, fv, fw, su, sv, sw
     torch.cuda.empty_cache()
 
+    # ---- warm-start network (BF16 tensor-core convolutions) -----------------------
+    components["wsnet_128cubed"] = wsnet_perf()
+
+    # ---- batched mixed-precision solve, 256 uneven instances ---------------------
+    components["batch_256"] = batch_throughput()
+    torch.cuda.empty_cache()
+
+    # ---- time to relative residual 1e-8 (zero start): mixed vs plain FP64 -----
+    if not args.no_ttr:
+        components["time_to_residual"] = time_to_residual(args.ttr_fields)
+        torch.cuda.empty_cache()
+
     # ---- end to end through the public API from pinned host buffers ------------
     u_host = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
     f_host = torch.from_numpy(np.ascontiguousarray(f_np)).pin_memory()
@@ -368,6 +416,118 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
+WS_CHANNELS = [16, 32, 64, 64]
+
+
+def wsnet_flops(n, channels):
+    """Multiply-add FLOPs (2 per product) of the 3x3x3 convolutions of one
+    forward pass of the warm-start U-Net on n^3 (the 1x1x1 output layer,
+    pooling, upsampling and filter add < 0.1%)."""
+    L = len(channels)
+    fl = 0
+    for l in range(L):
+        v = (n >> l) ** 3
+        cin = 1 if l == 0 else channels[l - 1]
+        fl += 2 * 27 * v * (cin * channels[l] + channels[l] * channels[l])
+        if l <= L - 2:
+            fl += 2 * 27 * v * (channels[l + 1] * channels[l] + channels[l] * channels[l])
+    return fl
+
+
+def wsnet_perf(n=128, infer_reps=10, grad_reps=5):
+    """Inference and one training pass (forward, loss, backward) of the
+    warm-start net on n^3, timed with CUDA events."""
+    import torch
+    from paper_2310_01882_b300 import inputs
+    from paper_2310_01882_b300 import stencil as S
+    net = S.WsNet(len(WS_CHANNELS), WS_CHANNELS, n, seed=1)
+    f = S.Field.from_numpy(inputs.grf(n, seed=5))
+    u = S.Field(n, n, n)
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.standard_normal(n ** 3).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal(n ** 3).astype(np.float32)).cuda()
+    y = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        S.wsnet_infer(net, f, u)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(infer_reps):
+        S.wsnet_infer(net, f, u)
+    e1.record()
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / infer_reps
+    for _ in range(2):
+        S.wsnet_loss_grad(net, x, t, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(grad_reps):
+        S.wsnet_loss_grad(net, x, t, y)
+    torch.cuda.synchronize()
+    grad_ms = (time.perf_counter() - t0) * 1e3 / grad_reps
+    S.wsnet_status(net)
+    fl = wsnet_flops(n, WS_CHANNELS)
+    net.close()
+    return {"grid": n, "channels": WS_CHANNELS, "conv": "tcgen05 (kind::f16, bf16 in, f32 accumulate)",
+            "infer_ms": round(infer_ms, 3), "forward_gflop": round(fl / 1e9, 1),
+            "infer_tflops": round(fl / (infer_ms * 1e-3) / 1e12, 1),
+            "loss_grad_ms": round(grad_ms, 3), "loss_grad_tflops": round(3 * fl / (grad_ms * 1e-3) / 1e12, 1)}
+
+
+def batch_throughput(max_sweeps=4000, sweeps_per_cycle=400):
+    """The batched mixed-precision solve on 256 cubic instances of sizes
+    U[32,192] (seed 9; 5.98e8 interior points), sources iid U[0,1)
+    (seeds 1000+i), zero start, run for a fixed budget of max_sweeps inner
+    sweeps per instance (no instance reaches 1e-8 in it): inner lattice
+    updates per second over the whole call (set-up, autotuning, graph
+    capture and refinement included)."""
+    import torch
+    from paper_2310_01882_b300 import inputs
+    from paper_2310_01882_b300 import stencil as S
+    ctx = S.Context(0)
+    sizes = inputs.batch_sizes()
+    fs = [S.Field.from_numpy(inputs.uniform(n, n, n, 1000 + i)) for i, n in enumerate(sizes)]
+    out = {"workload": "256 Poisson instances, n ~ U[32,192] (seed 9), iid U[0,1) sources, zero start",
+           "points": int(sum(n ** 3 for n in sizes)), "max_sweeps": max_sweeps}
+    for name, dt in (("f32", S.F32), ("bf16", S.BF16)):
+        us = [S.Field(n, n, n) for n in sizes]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = S.stencil_batch_solve(ctx, us, fs, [1.0 / (n + 1) for n in sizes], 1e-8, inner_dtype=dt,
+                                    max_sweeps=max_sweeps, sweeps_per_cycle=sweeps_per_cycle)
+        torch.cuda.synchronize()
+        dts = time.perf_counter() - t0
+        lups = sum(r["sweeps"] * n ** 3 for r, n in zip(res, sizes))
+        out[name] = {"seconds": round(dts, 3), "glups": round(lups / dts / 1e9, 1),
+                     "sweeps_per_instance": int(np.median([r["sweeps"] for r in res])),
+                     "final_dtypes": sorted({int(r["final_dtype"]) for r in res})}
+        del us
+    del fs
+    ctx.close()
+    return out
+
+
+def time_to_residual(fields, n=128):
+    """Seconds for `fields` k^-3 GRF Poisson problems of n^3 (seeds 20000+i),
+    from zero starts, to reach relative residual 1e-8 as one job: plain FP64
+    Jacobi (8 streams, residual every 200 sweeps) against the mixed-precision
+    batch solve with FP32 and with BF16 inner storage.  The FP64 residual of
+    every returned u is checked afterwards."""
+    from paper_2310_01882_b300 import inputs, warmstart
+    from paper_2310_01882_b300 import stencil as S
+    solver = warmstart.Solver(n, streams=8)
+    fs = [S.Field.from_numpy(inputs.grf(n, seed=20000 + i)) for i in range(fields)]
+    out = {"workload": f"{fields} Poisson problems {n}^3, k^-3 GRF sources, zero start, rtol 1e-8",
+           "unit": "s"}
+    for kind in ("fp64", "f32", "bf16"):
+        dt, sweeps, worst, ok = warmstart.solve_together(solver, fs, [None] * fields, kind)
+        out[kind] = {"seconds": round(dt, 3), "sweeps_median": float(np.median(sweeps)),
+                     "glups": round(n ** 3 * float(np.sum(sweeps)) / dt / 1e9, 1), "worst_rel": worst, "ok": ok}
+    out["speedup_f32_vs_fp64"] = round(out["fp64"]["seconds"] / out["f32"]["seconds"], 3)
+    out["speedup_bf16_vs_fp64"] = round(out["fp64"]["seconds"] / out["bf16"]["seconds"], 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,11 +536,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual comparison")
+    ap.add_argument("--ttr-fields", type=int, default=16, help="problems in the time-to-residual comparison")
     ap.add_argument("--f64-config", type=int, default=None,
                     help="pin the headline's FP64 one-sweep configuration (index; profiling runs)")
     ap.add_argument("--grid", type=int, default=None, help="grid extent (profiling runs; default 512)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step (profiling runs; default 1000)")
-    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16"],
+    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet"],
                     help="run one dtype's step only (profiling runs)")
     ap.add_argument("--spp", type=int, default=0, help="sweeps per pass for --only runs (0 = library default)")
     ap.add_argument("--traffic", type=float, default=None,
