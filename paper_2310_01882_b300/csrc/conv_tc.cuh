@@ -234,5 +234,186 @@ __global__ void __launch_bounds__(128, 1) conv3_tc_kernel(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores.  For one chunk of 128-voxel tiles and
+// one group of TG = 128 / CIN taps:
+//   D[(tap, ci)][co] = sum over the chunk's voxels v of x[v + off(tap)][ci] g[v][co]
+// i.e. M = 128 rows (TG taps x CIN channels), N = COUT, K = voxels.  Both
+// operands are used as TMA lands them, MN-major: a tap's box is [v][ci]
+// (the M values of one voxel contiguous, one swizzle atom wide) and the
+// gradient box is [v][co].  The TG tap boxes of a stage sit TAP_BYTES apart
+// (the descriptor's leading byte offset between M atoms); 8-voxel row groups
+// are 8 rows apart (its stride byte offset).  The chunk's partial sums go to
+// part[chunk][co][tap*CIN + ci], the layout the fixed-order chunk reduction
+// reads.
+template <int CIN, int COUT>
+struct WgCfg {
+  static constexpr int TG = 128 / CIN;
+  static constexpr int TAP_BYTES = 128 * CIN * 2;
+  static constexpr int ABYTES = TG * TAP_BYTES;  // 32 KB
+  static constexpr int BBYTES = 128 * COUT * 2;
+  static constexpr int S = 3;
+  static constexpr int STAGE = ABYTES + BBYTES;  // a multiple of 1024
+  static constexpr int SMEM = 1024 + S * STAGE + 256;
+  static constexpr int TMEM_COLS = COUT < 32 ? 32 : COUT;
+  static constexpr uint64_t LAYOUT_A = TcSwz<CIN>::LAYOUT;
+  static constexpr uint64_t LAYOUT_B = TcSwz<COUT>::LAYOUT;
+};
+
+struct WgParams {
+  CUtensorMap tm_in;  // activations (CIN, W, H, D), box (CIN, W, HB, 1)
+  CUtensorMap tm_g;   // output gradient (COUT, W, H, D), box (COUT, W, HB, 1)
+  float* part;        // [chunk][COUT][kp]
+  int kp;
+  int D, H, W, HB;
+  int tiles;          // 128-voxel tiles in the grid
+  int chunk_tiles;    // tiles per chunk (K steps of one CTA)
+  uint32_t* status;
+};
+
+// smem descriptor with both offsets given (MN-major operands).
+__device__ __forceinline__ uint64_t tc_smem_desc2(uint32_t addr, uint64_t layout, uint32_t lbo_bytes,
+                                                  uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo_bytes >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= layout << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor with A and B MN-major (transposed).
+__host__ __device__ constexpr uint32_t tc_idesc_mn(int M, int N) {
+  return tc_idesc(M, N) | (1u << 15) | (1u << 16);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128, 1) wgrad_tc_kernel(const __grid_constant__ WgParams p) {
+  using Cfg = WgCfg<CIN, COUT>;
+  constexpr int S = Cfg::S;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* ring = base;
+  unsigned char* tail = base + S * Cfg::STAGE;
+  const uint32_t bar_full = smem_addr(tail);
+  const uint32_t bar_empty = bar_full + 8 * S;
+  const uint32_t bar_acc = bar_empty + 8 * S;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(tail + 8 * (2 * S + 1));
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tap0 = blockIdx.y * Cfg::TG;
+  const int ntap = min(Cfg::TG, 27 - tap0);
+  const int t_begin = blockIdx.x * p.chunk_tiles;
+  const int nk = min(p.chunk_tiles, p.tiles - t_begin);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    mbar_init(bar_acc, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(const_cast<uint32_t*>(tmem_slot))),
+                 "r"(Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int64_t HW = static_cast<int64_t>(p.H) * p.W;
+  if (warp == 0 && lane == 0) {
+    prefetch_tensormap(&p.tm_in);
+    prefetch_tensormap(&p.tm_g);
+    int issued = 0;
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % S;
+      const uint32_t par = (k / S) & 1u;
+      if (!mbar_wait_bounded(bar_empty + 8 * s, par ^ 1u, p.status)) { abort_flag = 1; break; }
+      const int64_t v0 = static_cast<int64_t>(t_begin + k) * 128;
+      const int z0 = static_cast<int>(v0 / HW);
+      const int y0 = static_cast<int>((v0 / p.W) % p.H);
+      const uint32_t a = smem_addr(ring + s * Cfg::STAGE);
+      mbar_arrive_expect_tx(bar_full + 8 * s, ntap * Cfg::TAP_BYTES + Cfg::BBYTES);
+      for (int j = 0; j < ntap; ++j) {
+        const int tap = tap0 + j;
+        tma_load_4d(a + j * Cfg::TAP_BYTES, &p.tm_in, 0, tap % 3 - 1, y0 + (tap / 3) % 3 - 1, z0 + tap / 9 - 1,
+                    bar_full + 8 * s);
+      }
+      tma_load_4d(a + Cfg::ABYTES, &p.tm_g, 0, 0, y0, z0, bar_full + 8 * s);
+      issued = k + 1;
+    }
+    // no copy may still be landing in shared memory when the CTA exits
+    for (int s = 0; s < S && s < issued; ++s) {
+      const int last = s + (issued - 1 - s) / S * S;
+      mbar_wait_bounded(bar_full + 8 * s, (last / S) & 1u, p.status);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = tc_idesc_mn(128, COUT);
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % S;
+      const uint32_t par = (k / S) & 1u;
+      if (*reinterpret_cast<volatile int*>(&abort_flag) || !mbar_wait_bounded(bar_full + 8 * s, par, p.status)) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = smem_addr(ring + s * Cfg::STAGE);
+      const uint32_t b = a + Cfg::ABYTES;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {  // 16 voxels per MMA
+        const uint64_t ad = tc_smem_desc2(a + kk * 16 * CIN * 2, Cfg::LAYOUT_A, Cfg::TAP_BYTES, 8 * CIN * 2);
+        const uint64_t bd = tc_smem_desc2(b + kk * 16 * COUT * 2, Cfg::LAYOUT_B, 16, 8 * COUT * 2);
+        const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       bar_empty + 8 * s)
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_acc)
+                 : "memory");
+  }
+  __syncwarp();
+  const bool acc_ok = mbar_wait_bounded(bar_acc, 0, p.status);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (__all_sync(0xffffffffu, acc_ok && !*reinterpret_cast<volatile int*>(&abort_flag))) {
+    const int m = warp * 32 + lane;  // row (tap0 + m / CIN, m % CIN)
+    const bool valid = m < ntap * CIN;
+    float* dst = p.part + static_cast<int64_t>(blockIdx.x) * COUT * p.kp + tap0 * CIN + m;
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) dst[static_cast<int64_t>(c0 + j) * p.kp] = __uint_as_float(r[j]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 }  // namespace net
 }  // namespace stencil

@@ -628,10 +628,64 @@ int launch_conv(int cin, int cout, bool relu, bool skip, const bf16* in, const b
 
 constexpr int kWgradChunk = 8192;
 
+template <int CIN, int COUT>
+int launch_wgrad_tc(const bf16* in, const bf16* g, float* part, int chunks, int D, int H, int W, uint32_t* status,
+                    cudaStream_t st) {
+  using Cfg = WgCfg<CIN, COUT>;
+  WgParams p;
+  auto swz = [](int c) {
+    return c == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+  };
+  const int hb = 128 / W;
+  const uint64_t dims_in[4] = {static_cast<uint64_t>(CIN), static_cast<uint64_t>(W), static_cast<uint64_t>(H),
+                               static_cast<uint64_t>(D)};
+  const uint64_t str_in[3] = {static_cast<uint64_t>(CIN) * 2, static_cast<uint64_t>(W) * CIN * 2,
+                              static_cast<uint64_t>(H) * W * CIN * 2};
+  const uint32_t box_in[4] = {static_cast<uint32_t>(CIN), static_cast<uint32_t>(W), static_cast<uint32_t>(hb), 1};
+  int rc = encode_tiled(&p.tm_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(in), dims_in, str_in, box_in,
+                        swz(CIN));
+  if (rc) return rc;
+  const uint64_t dims_g[4] = {static_cast<uint64_t>(COUT), static_cast<uint64_t>(W), static_cast<uint64_t>(H),
+                              static_cast<uint64_t>(D)};
+  const uint64_t str_g[3] = {static_cast<uint64_t>(COUT) * 2, static_cast<uint64_t>(W) * COUT * 2,
+                             static_cast<uint64_t>(H) * W * COUT * 2};
+  const uint32_t box_g[4] = {static_cast<uint32_t>(COUT), static_cast<uint32_t>(W), static_cast<uint32_t>(hb), 1};
+  rc = encode_tiled(&p.tm_g, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(g), dims_g, str_g, box_g,
+                    swz(COUT));
+  if (rc) return rc;
+  p.part = part;
+  p.kp = kpad(CIN);
+  p.D = D; p.H = H; p.W = W; p.HB = hb;
+  const int64_t V = static_cast<int64_t>(D) * H * W;
+  p.tiles = static_cast<int>(V / 128);
+  p.chunk_tiles = kWgradChunk / 128;
+  p.status = status;
+  const dim3 grid(chunks, (27 + Cfg::TG - 1) / Cfg::TG);
+  auto kern = wgrad_tc_kernel<CIN, COUT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+  if (e != cudaSuccess) return check_cuda(e, "wgrad tc attribute");
+  kern<<<grid, 128, Cfg::SMEM, st>>>(p);
+  return check_cuda(cudaGetLastError(), "wgrad tc launch");
+}
+
+// tc_status: as for launch_conv (null: the mma.sync kernel).
 int launch_wgrad(int cin, int cout, const bf16* in, const bf16* g, float* part, float* dW, int D, int H, int W,
-                 cudaStream_t st) {
+                 uint32_t* tc_status, cudaStream_t st) {
   const int64_t V = static_cast<int64_t>(D) * H * W;
   const int chunks = static_cast<int>((V + kWgradChunk - 1) / kWgradChunk);
+  if (tc_status && tc_eligible(cin, cout, D, H, W)) {
+    int rc = STENCIL_ERR_ARG;
+#define X(CI, CO) \
+    if (cin == CI && cout == CO) rc = launch_wgrad_tc<CI, CO>(in, g, part, chunks, D, H, W, tc_status, st);
+    X(16, 16) X(16, 32) X(16, 64) X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64)
+#undef X
+    if (rc) return rc == STENCIL_ERR_ARG ? set_error(rc, "wsnet: no tensor-core weight gradient for %d -> %d",
+                                                     cin, cout)
+                                         : rc;
+    wgrad_reduce_kernel<<<blocks_for(int64_t(cout) * kpad(cin)), 256, 0, st>>>(part, dW, cout, kpad(cin), 27 * cin,
+                                                                                 chunks);
+    return check_cuda(cudaGetLastError(), "wgrad reduce");
+  }
   const dim3 grid(chunks, 27);
 #define X(CI, CO)                                                                                   \
   if (cin == CI && cout == CO) {                                                                   \
@@ -788,7 +842,8 @@ int bias_grad(wsnet* w, const bf16* g, int64_t V, int C, float* db, cudaStream_t
 
 int conv_backward(wsnet* w, const Layer& ly, const bf16* in, const bf16* g, bf16* gin, int d, cudaStream_t st) {
   const int64_t V = static_cast<int64_t>(d) * d * d;
-  int rc = launch_wgrad(ly.cin, ly.cout, in, g, w->part, w->g + ly.woff, d, d, d, st);
+  int rc = launch_wgrad(ly.cin, ly.cout, in, g, w->part, w->g + ly.woff, d, d, d, w->use_tc ? w->status : nullptr,
+                        st);
   if (!rc) rc = bias_grad(w, g, V, ly.cout, w->g + ly.boff, st);
   if (!rc && gin)
     rc = launch_conv(ly.cout, ly.cin, false, false, g, ly.wt, w->zero_bias, nullptr, gin, d, d, d,

@@ -12,6 +12,7 @@ int sweep_variants_f64(int policy, int T, const SweepVariant** out) {
       variant<PolResident, TbCfg<PolResident, 1, 8, 4, 6, 2>>(),
       variant<PolResident, TbCfg<PolResident, 1, 4, 4, 6, 4>>(),
       variant<PolResident, TbCfg<PolResident, 1, 8, 8, 4, 1>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 2, 16, 5, 1>>(),
   };
   static const SweepVariant res2[] = {
       variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2>>(),
