@@ -74,6 +74,28 @@ def chosen_config(report, T, policy_name):
     return f"jacobi_tb<{policy_name},T={T},R={p['R']},WY={p['WY']},S={p['S']}>"
 
 
+HEADLINE_METRIC = "GLUP/s and % HBM roofline at 1 B300 (512^3 FP64 Jacobi 7-point Poisson sweeps)"
+
+
+def headline_config(world=1):
+    """The workload both arms report (the same dict on every line)."""
+    return {"workload": "jacobi_512cubed_f64", "grid": [N, N, N], "sweeps_per_step": SWEEPS,
+            "source": "k^-3 Gaussian random field seed 2", "u0": "U[0,1) seed 3",
+            "l2": "inputs 1.1 GB per field > 126 MB L2 (no flush needed)",
+            "parallelism": f"replicas x{world}"}
+
+
+def reduce_max(value, dist, device):
+    """The maximum of `value` over all ranks (the job's time is its slowest
+    rank's); `dist` is torch.distributed or None for one process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -177,11 +199,11 @@ def reference_arm(args, rank):
     dt = time.perf_counter() - t0
     value = N ** 3 * per_step_sweeps * args.steps / dt / 1e9
     sample = f"each step: {per_step_sweeps} FP64 Jacobi sweep of the 512^3 grid (plain C oracle, {threads} threads)"
-    line = {"impl": "reference", "metric": "GLUP/s (512^3 FP64 Jacobi 7-point Poisson sweeps)", "value": round(value, 4),
+    line = {"impl": "reference", "metric": HEADLINE_METRIC, "value": round(value, 4),
             "unit": "GLUP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "jacobi_512cubed_f64", "grid": [N, N, N], "sweeps_per_step": per_step_sweeps},
+            "config": headline_config(int(os.environ.get("WORLD_SIZE", 1))),
             "cpu_baseline": {"value": round(value, 4), "unit": "GLUP/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -225,11 +247,7 @@ def run_ours(args, rank, world, local_rank):
             fn()
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(e0.elapsed_time(e1), dist, dev)
         return ms / steps
 
     if args.only == "wsnet":
@@ -386,14 +404,11 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0:
         line = {
-            "metric": "GLUP/s and % HBM roofline at 1 B300 (512^3 FP64 Jacobi 7-point Poisson sweeps)",
+            "metric": HEADLINE_METRIC,
             "value": round(world * glups, 2), "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 storage, i64 fixed-point arithmetic", "data": "synthetic",
-            "config": {"workload": "jacobi_512cubed_f64", "grid": [N, N, N], "sweeps_per_step": SWEEPS,
-                       "source": "k^-3 Gaussian random field seed 2", "u0": "U[0,1) seed 3",
-                       "l2": "inputs 1.1 GB per field > 126 MB L2 (no flush needed)",
-                       "parallelism": f"replicas x{world}"},
+            "config": headline_config(world),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4),
                          "traffic": args.traffic if args.traffic is not None else
