@@ -39,6 +39,7 @@ constexpr uint32_t kStatusRange = 4u;
 constexpr size_t kScratchStatus = 0;      // uint32 status bits
 constexpr size_t kScratchMaxU = 16;       // uint64 bits of max|u| (incl. halo)
 constexpr size_t kScratchMaxF = 24;       // uint64 bits of max|f| (interior)
+constexpr size_t kScratchAdvRange = 32;   // 5 x uint64: max|u|, max|v|, max|w|, max and min nonzero |coef|
 constexpr size_t kScratchPartials = 256;  // residual partial sums
 constexpr int kMaxPartials = 2048;        // blocks of the residual kernel
 constexpr size_t kScratchBytes = kScratchPartials + sizeof(double) * 2 * kMaxPartials;

@@ -93,12 +93,60 @@ def test_advect_full_size():
 
 
 def test_advect_constant_fields_zero():
-    """Constant fields with tzc1 = tzc2: the tendency is zero up to the
-    rounding of one product (the kernel fuses multiply-adds, so the two
-    cancelling terms need not round identically)."""
+    """Constant fields with tzc1 = tzc2: the tendency is exactly zero (the
+    fluxes are formed exactly in integer fixed point, so the cancelling
+    terms are equal)."""
     c = np.full((10, 9, 12), 2.5)
     t = inputs.tzc(8, 3)
     su, sv, sw = run_advect(c, c, c, t, t)
-    scale = 2 * 2.5 * 2.5 * max(0.25, np.max(t))
     for s in (su, sv, sw):
-        assert np.max(np.abs(s[1:-1, 1:-1, 1:-1])) <= 4 * np.finfo(float).eps * scale
+        assert np.all(s[1:-1, 1:-1, 1:-1] == 0.0)
+
+
+@pytest.mark.parametrize("scale", [1e150, 1e-150, -3.0])
+def test_advect_extreme_magnitudes(scale):
+    """The fixed-point scale follows the fields' magnitude (here 10^150 and
+    10^-150 times the benchmark winds, and a negated copy)."""
+    u, v, w = (scale * a for a in inputs.winds(40, 24, 10, seeds=(11, 12, 13)))
+    t1, t2 = inputs.tzc(10, 7), inputs.tzc(10, 8)
+    ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, 0.25)
+    got = run_advect(u, v, w, t1, t2)
+    for g, r in zip(got, ref):
+        assert rel_err(g, r) <= 1e-13
+
+
+@pytest.mark.parametrize("case", ["small_w", "small_tcy", "zero_v"])
+def test_advect_uneven_magnitudes(case):
+    """Fields or factors whose magnitudes differ by more than 2^8 are
+    evaluated in binary64 (a single fixed-point scale would cost the small
+    one its precision); a field that is identically zero keeps the
+    fixed-point path.  Either way the result matches the oracle."""
+    u, v, w = inputs.winds(33, 20, 9, seeds=(21, 22, 23))
+    t1, t2 = inputs.tzc(9, 7), inputs.tzc(9, 8)
+    tcy = 0.25
+    if case == "small_w":
+        w = w * 1e-7
+    elif case == "small_tcy":
+        tcy = 0.25e-6
+    else:
+        v = np.zeros_like(v)
+    ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, tcy)
+    got = run_advect(u, v, w, t1, t2, tcy=tcy)
+    for g, r in zip(got, ref):
+        assert rel_err(g, r) <= 1e-13
+
+
+def test_advect_nonfinite_propagates():
+    """A NaN in u: the launch falls back to binary64, so exactly the cells
+    whose stencil reads it are NaN, as in the oracle, and the rest match."""
+    u, v, w = inputs.winds(20, 16, 8, seeds=(31, 32, 33))
+    u[4, 5, 6] = np.nan
+    t1, t2 = inputs.tzc(8, 7), inputs.tzc(8, 8)
+    ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, 0.25)
+    got = run_advect(u, v, w, t1, t2)
+    inner = (slice(1, -1),) * 3
+    for g, r in zip(got, ref):
+        g, r = g[inner], r[inner]
+        assert np.array_equal(np.isnan(g), np.isnan(r)) and np.isnan(r).any()
+        ok = ~np.isnan(r)
+        assert np.max(np.abs(g[ok] - r[ok])) <= 1e-13 * np.max(np.abs(r[ok]))
