@@ -392,7 +392,16 @@ STENCIL_API int stencil_residual_noalloc(const stencil_grid* u,
  *      + c1*w[k-1]*(w+w[k-1]) - c2*w[k+1]*(w+w[k+1])
  * (unnamed offsets are 0).  All six grids F64 with equal extents; inputs'
  * halos are filled by the caller; outputs are written on the interior only.
- * tzc1, tzc2: DEVICE arrays of nz doubles.  Binary64 arithmetic.
+ * tzc1, tzc2: DEVICE arrays of nz doubles.
+ * Arithmetic: 64-bit integer fixed point with one scale for u, v, w (from
+ * their largest magnitude, halos included) and one for the factors; every
+ * sum of two values is exact, every product keeps the high 64 bits of its
+ * exact 128-bit value, and each tendency is rounded to binary64 once: the
+ * error is at most about 2^-50 max|u,v,w|^2 max|factor|, the order of a
+ * binary64 evaluation's rounding error, and equal fluxes cancel exactly.  If the three fields' (or
+ * the factors') largest magnitudes differ by more than 2^8, or an input is
+ * not finite, the launch evaluates the formula in binary64 instead (NaN and
+ * Inf propagate as in binary64).  Uses the context's scratch; asynchronous.
  */
 STENCIL_API int stencil_advect_uvw(stencil_ctx* ctx, const stencil_grid* u,
                        const stencil_grid* v, const stencil_grid* w,

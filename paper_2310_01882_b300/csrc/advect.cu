@@ -9,14 +9,14 @@
 //   * one scale S per call from max |u|, |v|, |w| (halos included):
 //     X = round(x 2^S) with |X| <= 2^61, so every sum of two is exact;
 //   * each product a (b + c) keeps the high 64 bits of its exact 128-bit
-//     value (a truncation below 2^-58 max|x|^2), so equal fluxes cancel
-//     exactly and a flux difference is exact to that truncation;
+//     value (a truncation below 2^-56 max|x|^2), so equal fluxes cancel
+//     exactly;
 //   * the factors tcx, tcy, tzc1[k], tzc2[k] use one scale T from their
 //     maximum (|C| <= 2^62; exact for the binary64 inputs in use), each
 //     factor product again keeps its high 64 bits, the three terms are
 //     summed in 64 bits and the sum is rounded to binary64 once.
-// The error is of the order of 2^-56 max|x|^2 max|C| per output, below that
-// of the binary64 evaluation of the same formula.  When the fields'
+// The error is at most about 2^-50 max|x|^2 max|C| per output, the order of
+// the rounding error of a binary64 evaluation of the same formula.  When the fields'
 // magnitudes differ by more than 2^8, or the factors' do, or a value is not
 // finite, a single scale would cost the smaller field its precision, so the
 // launch evaluates the formula in binary64 instead (the decision is taken
