@@ -35,6 +35,9 @@ def lib():
         L.oracle_f32_to_bf16.argtypes = [p, p, i64]
         L.oracle_bf16_to_f32.argtypes = [p, p, i64]
         L.oracle_residual_f64.argtypes = [p, p, i64, i64, i64, d, p, p, i32]
+        L.oracle_rbgs_f64.argtypes = [p, p, i64, i64, i64, d, i64, i32]
+        L.oracle_rbgs_f32.argtypes = [p, p, i64, i64, i64, f32, i64]
+        L.oracle_rbgs_bf16.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_advect_uvw.argtypes = [p, p, p, p, p, p, p, p, d, d, i64, i64, i64, i32]
         L.oracle_refine.argtypes = [p, p, i64, i64, i64, d, d, i32, i64, i64, d, p, p, i64, p, p, p]
         L.oracle_refine.restype = i64
@@ -119,6 +122,33 @@ def jacobi_sweep_bf16(u16, f16, h):
     nx, ny, nz = _dims(u16)
     lib().oracle_jacobi_sweep_bf16(_ptr(u16), _ptr(out), _ptr(f16), nx, ny, nz, f32_coeff(h))
     return out
+
+
+def rbgs(u, f, h, nsweeps, nthreads=1):
+    """nsweeps red-black Gauss-Seidel sweeps in FP64; returns a new field."""
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    f = _c64(f)
+    nx, ny, nz = _dims(u)
+    lib().oracle_rbgs_f64(_ptr(u), _ptr(f), nx, ny, nz, h, nsweeps, nthreads)
+    return u
+
+
+def rbgs_f32(u, f, h, nsweeps):
+    """Red-black sweeps with FP32 storage and arithmetic (inputs float32)."""
+    u = np.array(u, dtype=np.float32, order="C", copy=True)
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    nx, ny, nz = _dims(u)
+    lib().oracle_rbgs_f32(_ptr(u), _ptr(f), nx, ny, nz, f32_coeff(h), nsweeps)
+    return u
+
+
+def rbgs_bf16(u16, f16, h, nsweeps):
+    """Red-black sweeps with bf16 storage (uint16 bit patterns), FP32 arithmetic."""
+    u16 = np.array(u16, dtype=np.uint16, order="C", copy=True)
+    f16 = np.ascontiguousarray(f16, dtype=np.uint16)
+    nx, ny, nz = _dims(u16)
+    lib().oracle_rbgs_bf16(_ptr(u16), _ptr(f16), nx, ny, nz, f32_coeff(h), nsweeps)
+    return u16
 
 
 def residual(u, f, h, want_r=False, nthreads=1):

@@ -162,6 +162,80 @@ void oracle_jacobi_sweep_bf16(const uint16_t* u, uint16_t* out,
 }
 
 /*
+ * Red-black Gauss-Seidel.  Section 4.1 names the relaxation benchmark
+ * Gauss-Seidel; with the red-black ordering every half sweep stays data
+ * parallel.  One sweep updates, in place, first every interior point with
+ * i + j + k even ("red") from its six neighbours, then every interior point
+ * with i + j + k odd ("black") from its neighbours, which are all red and
+ * already updated.  Each update is the Jacobi formula above (same operation
+ * order).  A point's neighbours have the other colour, so the order of the
+ * updates within one colour does not matter.
+ */
+void oracle_rbgs_f64(double* u, const double* f, int64_t nx, int64_t ny,
+                     int64_t nz, double h, int64_t nsweeps, int nthreads) {
+  const double hh = h * h;
+  for (int64_t sw = 0; sw < nsweeps; ++sw)
+    for (int color = 0; color < 2; ++color) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(oracle_num_threads(nthreads))
+#endif
+      for (int64_t k = 1; k <= nz; ++k)
+        for (int64_t j = 1; j <= ny; ++j)
+          for (int64_t i = 1; i <= nx; ++i) {
+            if (((i + j + k) & 1) != color) continue;
+            double s = AT(u, i - 1, j, k) + AT(u, i + 1, j, k);
+            s += AT(u, i, j - 1, k);
+            s += AT(u, i, j + 1, k);
+            s += AT(u, i, j, k - 1);
+            s += AT(u, i, j, k + 1);
+            s += hh * AT(f, i, j, k);
+            AT(u, i, j, k) = s / 6.0;
+          }
+    }
+#ifndef _OPENMP
+  (void)nthreads;
+#endif
+}
+
+/* The same with FP32 storage and arithmetic (hh the FP32 coefficient). */
+void oracle_rbgs_f32(float* u, const float* f, int64_t nx, int64_t ny,
+                     int64_t nz, float hh, int64_t nsweeps) {
+  for (int64_t sw = 0; sw < nsweeps; ++sw)
+    for (int color = 0; color < 2; ++color)
+      for (int64_t k = 1; k <= nz; ++k)
+        for (int64_t j = 1; j <= ny; ++j)
+          for (int64_t i = 1; i <= nx; ++i) {
+            if (((i + j + k) & 1) != color) continue;
+            float s = AT(u, i - 1, j, k) + AT(u, i + 1, j, k);
+            s += AT(u, i, j - 1, k);
+            s += AT(u, i, j + 1, k);
+            s += AT(u, i, j, k - 1);
+            s += AT(u, i, j, k + 1);
+            s += hh * AT(f, i, j, k);
+            AT(u, i, j, k) = s / 6.0f;
+          }
+}
+
+/* The same with bf16 storage of u and f, FP32 arithmetic. */
+void oracle_rbgs_bf16(uint16_t* u, const uint16_t* f, int64_t nx, int64_t ny,
+                      int64_t nz, float hh, int64_t nsweeps) {
+  for (int64_t sw = 0; sw < nsweeps; ++sw)
+    for (int color = 0; color < 2; ++color)
+      for (int64_t k = 1; k <= nz; ++k)
+        for (int64_t j = 1; j <= ny; ++j)
+          for (int64_t i = 1; i <= nx; ++i) {
+            if (((i + j + k) & 1) != color) continue;
+            float s = bf16_to_float(AT(u, i - 1, j, k)) + bf16_to_float(AT(u, i + 1, j, k));
+            s += bf16_to_float(AT(u, i, j - 1, k));
+            s += bf16_to_float(AT(u, i, j + 1, k));
+            s += bf16_to_float(AT(u, i, j, k - 1));
+            s += bf16_to_float(AT(u, i, j, k + 1));
+            s += hh * bf16_to_float(AT(f, i, j, k));
+            AT(u, i, j, k) = float_to_bf16(s / 6.0f);
+          }
+}
+
+/*
  * Residual of the Poisson problem A u = f with the 7-point operator
  *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2
  *     r = f - A u

@@ -12,7 +12,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
-PINS = ["tests/test_oracle_jacobi.py", "tests/test_oracle_residual.py", "tests/test_oracle_advect.py"]
+PINS = ["tests/test_oracle_jacobi.py", "tests/test_oracle_residual.py", "tests/test_oracle_advect.py",
+        "tests/test_oracle_rbgs.py"]
 
 MUTANTS = {
     "sweep_z_as_y": ("s += AT(u, i, j, k + 1);\n        s += hh", "s += AT(u, i, j + 1, k);\n        s += hh"),
@@ -27,6 +28,10 @@ MUTANTS = {
     "su_sign_x": ("tx = tcx * (AT(u, i - 1, j, k) * (AT(u, i, j, k) + AT(u, i - 1, j, k)) -",
                   "tx = tcx * (AT(u, i - 1, j, k) * (AT(u, i, j, k) + AT(u, i - 1, j, k)) +"),
     "sw_drop_y": ("AT(sw, i, j, k) = tx + ty + tz;", "AT(sw, i, j, k) = tx + tz;"),
+    "rb_black_first": ("if (((i + j + k) & 1) != color) continue;", "if (((i + j + k + 1) & 1) != color) continue;"),
+    "rb_colour_ij": ("if (((i + j + k) & 1) != color) continue;", "if (((i + j) & 1) != color) continue;"),
+    "rb_drop_source": ("s += hh * AT(f, i, j, k);\n            AT(u, i, j, k) = s / 6.0;",
+                       "s += 0.0 * AT(f, i, j, k);\n            AT(u, i, j, k) = s / 6.0;"),
 }
 
 
