@@ -325,18 +325,23 @@ def run_ours(args, rank, world, local_rank):
         return
     # ---- variants: FP32 / BF16 storage (sweeps per pass 1, 2, 4), FP64 ------
     variants = {}
-    cases = [("f64_fixed_T2", S.F64, 0, 2), ("f64_native", S.F64, S.SWEEP_FP64_NATIVE, 1)]
-    variants_work = {"f64_fixed_T2": work}
+    cases = [("f64_fixed_T2", S.F64, 0, 2), ("f64_native", S.F64, S.SWEEP_FP64_NATIVE, 1),
+             ("f64_redblack", S.F64, 0, 1)]
+    variants_work = {"f64_fixed_T2": work, "f64_redblack": work}
     for dname, dt in (("f32", S.F32), ("bf16", S.BF16)):
         for T in (1, 2, 4):
             cases.append((f"{dname}_T{T}", dt, 0, T))
+    cases.append(("f32_redblack_x2", S.F32, 0, 2))
     for name, dt, flags, T in cases:
         a, b, c = fields(dt)
         if not args.no_tune and name.endswith("_T1") and name.split("_")[0] in ("f32", "bf16"):
             tune_reports[name.split("_")[0]] = S.stencil_autotune_sweep(ctx, a, b, c, None, h)
         nsw = SWEEPS if name != "f64_native" else 200
         wk = variants_work.get(name)
-        vms = timed_steps(lambda: S.stencil_jacobi_sweep(ctx, a, b, c, wk, h, nsw, T, flags), 2, 1)
+        # red-black: T red-black sweeps per pass (2T colour stages); each
+        # sweep updates every point once
+        fn = S.stencil_redblack_sweep if "redblack" in name else S.stencil_jacobi_sweep
+        vms = timed_steps(lambda: fn(ctx, a, b, c, wk, h, nsw, T, flags), 2, 1)
         S.stencil_ctx_status(ctx)
         gl = N ** 3 * nsw / (vms * 1e-3) / 1e9
         bytes_per = ALGO_BYTES[name.split("_")[0]] / T  # HBM bytes per lattice update at T sweeps per pass
@@ -526,20 +531,25 @@ def time_to_residual(fields, n=128):
     """Seconds for `fields` k^-3 GRF Poisson problems of n^3 (seeds 20000+i),
     from zero starts, to reach relative residual 1e-8 as one job: plain FP64
     Jacobi (8 streams, residual every 200 sweeps) against the mixed-precision
-    batch solve with FP32 and with BF16 inner storage.  The FP64 residual of
-    every returned u is checked afterwards."""
+    batch solve with FP32 and with BF16 inner storage; then the same with
+    red-black Gauss-Seidel sweeps (plain FP64, and FP32 inner).  The FP64
+    residual of every returned u is checked afterwards."""
     from paper_2310_01882_b300 import inputs, warmstart
     from paper_2310_01882_b300 import stencil as S
     solver = warmstart.Solver(n, streams=8)
     fs = [S.Field.from_numpy(inputs.grf(n, seed=20000 + i)) for i in range(fields)]
     out = {"workload": f"{fields} Poisson problems {n}^3, k^-3 GRF sources, zero start, rtol 1e-8",
            "unit": "s"}
-    for kind in ("fp64", "f32", "bf16"):
+    for kind in ("fp64", "f32", "bf16", "fp64rb", "f32rb"):
         dt, sweeps, worst, ok = warmstart.solve_together(solver, fs, [None] * fields, kind)
         out[kind] = {"seconds": round(dt, 3), "sweeps_median": float(np.median(sweeps)),
                      "glups": round(n ** 3 * float(np.sum(sweeps)) / dt / 1e9, 1), "worst_rel": worst, "ok": ok}
     out["speedup_f32_vs_fp64"] = round(out["fp64"]["seconds"] / out["f32"]["seconds"], 3)
     out["speedup_bf16_vs_fp64"] = round(out["fp64"]["seconds"] / out["bf16"]["seconds"], 3)
+    # red-black Gauss-Seidel (the paper's benchmark name): plain FP64 and as
+    # the inner sweeps of the FP32 refinement
+    out["speedup_fp64rb_vs_fp64"] = round(out["fp64"]["seconds"] / out["fp64rb"]["seconds"], 3)
+    out["speedup_f32rb_vs_fp64"] = round(out["fp64"]["seconds"] / out["f32rb"]["seconds"], 3)
     return out
 
 

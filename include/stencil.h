@@ -159,6 +159,25 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
                          int32_t sweeps_per_pass, int32_t flags, void* stream);
 
 /*
+ * stencil_redblack_sweep -- nsweeps red-black Gauss-Seidel sweeps of the
+ * same Poisson relaxation (Section 4.1 names the benchmark Gauss-Seidel;
+ * the red-black ordering keeps every half sweep data parallel).  One sweep
+ * updates every interior point with i+j+k even ("red", halo indices) by
+ * u = (sum of its six neighbours + h^2 f) / 6, then every point with i+j+k
+ * odd ("black") by the same formula from the updated red values; the
+ * result equals the in-place sweeps exactly up to rounding.  It runs
+ * through the Jacobi kernel with a colour mask per stage: a pass of
+ * 2 x sweeps_per_pass stages applies sweeps_per_pass red-black sweeps while
+ * reading and writing each grid once (sweeps_per_pass 0 = 1; at most 2 for
+ * FP32/BF16 storage, 1 for F64).  Arguments, dtypes, the work grid, flags,
+ * halo handling, errors and asynchrony are those of stencil_jacobi_sweep.
+ */
+STENCIL_API int stencil_redblack_sweep(stencil_ctx* ctx, const stencil_grid* u,
+                                       const stencil_grid* u_tmp, const stencil_grid* f,
+                                       const stencil_grid* work, double h, int64_t nsweeps,
+                                       int32_t sweeps_per_pass, int32_t flags, void* stream);
+
+/*
  * stencil_autotune_sweep -- the project's autotuner for stencil_jacobi_sweep.
  * For the storage / arithmetic that (u dtype, flags, work) selects, time
  * every compiled configuration of the sweep kernel (sweeps fused per pass,
@@ -225,7 +244,8 @@ typedef struct {
   int32_t inner_dtype;       /* STENCIL_F32 or STENCIL_BF16 storage of the correction */
   int32_t sweeps_per_cycle;  /* inner sweeps per refinement cycle (0 = 100) */
   int32_t sweeps_per_pass;   /* sweeps fused per pass of the inner solve (0 = autotuned) */
-  int32_t reserved;
+  int32_t smoother;          /* inner sweeps: 0 = Jacobi, 1 = red-black Gauss-Seidel
+                                (stencil_redblack_sweep's, one sweep per pass) */
   double stall_ratio;        /* a cycle with rel > stall_ratio * previous rel escalates
                                 BF16 -> F32 storage (0 = 0.9999); F32 stalls end the
                                 instance with STENCIL_ERR_NOT_CONVERGED */
@@ -254,8 +274,9 @@ STENCIL_API int stencil_batch_workspace_size(const stencil_problem* probs, int32
  * residual rtol by mixed-precision iterative refinement: each cycle computes
  * r = f - A u and its norm in binary64 (bitwise the stencil_residual values),
  * stops an instance when ||r||/||f|| <= rtol, otherwise rounds r to the inner
- * storage type (round-to-nearest-even), runs sweeps_per_cycle Jacobi sweeps
- * of A e = r from e = 0 with binary32 arithmetic, and adds e to u in binary64.
+ * storage type (round-to-nearest-even), runs sweeps_per_cycle Jacobi (or,
+ * with opts.smoother = 1, red-black Gauss-Seidel) sweeps of A e = r from
+ * e = 0 with binary32 arithmetic, and adds e to u in binary64.
  * All active instances advance together: every pass of the inner solve is
  * one persistent launch over the tiles of all of them, and one cycle is one
  * CUDA graph (residual, check, cast, passes, update) that is replayed until
@@ -326,6 +347,14 @@ STENCIL_API int wsnet_infer(wsnet* net, const stencil_grid* f,
 STENCIL_API int wsnet_train_step(wsnet* net, const stencil_grid* f,
                                  const stencil_grid* u, int32_t count,
                                  float lr, double* loss, void* stream);
+/* Save the net's configuration and FP32 parameters to a file (8-byte magic
+ * "WSNET01", int32 levels, int32 channels[levels], int32 n, int64
+ * parameter count, the parameters in wsnet_get_params order; little
+ * endian); load them into a net created with the same levels, channels and
+ * n (STENCIL_ERR_ARG on a mismatch or an unreadable file; the net is then
+ * unchanged).  Synchronous. */
+STENCIL_API int wsnet_save(wsnet* net, const char* path);
+STENCIL_API int wsnet_load(wsnet* net, const char* path);
 /* 1 (the default): the 3x3x3 convolutions with at least 16 input and output
  * channels on grids whose rows of 16 to 128 voxels divide 128 run on the
  * tcgen05 tensor cores (accumulators in tensor memory); 0: every

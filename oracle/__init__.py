@@ -39,7 +39,7 @@ def lib():
         L.oracle_rbgs_f32.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_rbgs_bf16.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_advect_uvw.argtypes = [p, p, p, p, p, p, p, p, d, d, i64, i64, i64, i32]
-        L.oracle_refine.argtypes = [p, p, i64, i64, i64, d, d, i32, i64, i64, d, p, p, i64, p, p, p]
+        L.oracle_refine.argtypes = [p, p, i64, i64, i64, d, d, i32, i32, i64, i64, d, p, p, i64, p, p, p]
         L.oracle_refine.restype = i64
         L.oracle_num_threads.argtypes = [i32]
         L.oracle_num_threads.restype = i32
@@ -179,8 +179,9 @@ def advect_uvw(u, v, w, tzc1, tzc2, tcx, tcy, nthreads=1):
 INNER_CODES = {"f64": 0, "f32": 1, "bf16": 2}
 
 
-def refine(u0, f, h, rtol, inner="f32", m=100, max_sweeps=10 ** 7, stall_ratio=0.9999):
-    """Mixed-precision refinement (see oracle_refine).  Returns a dict with
+def refine(u0, f, h, rtol, inner="f32", m=100, max_sweeps=10 ** 7, stall_ratio=0.9999, smoother="jacobi"):
+    """Mixed-precision refinement (see oracle_refine; smoother "jacobi" or
+    "redblack" for the inner sweeps).  Returns a dict with
     u, sweeps, cycles, hist (rel of each residual evaluated), rel (final),
     final_inner and status (0 converged, -7 not converged / stalled,
     -6 non-finite)."""
@@ -193,7 +194,8 @@ def refine(u0, f, h, rtol, inner="f32", m=100, max_sweeps=10 ** 7, stall_ratio=0
     fin = np.zeros(1, dtype=np.int32)
     status = np.zeros(1, dtype=np.int32)
     work = np.zeros(6 * u.size, dtype=np.float64)
-    sweeps = lib().oracle_refine(_ptr(u), _ptr(f), nx, ny, nz, h, rtol, INNER_CODES[inner], m,
+    sweeps = lib().oracle_refine(_ptr(u), _ptr(f), nx, ny, nz, h, rtol, INNER_CODES[inner],
+                                 {"jacobi": 0, "redblack": 1}[smoother], m,
                                  max_sweeps, stall_ratio, _ptr(cycles), _ptr(hist), hist_len,
                                  _ptr(fin), _ptr(status), _ptr(work))
     c = int(cycles[0])

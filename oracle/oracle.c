@@ -338,8 +338,10 @@ void oracle_advect_uvw(const double* u, const double* v, const double* w,
  *      FP64 inner storage is never checked;
  *   4. r_lo = r rounded to the inner storage type (FP64 -> FP32 round to
  *      nearest even, then FP32 -> BF16 round to nearest even for BF16);
- *   5. e = 0, then m Jacobi sweeps of A e = r_lo with inner storage and FP32
- *      arithmetic (the sweep above with f := r_lo; FP64 for inner = F64);
+ *   5. e = 0, then m sweeps of A e = r_lo with inner storage and FP32
+ *      arithmetic (FP64 for inner = F64): Jacobi sweeps (smoother 0, the
+ *      sweep above with f := r_lo) or red-black Gauss-Seidel sweeps
+ *      (smoother 1, oracle_rbgs_* in place);
  *   6. u += e in FP64 (interior only); sweeps += m.
  * inner: 0 = F64, 1 = F32, 2 = BF16 (the library's dtype codes).  The zero
  * start is the caller's (u's interior set to 0).  u's halo is the Dirichlet
@@ -355,7 +357,7 @@ static void add_correction_f64(double* u, const double* e, int64_t nx,
 }
 
 int64_t oracle_refine(double* u, const double* f, int64_t nx, int64_t ny,
-                      int64_t nz, double h, double rtol, int inner,
+                      int64_t nz, double h, double rtol, int inner, int smoother,
                       int64_t m, int64_t max_sweeps, double stall_ratio,
                       int64_t* cycles, double* hist, int64_t hist_len,
                       int* final_inner, int* status, double* work) {
@@ -396,24 +398,36 @@ int64_t oracle_refine(double* u, const double* f, int64_t nx, int64_t ny,
     prev = rel;
     if (cur == 0) {
       memset(e64, 0, len * sizeof(double));
-      for (int64_t s = 0; s < m; ++s) {
-        oracle_jacobi_sweep_f64(e64, t64, r, nx, ny, nz, h, 1);
-        double* t = e64; e64 = t64; t64 = t;
+      if (smoother == 1) {
+        oracle_rbgs_f64(e64, r, nx, ny, nz, h, m, 1);
+      } else {
+        for (int64_t s = 0; s < m; ++s) {
+          oracle_jacobi_sweep_f64(e64, t64, r, nx, ny, nz, h, 1);
+          double* t = e64; e64 = t64; t64 = t;
+        }
       }
       add_correction_f64(u, e64, nx, ny, nz);
     } else if (cur == 1) {
       for (size_t q = 0; q < len; ++q) { r32[q] = (float)r[q]; e32[q] = 0.0f; }
-      for (int64_t s = 0; s < m; ++s) {
-        oracle_jacobi_sweep_f32(e32, t32, r32, nx, ny, nz, hh32);
-        float* t = e32; e32 = t32; t32 = t;
+      if (smoother == 1) {
+        oracle_rbgs_f32(e32, r32, nx, ny, nz, hh32, m);
+      } else {
+        for (int64_t s = 0; s < m; ++s) {
+          oracle_jacobi_sweep_f32(e32, t32, r32, nx, ny, nz, hh32);
+          float* t = e32; e32 = t32; t32 = t;
+        }
       }
       for (size_t q = 0; q < len; ++q) t64[q] = (double)e32[q];
       add_correction_f64(u, t64, nx, ny, nz);
     } else {
       for (size_t q = 0; q < len; ++q) { r16[q] = float_to_bf16((float)r[q]); e16[q] = 0; }
-      for (int64_t s = 0; s < m; ++s) {
-        oracle_jacobi_sweep_bf16(e16, t16, r16, nx, ny, nz, hh32);
-        uint16_t* t = e16; e16 = t16; t16 = t;
+      if (smoother == 1) {
+        oracle_rbgs_bf16(e16, r16, nx, ny, nz, hh32, m);
+      } else {
+        for (int64_t s = 0; s < m; ++s) {
+          oracle_jacobi_sweep_bf16(e16, t16, r16, nx, ny, nz, hh32);
+          uint16_t* t = e16; e16 = t16; t16 = t;
+        }
       }
       for (size_t q = 0; q < len; ++q) t64[q] = (double)bf16_to_float(e16[q]);
       add_correction_f64(u, t64, nx, ny, nz);

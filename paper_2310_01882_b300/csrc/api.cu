@@ -222,10 +222,15 @@ int stencil_ctx_status(stencil_ctx* ctx, void* stream) {
   return STENCIL_OK;
 }
 
-int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
-                         const stencil_grid* f, const stencil_grid* work, double h, int64_t nsweeps,
-                         int32_t sweeps_per_pass, int32_t flags, void* stream) {
-  if (!ctx) return set_error(STENCIL_ERR_ARG, "jacobi_sweep: null ctx");
+}  // extern "C"
+
+namespace {
+
+// Validation shared by the Jacobi and red-black sweep entry points.
+int sweep_call(const char* name, bool redblack, stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
+               const stencil_grid* f, const stencil_grid* work, double h, int64_t nsweeps, int32_t sweeps_per_pass,
+               int32_t flags, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "%s: null ctx", name);
   Grid gu, gt, gf, gw;
   int rc = validate_grid(u, "u", &gu, true);
   if (!rc) rc = validate_grid(u_tmp, "u_tmp", &gt, true);
@@ -235,23 +240,41 @@ int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_
   if ((rc = same_extents(gu, gt, "u", "u_tmp")) || (rc = same_extents(gu, gf, "u", "f"))) return rc;
   if (work && (rc = same_extents(gu, gw, "u", "work"))) return rc;
   if (gu.dtype != gt.dtype || gu.dtype != gf.dtype)
-    return set_error(STENCIL_ERR_DTYPE, "jacobi_sweep: u, u_tmp and f must share one dtype");
-  if (work && gw.dtype != STENCIL_F64)
-    return set_error(STENCIL_ERR_DTYPE, "jacobi_sweep: work must be F64");
+    return set_error(STENCIL_ERR_DTYPE, "%s: u, u_tmp and f must share one dtype", name);
+  if (work && gw.dtype != STENCIL_F64) return set_error(STENCIL_ERR_DTYPE, "%s: work must be F64", name);
   if (gu.data == gt.data || gu.data == gf.data || gt.data == gf.data ||
       (work && (gw.data == gu.data || gw.data == gt.data || gw.data == gf.data)))
-    return set_error(STENCIL_ERR_ARG, "jacobi_sweep: u, u_tmp, f and work must be distinct buffers");
-  if (nsweeps < 0) return set_error(STENCIL_ERR_ARG, "jacobi_sweep: nsweeps < 0");
-  if (sweeps_per_pass < 0 || sweeps_per_pass > 8)
-    return set_error(STENCIL_ERR_ARG, "jacobi_sweep: sweeps_per_pass must be 0..8");
+    return set_error(STENCIL_ERR_ARG, "%s: u, u_tmp, f and work must be distinct buffers", name);
+  if (nsweeps < 0) return set_error(STENCIL_ERR_ARG, "%s: nsweeps < 0", name);
+  const int max_pass = redblack ? 4 : 8;
+  if (sweeps_per_pass < 0 || sweeps_per_pass > max_pass)
+    return set_error(STENCIL_ERR_ARG, "%s: sweeps_per_pass must be 0..%d", name, max_pass);
   if (flags < STENCIL_SWEEP_AUTO || flags > STENCIL_SWEEP_FP64_FIXED)
-    return set_error(STENCIL_ERR_ARG, "jacobi_sweep: unknown flags %d", flags);
-  if (!(h > 0.0) || !(h < 1.0e150)) return set_error(STENCIL_ERR_ARG, "jacobi_sweep: h must be positive and finite");
+    return set_error(STENCIL_ERR_ARG, "%s: unknown flags %d", name, flags);
+  if (!(h > 0.0) || !(h < 1.0e150)) return set_error(STENCIL_ERR_ARG, "%s: h must be positive and finite", name);
   DeviceGuard dg(ctx->device);
   if (dg.rc) return dg.rc;
   const bool use_work = work && gu.dtype == STENCIL_F64;
-  return launch_jacobi(ctx, gu, gt, gf, use_work ? &gw : nullptr, h, nsweeps, sweeps_per_pass, flags,
-                       static_cast<cudaStream_t>(stream));
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (redblack)
+    return launch_redblack(ctx, gu, gt, gf, use_work ? &gw : nullptr, h, nsweeps, sweeps_per_pass, flags, st);
+  return launch_jacobi(ctx, gu, gt, gf, use_work ? &gw : nullptr, h, nsweeps, sweeps_per_pass, flags, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
+                         const stencil_grid* f, const stencil_grid* work, double h, int64_t nsweeps,
+                         int32_t sweeps_per_pass, int32_t flags, void* stream) {
+  return sweep_call("jacobi_sweep", false, ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass, flags, stream);
+}
+
+int stencil_redblack_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
+                           const stencil_grid* f, const stencil_grid* work, double h, int64_t nsweeps,
+                           int32_t sweeps_per_pass, int32_t flags, void* stream) {
+  return sweep_call("redblack_sweep", true, ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass, flags, stream);
 }
 
 static int policy_for(int32_t dtype, int32_t flags, int32_t with_work, int* policy) {

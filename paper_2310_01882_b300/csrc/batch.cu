@@ -8,9 +8,10 @@
 //      convergence / budget / stall decisions, BF16 -> F32 escalation;
 //   3. batch_resid_kernel<1>: r again, rounded to the inner storage type,
 //      and the correction e zeroed;
-//   4. sweeps_per_cycle Jacobi sweeps of A e = r_lo: each pass is one
-//      persistent launch of jacobi_tb over the tiles of all active instances
-//      (a device table of per-instance TMA descriptors, SrcBatch);
+//   4. sweeps_per_cycle Jacobi (or red-black Gauss-Seidel) sweeps of
+//      A e = r_lo: each pass is one persistent launch of jacobi_tb over the
+//      tiles of all active instances (a device table of per-instance TMA
+//      descriptors, SrcBatch);
 //   5. batch_update_kernel: u += e in binary64.
 // The cycle is captured once as a CUDA graph and replayed; after each replay
 // the host reads the number of instances still active.
@@ -325,13 +326,16 @@ Layout plan(const stencil_problem* probs, int n) {
 }
 
 // Compiled configurations of the inner sweep per storage type: (T, R, WY,
-// S, CTAs per SM).  The autotuner times each and keeps the fastest per sweep.
+// S, CTAs per SM[, red-black]).  The autotuner times each and keeps the
+// fastest per sweep.  Red-black passes hold one sweep in two colour stages.
 template <class... Cs>
 struct CfgList {};
 template <class P>
 using BatchCfgs = CfgList<TbCfg<P, 1, 8, 4, 4, 3>, TbCfg<P, 1, 8, 8, 4, 2>, TbCfg<P, 1, 4, 8, 6, 3>,
                           TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>, TbCfg<P, 2, 4, 8, 6, 2>>;
-constexpr int kNumCfg = 6;
+template <class P>
+using BatchCfgsRB = CfgList<TbCfg<P, 2, 4, 8, 6, 2, true>, TbCfg<P, 2, 8, 4, 5, 1, true>>;
+int num_cfg(bool rb) { return rb ? 2 : 6; }
 
 // Calls f(Cfg{}) for the c-th configuration of the list.
 template <class F, class... Cs>
@@ -340,18 +344,29 @@ void with_cfg(int c, CfgList<Cs...>, F&& f) {
   ((i++ == c ? (f(Cs{}), 0) : 0), ...);
 }
 
+// Calls f(Cfg{}) for configuration c of storage di (0 = F32, 1 = BF16).
+template <class F>
+void with_batch_cfg(int di, bool rb, int c, F&& f) {
+  if (di == 0) {
+    if (rb) with_cfg(c, BatchCfgsRB<PolF32>{}, f);
+    else with_cfg(c, BatchCfgs<PolF32>{}, f);
+  } else {
+    if (rb) with_cfg(c, BatchCfgsRB<PolBF16>{}, f);
+    else with_cfg(c, BatchCfgs<PolBF16>{}, f);
+  }
+}
+
 struct CfgInfo {
-  int T, BXO, BYO, BOXW, UROWS, FROWS, THREADS, SMEM;
+  int T;  // sweeps per pass
+  int BXO, BYO, BOXW, UROWS, FROWS, THREADS, SMEM;
 };
 
-CfgInfo cfg_info(int di, int c) {
+CfgInfo cfg_info(int di, bool rb, int c) {
   CfgInfo out{};
-  auto get = [&](auto cfg) {
+  with_batch_cfg(di, rb, c, [&](auto cfg) {
     using C = decltype(cfg);
-    out = CfgInfo{C::T, C::BXO, C::BYO, C::BOXW, C::UROWS, C::FROWS, C::THREADS, C::SMEM};
-  };
-  if (di == 0) with_cfg(c, BatchCfgs<PolF32>{}, get);
-  else with_cfg(c, BatchCfgs<PolBF16>{}, get);
+    out = CfgInfo{C::RB ? C::T / 2 : C::T, C::BXO, C::BYO, C::BOXW, C::UROWS, C::FROWS, C::THREADS, C::SMEM};
+  });
   return out;
 }
 
@@ -370,17 +385,15 @@ int launch_pass_cfg(const typename SrcBatch<Pol, DT>::Params& prm, int num_sms, 
   return check_cuda(cudaGetLastError(), "batch sweep launch");
 }
 
-int launch_pass(int di, int c, const InstDesc* desc, const InstState* state, const int64_t* base, int n,
+int launch_pass(int di, bool rb, int c, const InstDesc* desc, const InstState* state, const int64_t* base, int n,
                 int parity, uint32_t* status, int num_sms, cudaStream_t st) {
   int rc = 1;  // not a status: set when the configuration index matches
   if (di == 0) {
     typename SrcBatch<PolF32, 0>::Params p{desc, state, base, n, parity, status};
-    with_cfg(c, BatchCfgs<PolF32>{},
-             [&](auto cfg) { rc = launch_pass_cfg<PolF32, decltype(cfg), 0>(p, num_sms, st); });
+    with_batch_cfg(0, rb, c, [&](auto cfg) { rc = launch_pass_cfg<PolF32, decltype(cfg), 0>(p, num_sms, st); });
   } else {
     typename SrcBatch<PolBF16, 1>::Params p{desc, state, base, n, parity, status};
-    with_cfg(c, BatchCfgs<PolBF16>{},
-             [&](auto cfg) { rc = launch_pass_cfg<PolBF16, decltype(cfg), 1>(p, num_sms, st); });
+    with_batch_cfg(1, rb, c, [&](auto cfg) { rc = launch_pass_cfg<PolBF16, decltype(cfg), 1>(p, num_sms, st); });
   }
   return rc == 1 ? set_error(STENCIL_ERR_ARG, "batch: no sweep configuration %d", c) : rc;
 }
@@ -422,6 +435,7 @@ struct Solver {
   std::vector<InstDesc> desc;
   std::vector<int64_t> sbase;  // 2 x (n+1)
   int cfg[2] = {0, 0};
+  bool rb = false;             // red-black Gauss-Seidel inner sweeps
 
   InstDesc* d_desc() const { return reinterpret_cast<InstDesc*>(ws + L.desc); }
   InstState* d_state() const { return reinterpret_cast<InstState*>(ws + L.state); }
@@ -436,7 +450,7 @@ struct Solver {
   // Build tensor maps, geometry and item tables for configuration c of
   // storage di and upload them.
   int configure(int di, int c) {
-    const CfgInfo ci = cfg_info(di, c);
+    const CfgInfo ci = cfg_info(di, rb, c);
     const int elem = di == 0 ? 4 : 2;
     // z chunk: the longest (fewest re-read planes) that still gives the
     // resident CTAs (about 3 per SM) four items each over the whole batch.
@@ -466,7 +480,7 @@ struct Solver {
   }
 
   int pass(int di, int parity) {
-    return launch_pass(di, cfg[di], d_desc(), d_state(), d_sbase(di), n, parity, status(), ctx->num_sms, st);
+    return launch_pass(di, rb, cfg[di], d_desc(), d_state(), d_sbase(di), n, parity, status(), ctx->num_sms, st);
   }
 };
 
@@ -500,7 +514,7 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
     return set_error(STENCIL_ERR_DTYPE, "batch_solve: inner_dtype must be F32 or BF16");
   if (!(opts->rtol >= 0.0)) return set_error(STENCIL_ERR_ARG, "batch_solve: rtol must be >= 0");
   if (opts->sweeps_per_cycle < 0 || opts->sweeps_per_pass < 0 || opts->sweeps_per_pass > 8 ||
-      opts->max_sweeps < 0 || opts->reserved != 0)
+      opts->max_sweeps < 0 || opts->smoother < 0 || opts->smoother > 1)
     return set_error(STENCIL_ERR_ARG, "batch_solve: bad options");
   for (int i = 0; i < n; ++i) {
     Grid gu, gf;
@@ -543,6 +557,7 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
   Solver S;
   S.ctx = ctx;
   S.n = n;
+  S.rb = opts->smoother == 1;
   S.st = ctx->solve_stream;
   S.ws = static_cast<unsigned char*>(workspace);
   S.L = L;
@@ -596,8 +611,8 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
   for (int di = 0; di < (use_bf16 ? 2 : 1); ++di) {
     int best = -1;
     float best_t = 1e30f;
-    for (int c = 0; c < kNumCfg; ++c) {
-      const CfgInfo ci = cfg_info(di, c);
+    for (int c = 0; c < num_cfg(S.rb); ++c) {
+      const CfgInfo ci = cfg_info(di, S.rb, c);
       if (opts->sweeps_per_pass > 0 && ci.T != std::min(opts->sweeps_per_pass, 2)) continue;
       rc = S.configure(di, c);
       if (rc) return rc;
@@ -630,7 +645,7 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
     if (best < 0) best = 0;
     rc = S.configure(di, best);
     if (rc) return rc;
-    Tsel[di] = cfg_info(di, best).T;
+    Tsel[di] = cfg_info(di, S.rb, best).T;
   }
   rc = check_cuda(cudaMemcpyAsync(S.ws + L.state, state.data(), sizeof(InstState) * n, cudaMemcpyHostToDevice, st),
                   "upload states");

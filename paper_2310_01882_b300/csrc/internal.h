@@ -82,10 +82,14 @@ int sweep_variants(int policy, int T, const SweepVariant** out);
 int sweep_variants_f64(int policy, int T, const SweepVariant** out);
 int sweep_variants_f32(int T, const SweepVariant** out);
 int sweep_variants_bf16(int T, const SweepVariant** out);
+// Red-black Gauss-Seidel configurations (T stages = T/2 sweeps per pass).
+int sweep_variants_rb(int policy, int T, const SweepVariant** out);
 
 // Kernel launchers (jacobi.cu, residual.cu, advect.cu).
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
+int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
+                    double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
 int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,
                    int flags, char* report, size_t report_len, cudaStream_t st);
 int launch_residual(stencil_ctx* ctx, const Grid& u, const Grid& f, double h, const Grid* r,

@@ -260,6 +260,24 @@ int prepare(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, cons
 
 }  // namespace
 
+namespace {
+
+// After the last pass: the iterate is in `last` (u's buffer or u_tmp's);
+// bring it back into u (the resident policy unpacks the fixed point).
+int finish(stencil_ctx* ctx, const Prepared& P, const Grid& u, const Grid& last, bool in_tmp, cudaStream_t st) {
+  if (P.policy == kPolResident) {
+    const int64_t rows = u.ny * u.nz;
+    const int cblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 16 * ctx->num_sms));
+    fx_unpack_kernel<<<cblocks, dim3(32, 8), 0, st>>>(
+        static_cast<const unsigned long long*>(last.data), static_cast<double*>(u.data), u.nx, u.ny, u.nz,
+        last.sy, last.sz, u.sy, u.sz, P.a);
+    return check_cuda(cudaGetLastError(), "unpack kernel");
+  }
+  return in_tmp ? copy_interior_any(last, u, st) : STENCIL_OK;
+}
+
+}  // namespace
+
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
   if (nsweeps == 0) return STENCIL_OK;
@@ -277,16 +295,36 @@ int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f
     std::swap(a_in, b_out);
     left -= T;
   }
-  if (P.policy == kPolResident) {
-    const int64_t rows = u.ny * u.nz;
-    const int cblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 16 * ctx->num_sms));
-    fx_unpack_kernel<<<cblocks, dim3(32, 8), 0, st>>>(
-        static_cast<const unsigned long long*>(a_in->data), static_cast<double*>(u.data), u.nx, u.ny,
-        u.nz, a_in->sy, a_in->sz, u.sy, u.sz, P.a);
-    return check_cuda(cudaGetLastError(), "unpack kernel");
+  return finish(ctx, P, u, *a_in, a_in != &P.ui, st);
+}
+
+// nsweeps red-black Gauss-Seidel sweeps: passes of T = 2 x (sweeps per
+// pass) colour stages through the same kernel.  The fixed-point bound holds
+// as for Jacobi with 2 nsweeps half sweeps (each half sweep is an average
+// of neighbours plus h^2 f / 6, monotone in its inputs).
+int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
+                    double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
+  if (nsweeps == 0) return STENCIL_OK;
+  Prepared P;
+  int rc = prepare(ctx, u, ut, f, work, h, 2 * nsweeps, flags, true, st, &P);
+  if (rc) return rc;
+  const int want = spp > 0 ? spp : 1;
+  const Grid* a_in = &P.ui;
+  const Grid* b_out = &P.ti;
+  int64_t left = nsweeps;
+  while (left > 0) {
+    int T = 2 * static_cast<int>(std::min<int64_t>(left, want));
+    const SweepVariant* vs = nullptr;
+    int nv = 0;
+    for (; T >= 2; T -= 2)
+      if ((nv = sweep_variants_rb(P.policy, T, &vs)) > 0) break;
+    if (nv < 1) return set_error(STENCIL_ERR_ARG, "no compiled red-black configuration");
+    rc = vs[0].fn(ctx, *a_in, *b_out, P.fi, P.a, st);
+    if (rc) return rc;
+    std::swap(a_in, b_out);
+    left -= T / 2;
   }
-  if (a_in != &P.ui) rc = copy_interior_any(*a_in, u, st);
-  return rc;
+  return finish(ctx, P, u, *a_in, a_in != &P.ui, st);
 }
 
 int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,

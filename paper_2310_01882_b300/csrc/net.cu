@@ -14,9 +14,13 @@
 // are kept in FP32 (Adam) and mirrored to bfloat16 in two layouts: W[co][k]
 // with k = tap*Cin + ci (forward) and Wt[ci][k'] with k' = (26-tap)*Cout + co
 // (the input gradient is the forward convolution with flipped, transposed
-// weights).  The convolutions are implicit GEMMs on mma.sync m16n8k16 BF16.
+// weights).  The convolutions and weight gradients are implicit GEMMs on the
+// tcgen05 tensor cores (conv_tc.cuh) where the layer's channels and row
+// length allow it, and on mma.sync m16n8k16 otherwise (the one-channel first
+// layer, grids with rows shorter than 16 voxels).
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -1082,6 +1086,55 @@ extern "C" int wsnet_set_params(wsnet* w, const float* host, int64_t count) {
   if (!rc) rc = mirror(w, nullptr);
   if (!rc) rc = check_cuda(cudaDeviceSynchronize(), "wsnet_set_params sync");
   return rc;
+}
+
+// File layout of wsnet_save / wsnet_load (little endian): 8 bytes "WSNET01\0",
+// int32 levels, int32 channels[levels], int32 n, int64 parameter count,
+// then the FP32 parameters in wsnet_get_params order.
+static const char kWsMagic[8] = {'W', 'S', 'N', 'E', 'T', '0', '1', 0};
+
+extern "C" int wsnet_save(wsnet* w, const char* path) {
+  if (!w || !path) return set_error(STENCIL_ERR_ARG, "wsnet_save: bad arguments");
+  std::vector<float> host(static_cast<size_t>(w->nparams));
+  int rc = wsnet_get_params(w, host.data(), w->nparams);
+  if (rc) return rc;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return set_error(STENCIL_ERR_ARG, "wsnet_save: cannot open %s", path);
+  const int32_t hdr[2] = {w->L, w->n};
+  bool ok = fwrite(kWsMagic, 1, 8, fp) == 8 && fwrite(&hdr[0], 4, 1, fp) == 1;
+  for (int l = 0; l < w->L && ok; ++l) {
+    const int32_t c = w->C[l];
+    ok = fwrite(&c, 4, 1, fp) == 1;
+  }
+  const int64_t cnt = w->nparams;
+  ok = ok && fwrite(&hdr[1], 4, 1, fp) == 1 && fwrite(&cnt, 8, 1, fp) == 1 &&
+       fwrite(host.data(), sizeof(float), host.size(), fp) == host.size();
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? STENCIL_OK : set_error(STENCIL_ERR_ARG, "wsnet_save: write to %s failed", path);
+}
+
+extern "C" int wsnet_load(wsnet* w, const char* path) {
+  if (!w || !path) return set_error(STENCIL_ERR_ARG, "wsnet_load: bad arguments");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return set_error(STENCIL_ERR_ARG, "wsnet_load: cannot open %s", path);
+  char magic[8];
+  int32_t L = 0, n = 0;
+  int64_t cnt = 0;
+  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kWsMagic, 8) == 0 && fread(&L, 4, 1, fp) == 1 &&
+            L == w->L;
+  for (int l = 0; l < L && ok; ++l) {
+    int32_t c = 0;
+    ok = fread(&c, 4, 1, fp) == 1 && c == w->C[l];
+  }
+  ok = ok && fread(&n, 4, 1, fp) == 1 && n == w->n && fread(&cnt, 8, 1, fp) == 1 && cnt == w->nparams;
+  std::vector<float> host;
+  if (ok) {
+    host.resize(static_cast<size_t>(cnt));
+    ok = fread(host.data(), sizeof(float), host.size(), fp) == host.size();
+  }
+  fclose(fp);
+  if (!ok) return set_error(STENCIL_ERR_ARG, "wsnet_load: %s is not a file of a net of this configuration", path);
+  return wsnet_set_params(w, host.data(), cnt);
 }
 
 extern "C" int wsnet_infer(wsnet* w, const stencil_grid* f, const stencil_grid* u, void* stream) {

@@ -45,7 +45,7 @@ class stencil_problem(ctypes.Structure):
 class stencil_batch_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_sweeps", ctypes.c_int64), ("inner_dtype", ctypes.c_int32),
                 ("sweeps_per_cycle", ctypes.c_int32), ("sweeps_per_pass", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
+                ("smoother", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
 
 
 class stencil_result(ctypes.Structure):
@@ -66,6 +66,8 @@ SIGNATURES = {
     "stencil_ctx_status": ([_P, _P], ctypes.c_int),
     "stencil_jacobi_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                               ctypes.c_int32, _P], ctypes.c_int),
+    "stencil_redblack_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_int32, _P], ctypes.c_int),
     "stencil_residual": ([_P, _G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
     "stencil_advect_uvw": ([_P, _G, _G, _G, _G, _G, _G, _P, _P, ctypes.c_double, ctypes.c_double, _P],
                            ctypes.c_int),
@@ -86,6 +88,8 @@ SIGNATURES = {
     "wsnet_train_step": ([_P, _G, _G, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_double), _P],
                          ctypes.c_int),
     "wsnet_use_tcgen05": ([_P, ctypes.c_int32], ctypes.c_int),
+    "wsnet_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "wsnet_load": ([_P, ctypes.c_char_p], ctypes.c_int),
     "wsnet_status": ([_P, _P], ctypes.c_int),
     "wsnet_loss_grad": ([_P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "stencil_batch_workspace_size": ([ctypes.POINTER(stencil_problem), ctypes.c_int32,
@@ -213,6 +217,17 @@ def stencil_jacobi_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, 
                                              _stream(stream)))
 
 
+def stencil_redblack_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, flags=SWEEP_AUTO,
+                           stream=None):
+    """Red-black Gauss-Seidel sweeps; arguments as stencil_jacobi_sweep."""
+    gu, gt, gf = u.grid(), u_tmp.grid(), f.grid()
+    gw = work.grid() if work is not None else None
+    return _check(lib().stencil_redblack_sweep(ctx.handle, ctypes.byref(gu), ctypes.byref(gt), ctypes.byref(gf),
+                                               ctypes.byref(gw) if gw is not None else None,
+                                               float(h), int(nsweeps), int(sweeps_per_pass), int(flags),
+                                               _stream(stream)))
+
+
 def stencil_autotune_sweep(ctx, u, u_tmp, f, work, h, flags=SWEEP_AUTO, stream=None):
     """Time every compiled sweep configuration on these grids and keep the
     fastest in ctx (see include/stencil.h).  Returns the text report."""
@@ -280,7 +295,7 @@ def stencil_batch_workspace_size(us, fs, hs):
 
 
 def stencil_batch_solve(ctx, us, fs, hs, rtol, inner_dtype=F32, max_sweeps=0, sweeps_per_cycle=0,
-                        sweeps_per_pass=0, stall_ratio=0.0, workspace=None, stream=None):
+                        sweeps_per_pass=0, stall_ratio=0.0, workspace=None, stream=None, smoother=0):
     """Solve the instances (F64 Fields us, fs; spacings hs) in place.
     workspace: a CUDA tensor of >= stencil_batch_workspace_size bytes (one is
     allocated if None).  Returns a list of dicts (sweeps, cycles, status,
@@ -292,7 +307,7 @@ def stencil_batch_solve(ctx, us, fs, hs, rtol, inner_dtype=F32, max_sweeps=0, sw
         workspace = torch.empty(need, dtype=torch.uint8, device=us[0].storage.device)
     assert workspace.numel() * workspace.element_size() >= need
     opts = stencil_batch_opts(float(rtol), int(max_sweeps), int(inner_dtype), int(sweeps_per_cycle),
-                              int(sweeps_per_pass), 0, float(stall_ratio))
+                              int(sweeps_per_pass), int(smoother), float(stall_ratio))
     res = (stencil_result * len(us))()
     _check(lib().stencil_batch_solve(ctx.handle, arr, len(us), ctypes.byref(opts),
                                      ctypes.c_void_p(workspace.data_ptr()), need, res, _stream(stream)))
@@ -332,6 +347,14 @@ class WsNet:
             self.close()
         except Exception:
             pass
+
+
+def wsnet_save(net, path):
+    return _check(lib().wsnet_save(net.handle, os.fsencode(path)))
+
+
+def wsnet_load(net, path):
+    return _check(lib().wsnet_load(net.handle, os.fsencode(path)))
 
 
 def wsnet_use_tcgen05(net, enable):

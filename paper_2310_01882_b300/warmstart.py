@@ -48,7 +48,7 @@ class Solver:
         self.work = [S.Field(n, n, n) for _ in range(streams)]
         self.norms = torch.zeros((streams, 2), dtype=torch.float64, device="cuda")
 
-    def solve(self, us, fs, chunk=1000, max_sweeps=2_000_000):
+    def solve(self, us, fs, chunk=1000, max_sweeps=2_000_000, redblack=False):
         """Sweep every u (F64 Fields, in place) until its relative residual is
         <= RTOL, checking every `chunk` sweeps.  The streams work through the
         instances as a queue: a stream whose instance has finished takes the
@@ -78,8 +78,9 @@ class Solver:
                     out[i] = (sweeps[i], float(rel))
                     slot[j] = None
                     continue
-                S.stencil_jacobi_sweep(self.ctxs[j], us[i], self.tmp[j], fs[i], self.work[j], self.h, chunk,
-                                       0, S.SWEEP_AUTO, stream=self.streams[j])
+                sweep = S.stencil_redblack_sweep if redblack else S.stencil_jacobi_sweep
+                sweep(self.ctxs[j], us[i], self.tmp[j], fs[i], self.work[j], self.h, chunk, 0, S.SWEEP_AUTO,
+                      stream=self.streams[j])
                 sweeps[i] += chunk
 
 
@@ -171,9 +172,10 @@ def evaluate(net, solver, seeds, chunk=200, judge_sweeps=50):
 def solve_together(solver, fs, starts, kind, chunk=200, sweeps_per_cycle=400):
     """Bring every field to RTOL together (throughput: the fields are solved
     as one job) and time it.  kind "fp64": plain FP64 Jacobi on the
-    solver's streams, residual checked every `chunk` sweeps; "f32"/"bf16":
-    stencil_batch_solve with that inner storage, every active instance in
-    one persistent launch per pass.  starts: list of None (zero) or F64
+    solver's streams, residual checked every `chunk` sweeps ("fp64rb":
+    red-black Gauss-Seidel); "f32"/"bf16": stencil_batch_solve with that
+    inner storage, every active instance in one persistent launch per pass
+    ("f32rb": red-black inner sweeps).  starts: list of None (zero) or F64
     storage tensors to copy.  Returns (seconds, sweeps list, max rel, ok)."""
     import torch
     n, h = solver.n, solver.h
@@ -185,17 +187,17 @@ def solve_together(solver, fs, starts, kind, chunk=200, sweeps_per_cycle=400):
         us.append(u)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    if kind == "fp64":
-        info = solver.solve(us, fs, chunk=chunk)
+    if kind in ("fp64", "fp64rb"):
+        info = solver.solve(us, fs, chunk=chunk, redblack=(kind == "fp64rb"))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         sweeps = [sw for sw, _ in info]
         rels = [rel for _, rel in info]
         ok = all(r <= RTOL for r in rels)
     else:
-        inner = S.F32 if kind == "f32" else S.BF16
+        inner = S.BF16 if kind.startswith("bf16") else S.F32
         res = S.stencil_batch_solve(solver.ctxs[0], us, fs, [h] * len(us), RTOL, inner_dtype=inner,
-                                    sweeps_per_cycle=sweeps_per_cycle)
+                                    sweeps_per_cycle=sweeps_per_cycle, smoother=int(kind.endswith("rb")))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         sweeps = [r["sweeps"] for r in res]

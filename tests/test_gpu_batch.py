@@ -26,14 +26,16 @@ def make_batch(sizes, seed0):
     return us, fs, hs, f_np
 
 
+@pytest.mark.parametrize("smoother", ["jacobi", "redblack"])
 @pytest.mark.parametrize("inner,name", [(S.F32, "f32"), (S.BF16, "bf16")])
-def test_batch_matches_refinement_oracle(inner, name):
+def test_batch_matches_refinement_oracle(inner, name, smoother):
     import torch
     us, fs, hs, f_np = make_batch(SIZES, 100)
-    res = S.stencil_batch_solve(ctx(), us, fs, hs, 1e-8, inner_dtype=inner, sweeps_per_cycle=40)
+    res = S.stencil_batch_solve(ctx(), us, fs, hs, 1e-8, inner_dtype=inner, sweeps_per_cycle=40,
+                                smoother={"jacobi": 0, "redblack": 1}[smoother])
     torch.cuda.synchronize()
     for q, (u, f, h, r) in enumerate(zip(us, f_np, hs, res)):
-        ref = oracle.refine(np.zeros_like(f), f, h, 1e-8, inner=name, m=40)
+        ref = oracle.refine(np.zeros_like(f), f, h, 1e-8, inner=name, m=40, smoother=smoother)
         got = u.to_numpy()
         nr, nf = oracle.residual(got, f, h)
         assert r["status"] == 0 and ref["status"] == 0, (q, r, ref["status"])

@@ -161,3 +161,29 @@ def test_training_reduces_loss():
     losses = [S.wsnet_train_step(net, fs, us, 2e-3) for _ in range(40)]
     assert losses[-1] < 0.3 * losses[0], losses[::8]
     net.close()
+
+
+def test_save_load_roundtrip(tmp_path):
+    """wsnet_save / wsnet_load restore the parameters bit for bit (and the
+    inference with them); a net of another shape refuses the file."""
+    import torch
+    n = 16
+    a = S.WsNet(2, [16, 32], n, seed=21)
+    b = S.WsNet(2, [16, 32], n, seed=22)
+    path = str(tmp_path / "net.bin")
+    S.wsnet_save(a, path)
+    S.wsnet_load(b, path)
+    assert np.array_equal(a.get_params(), b.get_params())
+    f = S.Field.from_numpy(inputs.grf(n, seed=4))
+    ua, ub = S.Field(n, n, n), S.Field(n, n, n)
+    S.wsnet_infer(a, f, ua)
+    S.wsnet_infer(b, f, ub)
+    torch.cuda.synchronize()
+    assert np.array_equal(ua.to_numpy(), ub.to_numpy())
+    c = S.WsNet(2, [16, 16], n, seed=23)
+    before = c.get_params()
+    with pytest.raises(S.StencilError):
+        S.wsnet_load(c, path)
+    assert np.array_equal(before, c.get_params())
+    for net in (a, b, c):
+        net.close()

@@ -85,3 +85,29 @@ def test_nonfinite_source_reported():
     f[3, 3, 3] = np.nan
     res = oracle.refine(np.zeros_like(f), f, 1.0 / 7, rtol=1e-8)
     assert res["status"] == -6 and res["sweeps"] == 0
+
+
+def test_redblack_f64_inner_equals_plain_redblack():
+    """The same restart argument holds for any stationary linear iteration,
+    so red-black inner sweeps with FP64 storage reproduce plain red-black
+    Gauss-Seidel iterates."""
+    n = 10
+    f = inputs.grf(n, seed=24)
+    h = 1.0 / (n + 1)
+    res = oracle.refine(np.zeros_like(f), f, h, rtol=0.0, inner="f64", m=5, max_sweeps=40, smoother="redblack")
+    assert res["sweeps"] == 40 and res["cycles"] == 8 and res["status"] == -7
+    plain = oracle.rbgs(np.zeros_like(f), f, h, 40)
+    assert np.max(np.abs(res["u"] - plain)) <= 1e-13 * np.max(np.abs(plain))
+
+
+def test_redblack_f32_inner_reaches_target_in_about_half_the_sweeps():
+    n = 12
+    f = inputs.grf(n, seed=25)
+    h = 1.0 / (n + 1)
+    jac = oracle.refine(np.zeros_like(f), f, h, rtol=1e-8, inner="f32", m=20)
+    rb = oracle.refine(np.zeros_like(f), f, h, rtol=1e-8, inner="f32", m=20, smoother="redblack")
+    assert rb["status"] == 0 and jac["status"] == 0
+    nr, nf = oracle.residual(rb["u"], f, h)
+    assert nr / nf <= 1e-8
+    # the asymptotic rate of red-black is the square of Jacobi's
+    assert 0.4 * jac["sweeps"] <= rb["sweeps"] <= 0.6 * jac["sweeps"], (rb["sweeps"], jac["sweeps"])
