@@ -22,7 +22,7 @@
 #include <vector>
 
 #include "internal.h"
-#include "sweep_kernel.cuh"
+#include "sweep_rb_kernel.cuh"
 
 namespace stencil {
 
@@ -326,15 +326,15 @@ Layout plan(const stencil_problem* probs, int n) {
 }
 
 // Compiled configurations of the inner sweep per storage type: (T, R, WY,
-// S, CTAs per SM[, red-black]).  The autotuner times each and keeps the
-// fastest per sweep.  Red-black passes hold one sweep in two colour stages.
+// S, CTAs per SM).  The autotuner times each and keeps the fastest per
+// sweep.  Red-black passes (RbCfg) hold one sweep per two colour stages.
 template <class... Cs>
 struct CfgList {};
 template <class P>
 using BatchCfgs = CfgList<TbCfg<P, 1, 8, 4, 4, 3>, TbCfg<P, 1, 8, 8, 4, 2>, TbCfg<P, 1, 4, 8, 6, 3>,
                           TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>, TbCfg<P, 2, 4, 8, 6, 2>>;
 template <class P>
-using BatchCfgsRB = CfgList<TbCfg<P, 2, 4, 8, 6, 2, true>, TbCfg<P, 2, 8, 4, 5, 1, true>>;
+using BatchCfgsRB = CfgList<RbCfg<P, 2, 4, 8, 6, 1>, RbCfg<P, 4, 2, 4, 7, 1>>;
 int num_cfg(bool rb) { return rb ? 2 : 6; }
 
 // Calls f(Cfg{}) for the c-th configuration of the list.
@@ -372,7 +372,7 @@ CfgInfo cfg_info(int di, bool rb, int c) {
 
 template <class Pol, class Cfg, int DT>
 int launch_pass_cfg(const typename SrcBatch<Pol, DT>::Params& prm, int num_sms, cudaStream_t st) {
-  auto kern = jacobi_tb<Pol, Cfg, SrcBatch<Pol, DT>>;
+  auto kern = sweep_kernel_for<Pol, Cfg, SrcBatch<Pol, DT>>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
   if (e != cudaSuccess) return check_cuda(e, "cudaFuncSetAttribute");
   e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -390,10 +390,14 @@ int launch_pass(int di, bool rb, int c, const InstDesc* desc, const InstState* s
   int rc = 1;  // not a status: set when the configuration index matches
   if (di == 0) {
     typename SrcBatch<PolF32, 0>::Params p{desc, state, base, n, parity, status};
-    with_batch_cfg(0, rb, c, [&](auto cfg) { rc = launch_pass_cfg<PolF32, decltype(cfg), 0>(p, num_sms, st); });
+    auto go = [&](auto cfg) { rc = launch_pass_cfg<PolF32, decltype(cfg), 0>(p, num_sms, st); };
+    if (rb) with_cfg(c, BatchCfgsRB<PolF32>{}, go);
+    else with_cfg(c, BatchCfgs<PolF32>{}, go);
   } else {
     typename SrcBatch<PolBF16, 1>::Params p{desc, state, base, n, parity, status};
-    with_batch_cfg(1, rb, c, [&](auto cfg) { rc = launch_pass_cfg<PolBF16, decltype(cfg), 1>(p, num_sms, st); });
+    auto go = [&](auto cfg) { rc = launch_pass_cfg<PolBF16, decltype(cfg), 1>(p, num_sms, st); };
+    if (rb) with_cfg(c, BatchCfgsRB<PolBF16>{}, go);
+    else with_cfg(c, BatchCfgs<PolBF16>{}, go);
   }
   return rc == 1 ? set_error(STENCIL_ERR_ARG, "batch: no sweep configuration %d", c) : rc;
 }

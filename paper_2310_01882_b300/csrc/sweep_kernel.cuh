@@ -1,8 +1,7 @@
 // sweep_kernel.cuh -- the 7-point Jacobi sweep kernel template (Section 4.1's
 // relaxation in the Poisson form, applied out of place as a stencil apply is,
-// Section 2.2), with temporal blocking: T sweeps per pass over HBM.  With a
-// colour mask per stage the same kernel runs red-black Gauss-Seidel sweeps
-// (Section 4.1's benchmark name; see TbCfg::RB).
+// Section 2.2), with temporal blocking: T sweeps per pass over HBM.  Its
+// red-black Gauss-Seidel sibling is sweep_rb_kernel.cuh.
 //
 // jacobi_tb<Policy, Cfg, Src>: one kernel for every storage / arithmetic
 // policy (policies.cuh) and every work source: a single grid (SrcGrid) or a
@@ -58,15 +57,10 @@ __device__ __forceinline__ Item decode_item(const SweepGeom& g, int64_t item) {
   return t;
 }
 
-// RB_: red-black Gauss-Seidel instead of Jacobi.  Stage t then updates only
-// the points of colour (t-1) mod 2 (colour = (i+j+k) mod 2, red = 0) and
-// carries the others over, so a pass of T stages is T/2 red-black sweeps
-// (each half sweep reads the other colour, which the previous stage holds).
-template <class Pol, int T_, int R_, int WY_, int S_, int MINB_, bool RB_ = false>
+template <class Pol, int T_, int R_, int WY_, int S_, int MINB_>
 struct TbCfg {
   static constexpr int T = T_, R = R_, WY = WY_, S = S_, MINB = MINB_;
-  static constexpr bool RB = RB_;
-  static_assert(!RB || T % 2 == 0, "a red-black pass holds whole sweeps");
+  static constexpr bool RB = false;
   static constexpr int A = 16 / Pol::kElem;      // TMA x granule in elements
   static constexpr int BOXW = 32 + A;            // staged columns (any 0 <= off < A)
   static constexpr int BXO = 32 - 2 * T;         // output columns per tile
@@ -178,7 +172,7 @@ template <class Pol, class Cfg, int ROT>
 __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename Pol::K& k,
                                         const unsigned char* ring, int slot, uint32_t seq, int j,
                                         int p, int row0, int lane, int off, bool xin, uint32_t ymask,
-                                        int pb, typename Pol::T* orow0, int64_t sy, int64_t sz, int nz) {
+                                        typename Pol::T* orow0, int64_t sy, int64_t sz, int nz) {
   using T = typename Pol::T;
   using C = typename Pol::C;
   constexpr int TT = Cfg::T, S = Cfg::S;
@@ -215,10 +209,8 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
       const C xp = __shfl_down_sync(0xffffffffu, c, 1);
       const int w = rr - (TT - t);  // warp row, -T..R+T-1
       const bool in = xin && zin && ((ymask >> (w + TT)) & 1u);
-      // red-black: this stage's colour only (pb: parity of x + y at w = 0)
-      const bool upd = Cfg::RB ? (in && (((pb + w + q) & 1) == ((t - 1) & 1))) : in;
       C v = c;
-      if (upd) {
+      if (in) {
         const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + lane];
         v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2],
                         st.W[t - 1][OLD][rr + 1], st.W[t - 1][NEW][rr + 1], fv, k);
@@ -282,7 +274,6 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
       ymask |= (y >= 1 && y <= v.ny) ? (1u << (w + TT)) : 0u;
     }
     typename Pol::T* orow0 = v.out + x + (t.yo + row0) * v.sy;
-    const int pb = static_cast<int>((x + t.yo + row0) & 1);
     const int steps = (t.ze - t.zs + 1) + 2 * TT;
     const uint32_t seq0 = it;
     int j = 0;
@@ -305,7 +296,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     const int slot = wait(j);                                                                      \
     if (slot < 0) return;                                                                          \
     tb_step<Pol, Cfg, ROT>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off, xin,  \
-                           ymask, pb, orow0, v.sy, v.sz, static_cast<int>(v.nz));                  \
+                           ymask, orow0, v.sy, v.sz, static_cast<int>(v.nz));                      \
     if (j >= TT) release(seq0 + j - TT);                                                           \
     if (++j >= steps) break;                                                                       \
   }

@@ -7,7 +7,7 @@
 #include <algorithm>
 
 #include "internal.h"
-#include "sweep_kernel.cuh"
+#include "sweep_rb_kernel.cuh"
 
 namespace stencil {
 namespace {
@@ -53,7 +53,7 @@ int grid_for(K kernel, int threads, int smem, int64_t items, int num_sms, int* g
 template <class Pol, class Cfg>
 int run_tb(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, const SweepArgs& a,
            cudaStream_t st) {
-  auto kern = jacobi_tb<Pol, Cfg, SrcGrid<Pol>>;
+  auto kern = sweep_kernel_for<Pol, Cfg, SrcGrid<Pol>>();
   SingleParams<Pol> prm;
   int rc = make_tensor_map(&prm.tm_u, in, Cfg::BOXW, Cfg::UROWS);
   if (rc) return rc;

@@ -1,25 +1,33 @@
-// sweep_rb.cu -- compiled configurations of the sweep kernel for red-black
-// Gauss-Seidel (TbCfg<..., RB = true>): T = 2 stages (one red-black sweep)
-// per pass for every policy, T = 4 (two sweeps) for FP32 and BF16 storage.
-// TbCfg<policy, T, R, WY, S, CTAs per SM, red-black>.
+// sweep_rb.cu -- compiled configurations of the red-black Gauss-Seidel
+// kernel (RbCfg, sweep_rb_kernel.cuh): T = 2 colour stages (one red-black
+// sweep) per pass for every policy, T = 4 (two sweeps) for FP32 and BF16
+// storage.  RbCfg<policy, T, R, WY, S, CTAs per SM>.
 #include "sweep_launch.cuh"
 
 namespace stencil {
 
 int sweep_variants_rb(int policy, int T, const SweepVariant** out) {
   static const SweepVariant res2[] = {
-      variant<PolResident, TbCfg<PolResident, 2, 2, 4, 6, 3, true>>(),
-      variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2, true>>(),
+      variant<PolResident, RbCfg<PolResident, 2, 2, 8, 6, 1>>(),
   };
-  static const SweepVariant fix2[] = {variant<PolFixed, TbCfg<PolFixed, 2, 4, 4, 5, 2, true>>()};
-  static const SweepVariant f642[] = {variant<PolF64, TbCfg<PolF64, 2, 4, 4, 5, 2, true>>()};
+  static const SweepVariant fix2[] = {
+      variant<PolFixed, RbCfg<PolFixed, 2, 2, 8, 6, 1>>(),
+  };
+  static const SweepVariant f642[] = {
+      variant<PolF64, RbCfg<PolF64, 2, 2, 8, 6, 1>>(),
+  };
   static const SweepVariant f322[] = {
-      variant<PolF32, TbCfg<PolF32, 2, 4, 8, 6, 2, true>>(),
-      variant<PolF32, TbCfg<PolF32, 2, 8, 4, 5, 1, true>>(),
+      variant<PolF32, RbCfg<PolF32, 2, 4, 8, 6, 1>>(),
   };
-  static const SweepVariant f324[] = {variant<PolF32, TbCfg<PolF32, 4, 4, 4, 7, 1, true>>()};
-  static const SweepVariant b162[] = {variant<PolBF16, TbCfg<PolBF16, 2, 4, 8, 6, 2, true>>()};
-  static const SweepVariant b164[] = {variant<PolBF16, TbCfg<PolBF16, 4, 4, 4, 7, 1, true>>()};
+  static const SweepVariant f324[] = {
+      variant<PolF32, RbCfg<PolF32, 4, 2, 4, 7, 1>>(),
+  };
+  static const SweepVariant b162[] = {
+      variant<PolBF16, RbCfg<PolBF16, 2, 4, 8, 6, 1>>(),
+  };
+  static const SweepVariant b164[] = {
+      variant<PolBF16, RbCfg<PolBF16, 4, 2, 4, 7, 1>>(),
+  };
 #define RET(arr)             \
   {                          \
     *out = arr;              \
