@@ -183,6 +183,50 @@ def cpu_baseline(u0, f, h, budget_s=12.0):
             "sample": f"{n} FP64 Jacobi sweeps of the 512^3 grid (plain C oracle, OpenMP over z, {threads} threads)"}
 
 
+def cpu_rows(u0, f, h, winds, tzc):
+    """The oracle as it stands, timed on this host beside the GPU rows (each
+    a bounded sample): the FP64 residual of the 512^3 grid, one advection of
+    512x512x256, the 64^3 Jacobi configuration (100 sweeps, one core and all
+    cores), a 32^3 mixed-precision refinement to 1e-8 and one forward pass of
+    the warm-start U-Net on 32^3."""
+    import oracle
+    from oracle import net as onet
+    from paper_2310_01882_b300 import inputs
+    threads = oracle.num_threads(0)
+    out = {"cores": threads, "kind": "oracle"}
+    t0 = time.perf_counter()
+    oracle.residual(u0, f, h, nthreads=threads)
+    dt = time.perf_counter() - t0
+    out["residual_512cubed"] = {"seconds": round(dt, 3), "gpts": round(N ** 3 / dt / 1e9, 3)}
+    uw, vw, ww = winds
+    t0 = time.perf_counter()
+    oracle.advect_uvw(uw, vw, ww, tzc[0], tzc[1], 0.25, 0.25, nthreads=threads)
+    dt = time.perf_counter() - t0
+    pts = (uw.shape[0] - 2) * (uw.shape[1] - 2) * (uw.shape[2] - 2)
+    out["advect_512x512x256"] = {"seconds": round(dt, 3), "gpts": round(pts / dt / 1e9, 3)}
+    f64, h64 = inputs.sin_source(64)
+    u64 = inputs.uniform(64, 64, 64, seed=1)
+    for nt, key in ((1, "jacobi_64cubed_100_sweeps_1core"), (threads, "jacobi_64cubed_100_sweeps_allcores")):
+        t0 = time.perf_counter()
+        oracle.jacobi(u64, f64, h64, 100, nthreads=nt)
+        dt = time.perf_counter() - t0
+        out[key] = {"seconds": round(dt, 3), "glups": round(64 ** 3 * 100 / dt / 1e9, 3)}
+    f32c = inputs.grf(32, seed=20000)
+    t0 = time.perf_counter()
+    res = oracle.refine(np.zeros_like(f32c), f32c, 1.0 / 33, 1e-8, inner="f32", m=400)
+    dt = time.perf_counter() - t0
+    out["refine_32cubed_f32_to_1e-8"] = {"seconds": round(dt, 3), "sweeps": res["sweeps"],
+                                         "glups": round(32 ** 3 * res["sweeps"] / dt / 1e9, 3)}
+    p = onet.init_params(WS_CHANNELS, seed=1)
+    x = inputs.grf(32, seed=5)[1:-1, 1:-1, 1:-1, None]
+    t0 = time.perf_counter()
+    onet.forward(p, x, WS_CHANNELS)
+    dt = time.perf_counter() - t0
+    out["wsnet_forward_32cubed"] = {"seconds": round(dt, 3),
+                                    "tflops": round(wsnet_flops(32, WS_CHANNELS) / dt / 1e12, 4)}
+    return out
+
+
 def reference_arm(args, rank):
     """--impl reference: the CPU oracle timed on this machine's host cores."""
     if rank != 0:
@@ -361,10 +405,11 @@ def run_ours(args, rank, world, local_rank):
     del u, ut, f, work
     torch.cuda.empty_cache()
     uw, vw, ww = inputs.winds(512, 512, 256)
+    winds_np, tzc_np = (uw, vw, ww), (inputs.tzc(256, 7), inputs.tzc(256, 8))
     fu, fv, fw = (S.Field.from_numpy(a, S.F64, device=dev) for a in (uw, vw, ww))
     su, sv, sw = fu.like(), fu.like(), fu.like()
-    t1 = torch.from_numpy(inputs.tzc(256, 7)).to(dev)
-    t2 = torch.from_numpy(inputs.tzc(256, 8)).to(dev)
+    t1 = torch.from_numpy(tzc_np[0]).to(dev)
+    t2 = torch.from_numpy(tzc_np[1]).to(dev)
     ams = timed_steps(lambda: S.stencil_advect_uvw(ctx, fu, fv, fw, su, sv, sw, t1, t2, 0.25, 0.25), 5, 2)
     pts = 512 * 512 * 256
     components["advect_f64"] = {"ms": round(ams, 3), "gpts": round(pts / (ams * 1e-3) / 1e9, 2),
@@ -403,9 +448,10 @@ def run_ours(args, rank, world, local_rank):
            "h2d_bytes_per_step": int(u_host.numel() * 8 + f_host.numel() * 8),
            "d2h_bytes_per_step": int(out_host.numel() * 8)}
 
-    cpu = None
+    cpu = rows_cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(u0, f_np, h)
+        rows_cpu = cpu_rows(u0, f_np, h, winds_np, tzc_np)
 
     if rank == 0:
         line = {
@@ -422,6 +468,7 @@ def run_ours(args, rank, world, local_rank):
                          "kernel": kernel_name, "sweeps_per_launch": T_head, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": N ** 3 * ALGO_BYTES["f64"]},
             "cpu_baseline": cpu,
+            "cpu_rows": rows_cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
