@@ -415,5 +415,224 @@ __global__ void __launch_bounds__(128, 1) wgrad_tc_kernel(const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Convolution of grids whose rows are 128 voxels long, one output row
+// (M = 128 voxels) per tile, persistent CTAs.  Instead of one TMA box per
+// tap, a CTA loads for each row the three planes' halo boxes (3 rows x 130
+// voxels, one per 8-channel group) once and forms the 27 taps' A operands as
+// shifted views of them: a tap (dz, dy, dx) starts (dy * 130 + dx) voxels
+// into plane dz's box.  The operands use the unswizzled K-major layout
+// (8-voxel x 16-byte core matrices, contiguous since a box row is one
+// voxel's 8 channels), so any voxel offset is a valid start; the two
+// 8-channel halves of a 16-channel MMA chunk are one box apart (the
+// descriptor's leading byte offset).  The weights, [k/8][co][8] with
+// k = tap*CIN + ci, are loaded once per CTA with one TMA box.
+// Warp roles: 0 = TMA producer (double-buffered row boxes), 1 = MMA issuer
+// (two accumulators in tensor memory, so a row's MMAs overlap the previous
+// row's epilogue), 2..5 = epilogue (bias, skip, ReLU, bf16 store).
+template <int CIN, int COUT>
+struct RowCfg {
+  static constexpr int G = CIN / 8;              // 8-channel groups
+  static constexpr int BOXW = 130;               // voxels per box row (x = -1 .. 128)
+  static constexpr int BOX_TX = 8 * BOXW * 3 * 2;  // bytes TMA writes per box
+  static constexpr int BOX = (BOX_TX + 127) / 128 * 128;
+  static constexpr int ASTAGE = 3 * G * BOX;     // one row's boxes (3 planes x G groups)
+  static constexpr int KG = 27 * G;              // 8-wide k groups of the weights
+  static constexpr int BBYTES = 16 * COUT * KG;
+  static constexpr int BOFF = 2 * ASTAGE;        // weights after the two row stages
+  static constexpr int SMEM = 1024 + BOFF + (BBYTES + 127) / 128 * 128 + 256;
+  static constexpr int ACC_COLS = COUT < 32 ? 32 : COUT;
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;
+};
+
+struct RowParams {
+  CUtensorMap tm_in;  // activations as (8, G, W, H, D), box (8, 1, 130, 3, 1), no swizzle
+  CUtensorMap tm_w;   // weights as (8, COUT, KG), box (8, COUT, KG), no swizzle
+  const float* bias;
+  const __nv_bfloat16* skip;
+  __nv_bfloat16* out;
+  int D, H;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d_net(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+template <int CIN, int COUT, bool RELU, bool SKIP>
+__global__ void __launch_bounds__(192, 1) conv3_row_tc_kernel(const __grid_constant__ RowParams p) {
+  using Cfg = RowCfg<CIN, COUT>;
+  constexpr int G = Cfg::G;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* tail = base + Cfg::BOFF + (Cfg::BBYTES + 127) / 128 * 128;
+  const uint32_t bar_a_full = smem_addr(tail);  // [2]
+  const uint32_t bar_a_empty = bar_a_full + 16;  // [2]
+  const uint32_t bar_acc_full = bar_a_empty + 16;  // [2]
+  const uint32_t bar_acc_empty = bar_acc_full + 16;  // [2]
+  const uint32_t bar_w = bar_acc_empty + 16;
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(tail + 128);
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rows = p.D * p.H;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(bar_a_full + 8 * s, 1);
+      mbar_init(bar_a_empty + 8 * s, 1);
+      mbar_init(bar_acc_full + 8 * s, 1);
+      mbar_init(bar_acc_empty + 8 * s, 4);
+    }
+    mbar_init(bar_w, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(const_cast<uint32_t*>(tmem_slot))),
+                 "r"(Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_base = smem_addr(base);
+  const uint32_t b_base = a_base + Cfg::BOFF;
+  if (warp == 0) {
+    if (lane == 0) {
+      prefetch_tensormap(&p.tm_in);
+      prefetch_tensormap(&p.tm_w);
+      mbar_arrive_expect_tx(bar_w, Cfg::BBYTES);
+      tma_load_3d_net(b_base, &p.tm_w, 0, 0, 0, bar_w);
+      int i = 0;
+      for (int r = blockIdx.x; r < rows; r += gridDim.x, ++i) {
+        const int s = i & 1;
+        if (!mbar_wait_bounded(bar_a_empty + 8 * s, ((i >> 1) & 1) ^ 1u, p.status)) { abort_flag = 1; break; }
+        const int z0 = r / p.H, y0 = r - z0 * p.H;
+        mbar_arrive_expect_tx(bar_a_full + 8 * s, 3 * G * Cfg::BOX_TX);
+        for (int dz = 0; dz < 3; ++dz)
+          for (int g = 0; g < G; ++g)
+            tma_load_5d(a_base + s * Cfg::ASTAGE + (dz * G + g) * Cfg::BOX, &p.tm_in, 0, g, -1, y0 - 1,
+                        z0 + dz - 1, bar_a_full + 8 * s);
+      }
+      // no copy may still be landing in shared memory when the CTA exits
+      for (int q = i > 2 ? i - 2 : 0; q < i; ++q) mbar_wait_bounded(bar_a_full + 8 * (q & 1), (q >> 1) & 1, p.status);
+      mbar_wait_bounded(bar_w, 0, p.status);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(128, COUT);
+      bool ok = mbar_wait_bounded(bar_w, 0, p.status);
+      int i = 0;
+      for (int r = blockIdx.x; ok && r < rows; r += gridDim.x, ++i) {
+        const int s = i & 1, acc = i & 1;
+        if (*reinterpret_cast<volatile int*>(&abort_flag) ||
+            !mbar_wait_bounded(bar_a_full + 8 * s, (i >> 1) & 1, p.status) ||
+            !mbar_wait_bounded(bar_acc_empty + 8 * acc, ((i >> 1) & 1) ^ 1u, p.status)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + acc * Cfg::ACC_COLS;
+        const uint32_t a_row = a_base + s * Cfg::ASTAGE;
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+#pragma unroll
+          for (int kc = 0; kc < CIN / 16; ++kc) {
+            const uint32_t a = a_row + (dz * G + 2 * kc) * Cfg::BOX + (dy * Cfg::BOXW + dx) * 16;
+            const uint32_t b = b_base + (tap * G + 2 * kc) * (COUT * 16);
+            const uint64_t ad = tc_smem_desc2(a, 0, Cfg::BOX, 128);
+            const uint64_t bd = tc_smem_desc2(b, 0, COUT * 16, 128);
+            const uint32_t en = (tap > 0 || kc > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(en)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bar_a_empty + 8 * s)
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bar_acc_full + 8 * acc)
+                     : "memory");
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else {
+    // epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) ...
+    const int quarter = warp & 3;
+    const int x = quarter * 32 + lane;  // output voxel in the row
+    int i = 0;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x, ++i) {
+      const int acc = i & 1;
+      const bool ready = mbar_wait_bounded(bar_acc_full + 8 * acc, (i >> 1) & 1, p.status);
+      if (!__all_sync(0xffffffffu, ready)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t v = static_cast<int64_t>(r) * 128 + x;
+      float vals[COUT];
+#pragma unroll
+      for (int c0 = 0; c0 < COUT; c0 += 16) {
+        uint32_t q[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+              "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+            : "r"(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + acc * Cfg::ACC_COLS + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) vals[c0 + j] = __uint_as_float(q[j]);
+      }
+      // the accumulator may be reused once every epilogue warp has read it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_acc_empty + 8 * acc);
+      uint32_t packed[COUT / 2];
+#pragma unroll
+      for (int c = 0; c < COUT; c += 2) {
+        float a0 = vals[c] + p.bias[c], a1 = vals[c + 1] + p.bias[c + 1];
+        if (SKIP) {
+          a0 += __bfloat162float(p.skip[v * COUT + c]);
+          a1 += __bfloat162float(p.skip[v * COUT + c + 1]);
+        }
+        if (RELU) {
+          a0 = fmaxf(a0, 0.0f);
+          a1 = fmaxf(a1, 0.0f);
+        }
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+        packed[c / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(p.out + v * COUT);
+#pragma unroll
+      for (int q = 0; q < COUT / 8; ++q)
+        dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2], packed[4 * q + 3]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 }  // namespace net
 }  // namespace stencil

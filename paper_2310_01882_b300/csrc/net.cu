@@ -305,69 +305,212 @@ __global__ void chan_sum_reduce_kernel(const float* __restrict__ part, float* __
   }
 }
 
+// The pooling, upsampling and ReLU-mask kernels move 8 channels (16 bytes)
+// per thread; channel counts are multiples of 16.
+__device__ __forceinline__ void load8(const bf16* p, float (&f)[8]) {
+  const uint4 q = *reinterpret_cast<const uint4*>(p);
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __uint_as_float(w[i] << 16);
+    f[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+__device__ __forceinline__ void store8(bf16* p, const float (&f)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) w[i] = pack2(__float2bfloat16_rn(f[2 * i]), __float2bfloat16_rn(f[2 * i + 1]));
+  *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// 2x2x2 average pooling: coarse (D/2, H/2, W/2) from the fine grid.
 __global__ void pool2_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int D, int H, int W, int C) {
-  const int d = D / 2, h = H / 2, w = W / 2;
-  const int64_t n = static_cast<int64_t>(d) * h * w * C;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int c = static_cast<int>(i % C);
-    const int64_t v = i / C;
-    const int x = static_cast<int>(v % w), y = static_cast<int>((v / w) % h), z = static_cast<int>(v / (w * h));
-    float s = 0.0f;
+  const uint32_t d = D / 2, h = H / 2, w = W / 2, G = C / 8;
+  const uint32_t n = d * h * w * G;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t g = i % G, v = i / G;
+    const uint32_t x = v % w, y = (v / w) % h, z = v / (w * h);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int dz = 0; dz < 2; ++dz)
       for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-          s += __bfloat162float(in[((static_cast<int64_t>(2 * z + dz) * H + 2 * y + dy) * W + 2 * x + dx) * C + c]);
-    out[i] = __float2bfloat16_rn(s * 0.125f);
+        for (int dx = 0; dx < 2; ++dx) {
+          float f[8];
+          load8(in + (((2 * z + dz) * static_cast<uint64_t>(H) + 2 * y + dy) * W + 2 * x + dx) * C + 8 * g, f);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) s[k] += f[k];
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] *= 0.125f;
+    store8(out + static_cast<uint64_t>(v) * C + 8 * g, s);
   }
 }
 
 // Adjoint of pool2: every fine voxel gets g/8 of its block.
 __global__ void pool2_bwd_kernel(const bf16* __restrict__ g, bf16* __restrict__ out, int D, int H, int W, int C) {
-  const int64_t n = static_cast<int64_t>(D) * H * W * C;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int c = static_cast<int>(i % C);
-    const int64_t v = i / C;
-    const int x = static_cast<int>(v % W), y = static_cast<int>((v / W) % H), z = static_cast<int>(v / (W * H));
-    const int64_t q = ((static_cast<int64_t>(z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c;
-    out[i] = __float2bfloat16_rn(__bfloat162float(g[q]) * 0.125f);
+  const uint32_t G = C / 8;
+  const uint32_t n = static_cast<uint32_t>(D) * H * W * G;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t c8 = i % G, v = i / G;
+    const uint32_t x = v % W, y = (v / W) % H, z = v / (W * H);
+    float f[8];
+    load8(g + (((z / 2) * static_cast<uint64_t>(H / 2) + y / 2) * (W / 2) + x / 2) * C + 8 * c8, f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] *= 0.125f;
+    store8(out + static_cast<uint64_t>(v) * C + 8 * c8, f);
   }
 }
 
 // Nearest 2x upsampling: fine grid (D, H, W) from the coarse one.
 __global__ void up2_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int D, int H, int W, int C) {
-  const int64_t n = static_cast<int64_t>(D) * H * W * C;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int c = static_cast<int>(i % C);
-    const int64_t v = i / C;
-    const int x = static_cast<int>(v % W), y = static_cast<int>((v / W) % H), z = static_cast<int>(v / (W * H));
-    out[i] = in[((static_cast<int64_t>(z / 2) * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+  const uint32_t G = C / 8;
+  const uint32_t n = static_cast<uint32_t>(D) * H * W * G;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t c8 = i % G, v = i / G;
+    const uint32_t x = v % W, y = (v / W) % H, z = v / (W * H);
+    *reinterpret_cast<uint4*>(out + static_cast<uint64_t>(v) * C + 8 * c8) = *reinterpret_cast<const uint4*>(
+        in + (((z / 2) * static_cast<uint64_t>(H / 2) + y / 2) * (W / 2) + x / 2) * C + 8 * c8);
   }
 }
 
 // Adjoint of up2: coarse voxel gets the sum of its 8 fine gradients.
 __global__ void up2_bwd_kernel(const bf16* __restrict__ g, bf16* __restrict__ out, int d, int h, int w, int C) {
-  const int H = 2 * h, W = 2 * w;
-  const int64_t n = static_cast<int64_t>(d) * h * w * C;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    const int c = static_cast<int>(i % C);
-    const int64_t v = i / C;
-    const int x = static_cast<int>(v % w), y = static_cast<int>((v / w) % h), z = static_cast<int>(v / (w * h));
-    float s = 0.0f;
+  const uint32_t H = 2 * h, W = 2 * w, G = C / 8;
+  const uint32_t n = static_cast<uint32_t>(d) * h * w * G;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t c8 = i % G, v = i / G;
+    const uint32_t x = v % w, y = (v / w) % h, z = v / (w * h);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int dz = 0; dz < 2; ++dz)
       for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-          s += __bfloat162float(g[((static_cast<int64_t>(2 * z + dz) * H + 2 * y + dy) * W + 2 * x + dx) * C + c]);
-    out[i] = __float2bfloat16_rn(s);
+        for (int dx = 0; dx < 2; ++dx) {
+          float f[8];
+          load8(g + (((2 * z + dz) * static_cast<uint64_t>(H) + 2 * y + dy) * W + 2 * x + dx) * C + 8 * c8, f);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) s[k] += f[k];
+        }
+    store8(out + static_cast<uint64_t>(v) * C + 8 * c8, s);
   }
 }
 
-// g_out = (g + addend) * (act > 0), bf16 (addend may be null).
+// g_out = (g + addend) * (act > 0), bf16 (addend may be null); n a multiple of 8.
 __global__ void relu_bwd_kernel(const bf16* __restrict__ g, const bf16* __restrict__ addend,
                                 const bf16* __restrict__ act, bf16* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-    float v = __bfloat162float(g[i]);
-    if (addend) v += __bfloat162float(addend[i]);
-    out[i] = __float2bfloat16_rn(__bfloat162float(act[i]) > 0.0f ? v : 0.0f);
+  for (int64_t i = 8 * (blockIdx.x * int64_t(blockDim.x) + threadIdx.x); i < n;
+       i += 8 * int64_t(gridDim.x) * blockDim.x) {
+    float v[8], a[8];
+    load8(g + i, v);
+    load8(act + i, a);
+    if (addend) {
+      float e[8];
+      load8(addend + i, e);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] += e[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = a[k] > 0.0f ? v[k] : 0.0f;
+    store8(out + i, v);
+  }
+}
+
+// The first layer (one input channel) is too thin for the tensor cores:
+// 27 products per output channel.  Both kernels below use FP32 FMAs on the
+// bf16 inputs and bf16 weights (exact products), one voxel per thread.
+//
+// Neighbour offsets of voxel (x, y, z) in tap order (9 dz + 3 dy + dx),
+// with -1 for taps outside the grid.
+__device__ __forceinline__ void first_layer_taps(const bf16* __restrict__ in, uint32_t v, int D, int H, int W,
+                                                 float (&xv)[27]) {
+  const uint32_t x = v % W, y = (v / W) % H, z = v / (W * H);
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      const int zz = static_cast<int>(z) + dz - 1, yy = static_cast<int>(y) + dy - 1;
+      const bool row_ok = zz >= 0 && zz < D && yy >= 0 && yy < H;
+      const bf16* r = in + (static_cast<int64_t>(zz) * H + yy) * W;
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int xx = static_cast<int>(x) + dx - 1;
+        xv[9 * dz + 3 * dy + dx] = (row_ok && xx >= 0 && xx < W) ? __bfloat162float(r[xx]) : 0.0f;
+      }
+    }
+}
+
+// out[v][co] = ReLU(b[co] + sum_tap x[v + tap] W[co][tap]), COUT channels.
+template <int COUT>
+__global__ void __launch_bounds__(256) conv1_fwd_kernel(const bf16* __restrict__ in, const bf16* __restrict__ Wf,
+                                                        const float* __restrict__ bias, bf16* __restrict__ out,
+                                                        int D, int H, int W) {
+  constexpr int KP = kpad(1);
+  __shared__ float ws[COUT][27];
+  for (int i = threadIdx.x; i < COUT * 27; i += blockDim.x) ws[i / 27][i % 27] = __bfloat162float(Wf[(i / 27) * KP + i % 27]);
+  __syncthreads();
+  const uint32_t V = static_cast<uint32_t>(D) * H * W;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    float xv[27];
+    first_layer_taps(in, v, D, H, W, xv);
+#pragma unroll 1
+    for (int q = 0; q < COUT / 8; ++q) {
+      float f[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int co = 8 * q + k;
+        float a = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 27; ++t) a = fmaf(xv[t], ws[co][t], a);
+        f[k] = fmaxf(a + bias[co], 0.0f);
+      }
+      store8(out + static_cast<uint64_t>(v) * COUT + 8 * q, f);
+    }
+  }
+}
+
+// Weight-gradient partials of the first layer over chunks of voxels:
+//   P[chunk][co][tap] = sum_{v in chunk} g[v][co] x[v + tap].
+// 256 threads: warp w handles output channels 4 (w / 2) .. +3 for the
+// voxels of lane slot (w % 2) * 32 + lane, stride 64; the 64 slots are then
+// added in a fixed order (shuffle tree, then the two warps).
+template <int COUT>
+__global__ void __launch_bounds__(256) conv1_wgrad_kernel(const bf16* __restrict__ in, const bf16* __restrict__ g,
+                                                          float* __restrict__ part, int D, int H, int W, int chunk) {
+  static_assert(COUT == 16, "four channels per warp pair, eight warps");
+  constexpr int KP = kpad(1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cg = warp >> 1, slot = (warp & 1) * 32 + lane;
+  const uint32_t V = static_cast<uint32_t>(D) * H * W;
+  const uint32_t c0 = blockIdx.x * static_cast<uint32_t>(chunk);
+  const uint32_t c1 = min(c0 + static_cast<uint32_t>(chunk), V);
+  float acc[4][27];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int t = 0; t < 27; ++t) acc[c][t] = 0.0f;
+  for (uint32_t v = c0 + slot; v < c1; v += 64) {
+    float xv[27];
+    first_layer_taps(in, v, D, H, W, xv);
+    const uint2 gq = *reinterpret_cast<const uint2*>(g + static_cast<uint64_t>(v) * COUT + 4 * cg);
+    const float gv[4] = {__uint_as_float(gq.x << 16), __uint_as_float(gq.x & 0xffff0000u),
+                         __uint_as_float(gq.y << 16), __uint_as_float(gq.y & 0xffff0000u)};
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int t = 0; t < 27; ++t) acc[c][t] = fmaf(gv[c], xv[t], acc[c][t]);
+  }
+  __shared__ float red[8][4][27];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      float a = acc[c][t];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[warp][c][t] = a;
+    }
+  __syncthreads();
+  float* P = part + static_cast<int64_t>(blockIdx.x) * COUT * KP;
+  for (int i = threadIdx.x; i < COUT * 27; i += blockDim.x) {
+    const int co = i / 27, t = i % 27, w0 = 2 * (co / 4);
+    P[co * KP + t] = red[w0][co % 4][t] + red[w0 + 1][co % 4][t];
   }
 }
 
@@ -603,16 +746,74 @@ int launch_conv_tc(bool relu, bool skip, const bf16* in, const bf16* w, const fl
   return go(conv3_tc_kernel<CIN, COUT, S, false, false>);
 }
 
+// The row kernel (grids with 128-voxel rows).  Returns STENCIL_OK, an error,
+// or 1 when its tensor maps cannot be encoded (the caller then uses
+// conv3_tc_kernel).
+template <int CIN, int COUT>
+int launch_conv_row(bool relu, bool skip, const bf16* in, const bf16* w, const float* bias, const bf16* sk,
+                    bf16* out, int D, int H, int num_sms, uint32_t* status, cudaStream_t st) {
+  using Cfg = RowCfg<CIN, COUT>;
+  RowParams p;
+  const uint64_t dims_in[5] = {8, static_cast<uint64_t>(CIN / 8), 128, static_cast<uint64_t>(H),
+                               static_cast<uint64_t>(D)};
+  const uint64_t str_in[4] = {16, static_cast<uint64_t>(CIN) * 2, 128ull * CIN * 2,
+                              static_cast<uint64_t>(H) * 128 * CIN * 2};
+  const uint32_t box_in[5] = {8, 1, static_cast<uint32_t>(Cfg::BOXW), 3, 1};
+  if (encode_tiled(&p.tm_in, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(in), dims_in, str_in, box_in,
+                   CU_TENSOR_MAP_SWIZZLE_NONE))
+    return 1;
+  const uint64_t dims_w[3] = {8, static_cast<uint64_t>(COUT), static_cast<uint64_t>(Cfg::KG)};
+  const uint64_t str_w[2] = {static_cast<uint64_t>(kpad(CIN)) * 2, 16};
+  const uint32_t box_w[3] = {8, static_cast<uint32_t>(COUT), static_cast<uint32_t>(Cfg::KG)};
+  if (encode_tiled(&p.tm_w, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(w), dims_w, str_w, box_w,
+                   CU_TENSOR_MAP_SWIZZLE_NONE))
+    return 1;
+  p.bias = bias;
+  p.skip = sk;
+  p.out = out;
+  p.D = D;
+  p.H = H;
+  p.status = status;
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return check_cuda(e, "conv row attribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, Cfg::SMEM);
+    if (e != cudaSuccess) return check_cuda(e, "conv row occupancy");
+    const int grid = std::max(1, std::min(D * H, std::max(per_sm, 1) * num_sms));
+    kern<<<grid, 192, Cfg::SMEM, st>>>(p);
+    return check_cuda(cudaGetLastError(), "conv row launch");
+  };
+  if (relu && skip) return go(conv3_row_tc_kernel<CIN, COUT, true, true>);
+  if (relu) return go(conv3_row_tc_kernel<CIN, COUT, true, false>);
+  return go(conv3_row_tc_kernel<CIN, COUT, false, false>);
+}
+
 // tc_status: device status word of the tcgen05 path's bounded waits, or null
 // to use the mma.sync kernel for every layer.
 int launch_conv(int cin, int cout, bool relu, bool skip, const bf16* in, const bf16* w, const float* bias,
-                const bf16* sk, bf16* out, int D, int H, int W, uint32_t* tc_status, cudaStream_t st) {
+                const bf16* sk, bf16* out, int D, int H, int W, uint32_t* tc_status, int num_sms, cudaStream_t st) {
   const int64_t V = static_cast<int64_t>(D) * H * W;
+  // 16 input channels: the row kernel (at 32 its two row stages need 150 KB
+  // of shared memory, one CTA per SM, and the tile kernel is faster)
+  if (tc_status && W == 128 && cin == 16 && (cout == 16 || cout == 32)) {
+    int rc = 1;
+    if (cout == 16) rc = launch_conv_row<16, 16>(relu, skip, in, w, bias, sk, out, D, H, num_sms, tc_status, st);
+    else rc = launch_conv_row<16, 32>(relu, skip, in, w, bias, sk, out, D, H, num_sms, tc_status, st);
+    if (rc != 1) return rc;
+  }
   if (tc_status && tc_eligible(cin, cout, D, H, W)) {
 #define X(CI, CO) \
     if (cin == CI && cout == CO) return launch_conv_tc<CI, CO>(relu, skip, in, w, bias, sk, out, D, H, W, tc_status, st);
     X(16, 16) X(16, 32) X(16, 64) X(32, 16) X(32, 32) X(32, 64) X(64, 16) X(64, 32) X(64, 64)
 #undef X
+  }
+  if (cin == 1 && (cout == 16 || cout == 32 || cout == 64) && relu && !skip) {
+    const int g1 = static_cast<int>(std::min<int64_t>((V + 255) / 256, 16 * num_sms));
+    if (cout == 16) conv1_fwd_kernel<16><<<g1, 256, 0, st>>>(in, w, bias, out, D, H, W);
+    else if (cout == 32) conv1_fwd_kernel<32><<<g1, 256, 0, st>>>(in, w, bias, out, D, H, W);
+    else conv1_fwd_kernel<64><<<g1, 256, 0, st>>>(in, w, bias, out, D, H, W);
+    return check_cuda(cudaGetLastError(), "first-layer conv");
   }
   const int grid = static_cast<int>((V + 63) / 64);
 #define X(CI, CO)                                                                                           \
@@ -677,6 +878,14 @@ int launch_wgrad(int cin, int cout, const bf16* in, const bf16* g, float* part, 
                  uint32_t* tc_status, cudaStream_t st) {
   const int64_t V = static_cast<int64_t>(D) * H * W;
   const int chunks = static_cast<int>((V + kWgradChunk - 1) / kWgradChunk);
+  if (cin == 1 && cout == 16) {
+    conv1_wgrad_kernel<16><<<chunks, 256, 0, st>>>(in, g, part, D, H, W, kWgradChunk);
+    int rc = check_cuda(cudaGetLastError(), "first-layer wgrad");
+    if (rc) return rc;
+    wgrad_reduce_kernel<<<blocks_for(int64_t(cout) * kpad(cin)), 256, 0, st>>>(part, dW, cout, kpad(cin), 27 * cin,
+                                                                                 chunks);
+    return check_cuda(cudaGetLastError(), "wgrad reduce");
+  }
   if (tc_status && tc_eligible(cin, cout, D, H, W)) {
     int rc = STENCIL_ERR_ARG;
 #define X(CI, CO) \
@@ -755,6 +964,7 @@ struct wsnet {
   double *rms_part, *rms;
   uint32_t* status;  // device status word (bounded waits of the tensor-core kernels)
   int use_tc;        // 1: tcgen05 convolutions where eligible, 0: mma.sync everywhere
+  int num_sms;
   int64_t part_elems;
   int step;
   std::vector<void*> allocs;
@@ -796,30 +1006,32 @@ int forward(wsnet* w, cudaStream_t st) {
     const int d = w->dim[l];
     const bf16* in = w->x0;
     if (l > 0) {
-      pool2_kernel<<<blocks_for(w->V[l] * w->C[l - 1]), 256, 0, st>>>(w->b[l - 1], w->pl[l], 2 * d, 2 * d, 2 * d,
+      pool2_kernel<<<blocks_for(w->V[l] * w->C[l - 1] / 8), 256, 0, st>>>(w->b[l - 1], w->pl[l], 2 * d, 2 * d, 2 * d,
                                                                       w->C[l - 1]);
       in = w->pl[l];
     }
     const Layer& la = w->layers[li++];
     uint32_t* tcs = w->use_tc ? w->status : nullptr;
-    int rc = launch_conv(la.cin, la.cout, true, false, in, la.wf, w->p + la.boff, nullptr, w->a[l], d, d, d, tcs, st);
+    int rc = launch_conv(la.cin, la.cout, true, false, in, la.wf, w->p + la.boff, nullptr, w->a[l], d, d, d, tcs,
+                         w->num_sms, st);
     if (rc) return rc;
     const Layer& lb = w->layers[li++];
-    rc = launch_conv(lb.cin, lb.cout, true, false, w->a[l], lb.wf, w->p + lb.boff, nullptr, w->b[l], d, d, d, tcs, st);
+    rc = launch_conv(lb.cin, lb.cout, true, false, w->a[l], lb.wf, w->p + lb.boff, nullptr, w->b[l], d, d, d, tcs,
+                     w->num_sms, st);
     if (rc) return rc;
   }
   const bf16* h = w->b[L - 1];
   for (int l = L - 2; l >= 0; --l) {
     const int d = w->dim[l];
-    up2_kernel<<<blocks_for(w->V[l] * w->C[l + 1]), 256, 0, st>>>(h, w->u[l], d, d, d, w->C[l + 1]);
+    up2_kernel<<<blocks_for(w->V[l] * w->C[l + 1] / 8), 256, 0, st>>>(h, w->u[l], d, d, d, w->C[l + 1]);
     const Layer& la = w->layers[li++];
     uint32_t* tcs = w->use_tc ? w->status : nullptr;
     int rc = launch_conv(la.cin, la.cout, true, true, w->u[l], la.wf, w->p + la.boff, w->b[l], w->da[l], d, d, d, tcs,
-                         st);
+                         w->num_sms, st);
     if (rc) return rc;
     const Layer& lb = w->layers[li++];
     rc = launch_conv(lb.cin, lb.cout, true, false, w->da[l], lb.wf, w->p + lb.boff, nullptr, w->db[l], d, d, d, tcs,
-                     st);
+                     w->num_sms, st);
     if (rc) return rc;
     h = w->db[l];
   }
@@ -851,7 +1063,7 @@ int conv_backward(wsnet* w, const Layer& ly, const bf16* in, const bf16* g, bf16
   if (!rc) rc = bias_grad(w, g, V, ly.cout, w->g + ly.boff, st);
   if (!rc && gin)
     rc = launch_conv(ly.cout, ly.cin, false, false, g, ly.wt, w->zero_bias, nullptr, gin, d, d, d,
-                     w->use_tc ? w->status : nullptr, st);
+                     w->use_tc ? w->status : nullptr, w->num_sms, st);
   return rc;
 }
 
@@ -877,13 +1089,13 @@ int backward(wsnet* w, cudaStream_t st) {
     const int64_t V = w->V[l];
     const Layer& lb = w->layers[li--];
     const Layer& la = w->layers[li--];
-    relu_bwd_kernel<<<blocks_for(V * lb.cout), 256, 0, st>>>(w->gA[l], nullptr, w->db[l], w->gB[l], V * lb.cout);
+    relu_bwd_kernel<<<blocks_for(V * lb.cout / 8), 256, 0, st>>>(w->gA[l], nullptr, w->db[l], w->gB[l], V * lb.cout);
     rc = conv_backward(w, lb, w->da[l], w->gB[l], w->gA[l], d, st);
     if (rc) return rc;
-    relu_bwd_kernel<<<blocks_for(V * la.cout), 256, 0, st>>>(w->gA[l], nullptr, w->da[l], w->gs[l], V * la.cout);
+    relu_bwd_kernel<<<blocks_for(V * la.cout / 8), 256, 0, st>>>(w->gA[l], nullptr, w->da[l], w->gs[l], V * la.cout);
     rc = conv_backward(w, la, w->u[l], w->gs[l], w->gB[l], d, st);
     if (rc) return rc;
-    up2_bwd_kernel<<<blocks_for(w->V[l + 1] * la.cin), 256, 0, st>>>(w->gB[l], w->gA[l + 1], w->dim[l + 1],
+    up2_bwd_kernel<<<blocks_for(w->V[l + 1] * la.cin / 8), 256, 0, st>>>(w->gB[l], w->gA[l + 1], w->dim[l + 1],
                                                                      w->dim[l + 1], w->dim[l + 1], la.cin);
   }
   for (int l = L - 1; l >= 0; --l) {
@@ -891,15 +1103,15 @@ int backward(wsnet* w, cudaStream_t st) {
     const int64_t V = w->V[l];
     const Layer& lb = w->layers[li--];
     const Layer& la = w->layers[li--];
-    relu_bwd_kernel<<<blocks_for(V * lb.cout), 256, 0, st>>>(w->gA[l], l <= L - 2 ? w->gs[l] : nullptr, w->b[l],
+    relu_bwd_kernel<<<blocks_for(V * lb.cout / 8), 256, 0, st>>>(w->gA[l], l <= L - 2 ? w->gs[l] : nullptr, w->b[l],
                                                              w->gB[l], V * lb.cout);
     rc = conv_backward(w, lb, w->a[l], w->gB[l], w->gA[l], d, st);
     if (rc) return rc;
-    relu_bwd_kernel<<<blocks_for(V * la.cout), 256, 0, st>>>(w->gA[l], nullptr, w->a[l], w->gB[l], V * la.cout);
+    relu_bwd_kernel<<<blocks_for(V * la.cout / 8), 256, 0, st>>>(w->gA[l], nullptr, w->a[l], w->gB[l], V * la.cout);
     rc = conv_backward(w, la, l > 0 ? w->pl[l] : w->x0, w->gB[l], l > 0 ? w->gA[l] : nullptr, d, st);
     if (rc) return rc;
     if (l > 0)
-      pool2_bwd_kernel<<<blocks_for(w->V[l - 1] * la.cin), 256, 0, st>>>(w->gA[l], w->gA[l - 1], 2 * d, 2 * d,
+      pool2_bwd_kernel<<<blocks_for(w->V[l - 1] * la.cin / 8), 256, 0, st>>>(w->gA[l], w->gA[l - 1], 2 * d, 2 * d,
                                                                          2 * d, la.cin);
   }
   return check_cuda(cudaGetLastError(), "wsnet backward");
@@ -961,6 +1173,8 @@ extern "C" int wsnet_create(int device, int32_t levels, const int32_t* channels,
   w->device = device;
   w->L = levels;
   w->n = n;
+  w->num_sms = 148;
+  cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, device);
   for (int l = 0; l < levels; ++l) {
     w->C[l] = channels[l];
     w->dim[l] = n >> l;
