@@ -294,6 +294,15 @@ def run_ours(args, rank, world, local_rank):
         ms = reduce_max(e0.elapsed_time(e1), dist, dev)
         return ms / steps
 
+    if args.only == "batch":
+        # profiling runs: the 256 uneven instances, or with --grid N 32 instances of N^3
+        r = batch_throughput(max_sweeps=args.sweeps or 4000,
+                             sizes=[args.grid] * 32 if args.grid else None)
+        if rank == 0:
+            print(json.dumps({"metric": "batched mixed solve (profiling run)", **r}))
+        ctx.close()
+        return
+
     if args.only == "wsnet":
         r = wsnet_perf(N, infer_reps=args.steps, grad_reps=args.steps)
         if rank == 0:
@@ -541,7 +550,7 @@ def wsnet_perf(n=128, infer_reps=10, grad_reps=5):
             "loss_grad_ms": round(grad_ms, 3), "loss_grad_tflops": round(3 * fl / (grad_ms * 1e-3) / 1e12, 1)}
 
 
-def batch_throughput(max_sweeps=4000, sweeps_per_cycle=400):
+def batch_throughput(max_sweeps=4000, sweeps_per_cycle=400, sizes=None):
     """The batched mixed-precision solve on 256 cubic instances of sizes
     U[32,192] (seed 9; 5.98e8 interior points), sources iid U[0,1)
     (seeds 1000+i), zero start, run for a fixed budget of max_sweeps inner
@@ -552,9 +561,11 @@ def batch_throughput(max_sweeps=4000, sweeps_per_cycle=400):
     from paper_2310_01882_b300 import inputs
     from paper_2310_01882_b300 import stencil as S
     ctx = S.Context(0)
-    sizes = inputs.batch_sizes()
+    desc = f"{len(sizes)} Poisson instances of {sizes[0]}^3" if sizes else None
+    sizes = sizes or inputs.batch_sizes()
     fs = [S.Field.from_numpy(inputs.uniform(n, n, n, 1000 + i)) for i, n in enumerate(sizes)]
-    out = {"workload": "256 Poisson instances, n ~ U[32,192] (seed 9), iid U[0,1) sources, zero start",
+    out = {"workload": (desc or "256 Poisson instances, n ~ U[32,192] (seed 9)") +
+           ", iid U[0,1) sources, zero start",
            "points": int(sum(n ** 3 for n in sizes)), "max_sweeps": max_sweeps}
     for name, dt in (("f32", S.F32), ("bf16", S.BF16)):
         us = [S.Field(n, n, n) for n in sizes]
@@ -614,7 +625,7 @@ def main():
                     help="pin the headline's FP64 one-sweep configuration (index; profiling runs)")
     ap.add_argument("--grid", type=int, default=None, help="grid extent (profiling runs; default 512)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step (profiling runs; default 1000)")
-    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet"],
+    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet", "batch"],
                     help="run one dtype's step only (profiling runs)")
     ap.add_argument("--spp", type=int, default=0, help="sweeps per pass for --only runs (0 = library default)")
     ap.add_argument("--traffic", type=float, default=None,
