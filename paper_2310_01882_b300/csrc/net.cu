@@ -737,6 +737,8 @@ int launch_conv_tc(bool relu, bool skip, const bf16* in, const bf16* w, const fl
   const int grid = static_cast<int>(V / 128);
   auto go = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return check_cuda(e, "conv tc attribute");
     kern<<<grid, 128, Cfg::SMEM, st>>>(p);
     return check_cuda(cudaGetLastError(), "conv tc launch");
@@ -776,11 +778,12 @@ int launch_conv_row(bool relu, bool skip, const bf16* in, const bf16* w, const f
   p.status = status;
   auto go = [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return check_cuda(e, "conv row attribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 192, Cfg::SMEM);
-    if (e != cudaSuccess) return check_cuda(e, "conv row occupancy");
-    const int grid = std::max(1, std::min(D * H, std::max(per_sm, 1) * num_sms));
+    // two CTAs per SM: shared memory allows it for 16 input channels, and
+    // the CTAs never wait on one another (extra ones simply run later)
+    const int grid = std::max(1, std::min(D * H, 2 * num_sms));
     kern<<<grid, 192, Cfg::SMEM, st>>>(p);
     return check_cuda(cudaGetLastError(), "conv row launch");
   };
@@ -868,6 +871,8 @@ int launch_wgrad_tc(const bf16* in, const bf16* g, float* part, int chunks, int 
   const dim3 grid(chunks, (27 + Cfg::TG - 1) / Cfg::TG);
   auto kern = wgrad_tc_kernel<CIN, COUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return check_cuda(e, "wgrad tc attribute");
   kern<<<grid, 128, Cfg::SMEM, st>>>(p);
   return check_cuda(cudaGetLastError(), "wgrad tc launch");
