@@ -36,6 +36,7 @@ def lib():
         L.oracle_bf16_to_f32.argtypes = [p, p, i64]
         L.oracle_residual_f64.argtypes = [p, p, i64, i64, i64, d, p, p, i32]
         L.oracle_rbgs_f64.argtypes = [p, p, i64, i64, i64, d, i64, i32]
+        L.oracle_average2d.argtypes = [p, p, i64, i64, i64, i64]
         L.oracle_rbgs_f32.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_rbgs_bf16.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_advect_uvw.argtypes = [p, p, p, p, p, p, p, p, d, d, i64, i64, i64, i32]
@@ -122,6 +123,16 @@ def jacobi_sweep_bf16(u16, f16, h):
     nx, ny, nz = _dims(u16)
     lib().oracle_jacobi_sweep_bf16(_ptr(u16), _ptr(out), _ptr(f16), nx, ny, nz, f32_coeff(h))
     return out
+
+
+def average2d(u, nsweeps):
+    """nsweeps sweeps of the 2D four-neighbour average on every z plane;
+    returns a new field."""
+    u = np.array(u, dtype=np.float64, order="C", copy=True)
+    tmp = np.empty_like(u)
+    nx, ny, nz = _dims(u)
+    lib().oracle_average2d(_ptr(u), _ptr(tmp), nx, ny, nz, nsweeps)
+    return u
 
 
 def rbgs(u, f, h, nsweeps, nthreads=1):

@@ -162,6 +162,32 @@ void oracle_jacobi_sweep_bf16(const uint16_t* u, uint16_t* out,
 }
 
 /*
+ * The paper's running example (Section 2.2, Listing 1): each interior point
+ * of a 2D grid becomes the average of its four neighbours,
+ *   out(x, y) = (u(x-1, y) + u(x+1, y) + u(x, y-1) + u(x, y+1)) * 0.25,
+ * out of place (a stencil apply), the boundary kept.  A 3D field is taken as
+ * a stack of independent 2D planes (k = 1..nz; its z halo planes are not
+ * read).  nsweeps sweeps; the result is left in u, tmp is scratch.
+ */
+void oracle_average2d(double* u, double* tmp, int64_t nx, int64_t ny, int64_t nz, int64_t nsweeps) {
+  double* a = u;
+  double* b = tmp;
+  memcpy(b, a, field_len(nx, ny, nz) * sizeof(double));
+  for (int64_t sw = 0; sw < nsweeps; ++sw) {
+    for (int64_t k = 1; k <= nz; ++k)
+      for (int64_t j = 1; j <= ny; ++j)
+        for (int64_t i = 1; i <= nx; ++i) {
+          double s = AT(a, i - 1, j, k) + AT(a, i + 1, j, k);
+          s += AT(a, i, j - 1, k);
+          s += AT(a, i, j + 1, k);
+          AT(b, i, j, k) = s * 0.25;
+        }
+    double* t = a; a = b; b = t;
+  }
+  if (a != u) memcpy(u, a, field_len(nx, ny, nz) * sizeof(double));
+}
+
+/*
  * Red-black Gauss-Seidel.  Section 4.1 names the relaxation benchmark
  * Gauss-Seidel; with the red-black ordering every half sweep stays data
  * parallel.  One sweep updates, in place, first every interior point with
