@@ -427,6 +427,20 @@ def run_ours(args, rank, world, local_rank):
     del fu, fv, fw, su, sv, sw
     torch.cuda.empty_cache()
 
+    # ---- the paper's Listing 1: 2D four-neighbour average, 8192^2, binary64 ----
+    a2 = S.Field(8192, 8192, 1, S.F64, dev)
+    a2.storage.normal_()
+    a2t = a2.like()
+    a2ms = timed_steps(lambda: S.stencil_average2d(ctx, a2, a2t, 100), 2, 1)
+    pts2 = 8192 * 8192 * 100
+    components["average2d_8192sq_f64"] = {
+        "ms_per_sweep": round(a2ms / 100, 4), "glups": round(pts2 / (a2ms * 1e-3) / 1e9, 2),
+        "hbm_gbs": round(16 * pts2 / (a2ms * 1e-3) / 1e9, 1),
+        "frac_of_measured_hbm": round(16 * pts2 / (a2ms * 1e-3) / 1e9 / hbm_peak, 4),
+        "note": "binary64 in the order written (bitwise the definition): 4 FP64 instructions per update"}
+    del a2, a2t
+    torch.cuda.empty_cache()
+
     # ---- warm-start network (BF16 tensor-core convolutions) -----------------------
     components["wsnet_128cubed"] = wsnet_perf()
 

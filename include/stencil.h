@@ -159,6 +159,20 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
                          int32_t sweeps_per_pass, int32_t flags, void* stream);
 
 /*
+ * stencil_average2d -- the paper's running example (Section 2.2, Listing 1):
+ * nsweeps sweeps of the four-neighbour average
+ *   u'(x, y) = (u(x-1, y) + u(x+1, y) + u(x, y-1) + u(x, y+1)) * 0.25
+ * over the interior of every z plane of u (a 2D grid is nz = 1; the z halo
+ * planes are not read), out of place, the boundary kept.  Binary64 in the
+ * order written (no fused multiply-add): bitwise the definition.
+ *   u, u_tmp  F64 grids of equal extents and strides (u_tmp is scratch; its
+ *             halo is overwritten with u's); the result ends in u.
+ * Asynchronous on `stream`; argument errors as for stencil_jacobi_sweep.
+ */
+STENCIL_API int stencil_average2d(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
+                                  int64_t nsweeps, void* stream);
+
+/*
  * stencil_redblack_sweep -- nsweeps red-black Gauss-Seidel sweeps of the
  * same Poisson relaxation (Section 4.1 names the benchmark Gauss-Seidel;
  * the red-black ordering keeps every half sweep data parallel).  One sweep

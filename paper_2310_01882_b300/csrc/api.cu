@@ -271,6 +271,24 @@ int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_
   return sweep_call("jacobi_sweep", false, ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass, flags, stream);
 }
 
+int stencil_average2d(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp, int64_t nsweeps,
+                      void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "average2d: null ctx");
+  Grid gu, gt;
+  int rc = validate_grid(u, "u", &gu, false);
+  if (!rc) rc = validate_grid(u_tmp, "u_tmp", &gt, false);
+  if (rc) return rc;
+  if ((rc = same_extents(gu, gt, "u", "u_tmp"))) return rc;
+  if (gu.dtype != STENCIL_F64 || gt.dtype != STENCIL_F64)
+    return set_error(STENCIL_ERR_DTYPE, "average2d: u and u_tmp must be F64");
+  if (gu.data == gt.data) return set_error(STENCIL_ERR_ARG, "average2d: u and u_tmp must be distinct buffers");
+  if (gu.sy != gt.sy || gu.sz != gt.sz) return set_error(STENCIL_ERR_ARG, "average2d: u and u_tmp must share strides");
+  if (nsweeps < 0) return set_error(STENCIL_ERR_ARG, "average2d: nsweeps < 0");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  return launch_average2d(ctx, gu, gt, nsweeps, static_cast<cudaStream_t>(stream));
+}
+
 int stencil_redblack_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp,
                            const stencil_grid* f, const stencil_grid* work, double h, int64_t nsweeps,
                            int32_t sweeps_per_pass, int32_t flags, void* stream) {

@@ -88,6 +88,7 @@ int sweep_variants_rb(int policy, int T, const SweepVariant** out);
 // Kernel launchers (jacobi.cu, residual.cu, advect.cu).
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
+int launch_average2d(stencil_ctx* ctx, const Grid& u, const Grid& ut, int64_t nsweeps, cudaStream_t st);
 int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                     double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
 int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,

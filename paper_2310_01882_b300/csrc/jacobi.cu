@@ -278,6 +278,50 @@ int finish(stencil_ctx* ctx, const Prepared& P, const Grid& u, const Grid& last,
 
 }  // namespace
 
+namespace {
+
+// The four-neighbour average of the paper's running example (Section 2.2,
+// Listing 1) on every z plane, binary64 in the order of the definition
+// (two neighbours along x, then y-1, then y+1, times 0.25; no fused
+// multiply-add), one thread per point; neighbours come through L1.
+__global__ void __launch_bounds__(256)
+    average2d_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
+                     int64_t sy, int64_t sz) {
+  const int64_t i = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t j = 1 + blockIdx.y * int64_t(blockDim.y) + threadIdx.y;
+  if (i > nx || j > ny) return;
+  for (int64_t k = 1 + blockIdx.z; k <= nz; k += gridDim.z) {
+    const int64_t c = i + j * sy + k * sz;
+    double s = __dadd_rn(in[c - 1], in[c + 1]);
+    s = __dadd_rn(s, in[c - sy]);
+    s = __dadd_rn(s, in[c + sy]);
+    out[c] = __dmul_rn(s, 0.25);
+  }
+}
+
+}  // namespace
+
+int launch_average2d(stencil_ctx* ctx, const Grid& u, const Grid& ut, int64_t nsweeps, cudaStream_t st) {
+  (void)ctx;
+  if (nsweeps == 0) return STENCIL_OK;
+  int rc = copy_halo_any(u, ut, st);
+  if (rc) return rc;
+  const dim3 block(32, 8);
+  const dim3 grid(static_cast<unsigned>((u.nx + 31) / 32), static_cast<unsigned>((u.ny + 7) / 8),
+                  static_cast<unsigned>(std::min<int64_t>(u.nz, 65535)));
+  if (grid.y > 65535) return set_error(STENCIL_ERR_ARG, "average2d: ny too large");
+  const Grid* a = &u;
+  const Grid* b = &ut;
+  for (int64_t s = 0; s < nsweeps; ++s) {
+    average2d_kernel<<<grid, block, 0, st>>>(static_cast<const double*>(a->data), static_cast<double*>(b->data),
+                                             u.nx, u.ny, u.nz, u.sy, u.sz);
+    rc = check_cuda(cudaGetLastError(), "average2d kernel");
+    if (rc) return rc;
+    std::swap(a, b);
+  }
+  return a != &u ? copy_interior_any(*a, u, st) : STENCIL_OK;
+}
+
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
   if (nsweeps == 0) return STENCIL_OK;

@@ -66,6 +66,7 @@ SIGNATURES = {
     "stencil_ctx_status": ([_P, _P], ctypes.c_int),
     "stencil_jacobi_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                               ctypes.c_int32, _P], ctypes.c_int),
+    "stencil_average2d": ([_P, _G, _G, ctypes.c_int64, _P], ctypes.c_int),
     "stencil_redblack_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.c_int32, _P], ctypes.c_int),
     "stencil_residual": ([_P, _G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
@@ -215,6 +216,13 @@ def stencil_jacobi_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, 
                                              ctypes.byref(gw) if gw is not None else None,
                                              float(h), int(nsweeps), int(sweeps_per_pass), int(flags),
                                              _stream(stream)))
+
+
+def stencil_average2d(ctx, u, u_tmp, nsweeps, stream=None):
+    """The four-neighbour average on every z plane (F64 Fields)."""
+    gu, gt = u.grid(), u_tmp.grid()
+    return _check(lib().stencil_average2d(ctx.handle, ctypes.byref(gu), ctypes.byref(gt), int(nsweeps),
+                                          _stream(stream)))
 
 
 def stencil_redblack_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, flags=SWEEP_AUTO,
