@@ -37,6 +37,7 @@ def lib():
         L.oracle_residual_f64.argtypes = [p, p, i64, i64, i64, d, p, p, i32]
         L.oracle_rbgs_f64.argtypes = [p, p, i64, i64, i64, d, i64, i32]
         L.oracle_average2d.argtypes = [p, p, i64, i64, i64, i64]
+        L.oracle_apply_linear.argtypes = [p, p, i64, i64, i64, p, p, i32]
         L.oracle_rbgs_f32.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_rbgs_bf16.argtypes = [p, p, i64, i64, i64, f32, i64]
         L.oracle_advect_uvw.argtypes = [p, p, p, p, p, p, p, p, d, d, i64, i64, i64, i32]
@@ -133,6 +134,20 @@ def average2d(u, nsweeps):
     nx, ny, nz = _dims(u)
     lib().oracle_average2d(_ptr(u), _ptr(tmp), nx, ny, nz, nsweeps)
     return u
+
+
+def apply_linear(u, offsets, coeffs, out=None):
+    """out(x) = sum_p coeffs[p] * u(x + offsets[p]) on the interior (offsets:
+    (npoints, 3) ints dx, dy, dz in [-1, 1]); the halo of out is out's own
+    (zeros if out is None)."""
+    u = _c64(u)
+    out = np.zeros_like(u) if out is None else np.array(out, dtype=np.float64, order="C", copy=True)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    c = _c64(np.asarray(coeffs, dtype=np.float64).reshape(-1))
+    assert off.shape[0] == c.size and np.all(np.abs(off) <= 1)
+    nx, ny, nz = _dims(u)
+    lib().oracle_apply_linear(_ptr(u), _ptr(out), nx, ny, nz, _ptr(off), _ptr(c), c.size)
+    return out
 
 
 def rbgs(u, f, h, nsweeps, nthreads=1):

@@ -13,7 +13,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
 PINS = ["tests/test_oracle_jacobi.py", "tests/test_oracle_residual.py", "tests/test_oracle_advect.py",
-        "tests/test_oracle_rbgs.py", "tests/test_oracle_average2d.py"]
+        "tests/test_oracle_rbgs.py", "tests/test_oracle_average2d.py", "tests/test_oracle_apply_linear.py"]
 
 MUTANTS = {
     "sweep_z_as_y": ("s += AT(u, i, j, k + 1);\n        s += hh", "s += AT(u, i, j + 1, k);\n        s += hh"),
@@ -33,6 +33,8 @@ MUTANTS = {
     "avg2d_y_as_z": ("s += AT(a, i, j + 1, k);\n          AT(b, i, j, k) = s * 0.25;",
                      "s += AT(a, i, j, k + 1);\n          AT(b, i, j, k) = s * 0.25;"),
     "avg2d_third": ("AT(b, i, j, k) = s * 0.25;", "AT(b, i, j, k) = s * 0.3333333333333333;"),
+    "apply_axes_swapped": ("AT(in, i + offsets[3 * p], j + offsets[3 * p + 1], k + offsets[3 * p + 2])",
+                           "AT(in, i + offsets[3 * p + 1], j + offsets[3 * p], k + offsets[3 * p + 2])"),
     "rb_drop_source": ("s += hh * AT(f, i, j, k);\n            AT(u, i, j, k) = s / 6.0;",
                        "s += 0.0 * AT(f, i, j, k);\n            AT(u, i, j, k) = s / 6.0;"),
 }
