@@ -159,6 +159,24 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
                          int32_t sweeps_per_pass, int32_t flags, void* stream);
 
 /*
+ * stencil_apply_linear -- a general linear stencil apply (Section 2.2: a
+ * stencil.apply reads its input at constant offsets and yields one value
+ * per point of the output's bounds; here the body is a linear combination):
+ *   out(x, y, z) = sum_{p < npoints} coeffs[p] * in(x + dx_p, y + dy_p, z + dz_p)
+ * on the interior; each product is rounded, then added in the listed order
+ * (binary64, no fused multiply-add), so the result is bitwise that order's.
+ *   in, out   F64 grids of equal extents, distinct (out of place); out's
+ *             halo is not written.
+ *   offsets   HOST array of 3 * npoints int32 (dx, dy, dz), each in -1..1
+ *             (the one-cell halo); coeffs: HOST array of npoints doubles;
+ *             1 <= npoints <= 27.  Both are copied into the launch.
+ * Asynchronous on `stream`; STENCIL_ERR_ARG / _DTYPE on bad arguments.
+ */
+STENCIL_API int stencil_apply_linear(stencil_ctx* ctx, const stencil_grid* in, const stencil_grid* out,
+                                     const int32_t* offsets, const double* coeffs, int32_t npoints,
+                                     void* stream);
+
+/*
  * stencil_average2d -- the paper's running example (Section 2.2, Listing 1):
  * nsweeps sweeps of the four-neighbour average
  *   u'(x, y) = (u(x-1, y) + u(x+1, y) + u(x, y-1) + u(x, y+1)) * 0.25

@@ -271,6 +271,27 @@ int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u, const stencil_
   return sweep_call("jacobi_sweep", false, ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass, flags, stream);
 }
 
+int stencil_apply_linear(stencil_ctx* ctx, const stencil_grid* in, const stencil_grid* out, const int32_t* offsets,
+                         const double* coeffs, int32_t npoints, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "apply_linear: null ctx");
+  Grid gi, go;
+  int rc = validate_grid(in, "in", &gi, false);
+  if (!rc) rc = validate_grid(out, "out", &go, false);
+  if (rc) return rc;
+  if ((rc = same_extents(gi, go, "in", "out"))) return rc;
+  if (gi.dtype != STENCIL_F64 || go.dtype != STENCIL_F64)
+    return set_error(STENCIL_ERR_DTYPE, "apply_linear: in and out must be F64");
+  if (gi.data == go.data) return set_error(STENCIL_ERR_ARG, "apply_linear: in and out must be distinct (out of place)");
+  if (npoints < 1 || npoints > kMaxLinearTerms || !offsets || !coeffs)
+    return set_error(STENCIL_ERR_ARG, "apply_linear: need 1..%d terms", kMaxLinearTerms);
+  for (int p = 0; p < 3 * npoints; ++p)
+    if (offsets[p] < -1 || offsets[p] > 1)
+      return set_error(STENCIL_ERR_ARG, "apply_linear: offsets must lie in the one-cell halo (-1..1)");
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  return launch_apply_linear(ctx, gi, go, offsets, coeffs, npoints, static_cast<cudaStream_t>(stream));
+}
+
 int stencil_average2d(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp, int64_t nsweeps,
                       void* stream) {
   if (!ctx) return set_error(STENCIL_ERR_ARG, "average2d: null ctx");

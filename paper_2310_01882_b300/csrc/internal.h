@@ -89,6 +89,9 @@ int sweep_variants_rb(int policy, int T, const SweepVariant** out);
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
 int launch_average2d(stencil_ctx* ctx, const Grid& u, const Grid& ut, int64_t nsweeps, cudaStream_t st);
+constexpr int kMaxLinearTerms = 27;
+int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const int32_t* offsets,
+                        const double* coeffs, int npoints, cudaStream_t st);
 int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                     double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
 int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,

@@ -67,6 +67,7 @@ SIGNATURES = {
     "stencil_jacobi_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                               ctypes.c_int32, _P], ctypes.c_int),
     "stencil_average2d": ([_P, _G, _G, ctypes.c_int64, _P], ctypes.c_int),
+    "stencil_apply_linear": ([_P, _G, _G, _P, _P, ctypes.c_int32, _P], ctypes.c_int),
     "stencil_redblack_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.c_int32, _P], ctypes.c_int),
     "stencil_residual": ([_P, _G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
@@ -216,6 +217,17 @@ def stencil_jacobi_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, 
                                              ctypes.byref(gw) if gw is not None else None,
                                              float(h), int(nsweeps), int(sweeps_per_pass), int(flags),
                                              _stream(stream)))
+
+
+def stencil_apply_linear(ctx, inp, out, offsets, coeffs, stream=None):
+    """out = sum_p coeffs[p] * inp(. + offsets[p]) on the interior (offsets:
+    (npoints, 3) ints in -1..1; F64 Fields)."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64).reshape(-1))
+    gi, go = inp.grid(), out.grid()
+    return _check(lib().stencil_apply_linear(ctx.handle, ctypes.byref(gi), ctypes.byref(go),
+                                             ctypes.c_void_p(off.ctypes.data), ctypes.c_void_p(c.ctypes.data),
+                                             int(c.size) if c.size == off.shape[0] else -1, _stream(stream)))
 
 
 def stencil_average2d(ctx, u, u_tmp, nsweeps, stream=None):
