@@ -332,10 +332,11 @@ template <class... Cs>
 struct CfgList {};
 template <class P>
 using BatchCfgs = CfgList<TbCfg<P, 1, 8, 4, 4, 3>, TbCfg<P, 1, 8, 8, 4, 2>, TbCfg<P, 1, 4, 8, 6, 3>,
-                          TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>, TbCfg<P, 2, 4, 8, 6, 2>>;
+                          TbCfg<P, 1, 4, 4, 5, 6>, TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>,
+                          TbCfg<P, 2, 4, 8, 6, 2>, TbCfg<P, 2, 8, 4, 5, 3>, TbCfg<P, 2, 4, 4, 5, 4>>;
 template <class P>
 using BatchCfgsRB = CfgList<RbCfg<P, 2, 4, 8, 6, 1>, RbCfg<P, 4, 2, 4, 7, 1>>;
-int num_cfg(bool rb) { return rb ? 2 : 6; }
+int num_cfg(bool rb) { return rb ? 2 : 9; }
 
 // Calls f(Cfg{}) for the c-th configuration of the list.
 template <class F, class... Cs>

@@ -9,11 +9,15 @@ int sweep_variants_bf16(int T, const SweepVariant** out) {
       variant<PolBF16, TbCfg<PolBF16, 1, 8, 8, 4, 2>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 8, 4, 5, 3>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 4, 8, 6, 3>>(),
+      variant<PolBF16, TbCfg<PolBF16, 1, 4, 4, 5, 6>>(),
   };
   static const SweepVariant t2[] = {
       variant<PolBF16, TbCfg<PolBF16, 2, 8, 4, 5, 1>>(),
       variant<PolBF16, TbCfg<PolBF16, 2, 4, 8, 6, 2>>(),
       variant<PolBF16, TbCfg<PolBF16, 2, 4, 4, 6, 3>>(),
+      variant<PolBF16, TbCfg<PolBF16, 2, 8, 4, 5, 3>>(),
+      variant<PolBF16, TbCfg<PolBF16, 2, 4, 4, 5, 4>>(),
+      variant<PolBF16, TbCfg<PolBF16, 2, 2, 8, 6, 3>>(),
   };
   static const SweepVariant t4[] = {
       variant<PolBF16, TbCfg<PolBF16, 4, 4, 4, 7, 1>>(),

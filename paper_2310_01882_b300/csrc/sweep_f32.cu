@@ -9,11 +9,15 @@ int sweep_variants_f32(int T, const SweepVariant** out) {
       variant<PolF32, TbCfg<PolF32, 1, 8, 8, 4, 2>>(),
       variant<PolF32, TbCfg<PolF32, 1, 8, 4, 5, 3>>(),
       variant<PolF32, TbCfg<PolF32, 1, 4, 8, 6, 3>>(),
+      variant<PolF32, TbCfg<PolF32, 1, 4, 4, 5, 6>>(),
   };
   static const SweepVariant t2[] = {
       variant<PolF32, TbCfg<PolF32, 2, 8, 4, 5, 1>>(),
       variant<PolF32, TbCfg<PolF32, 2, 4, 8, 6, 2>>(),
       variant<PolF32, TbCfg<PolF32, 2, 4, 4, 6, 3>>(),
+      variant<PolF32, TbCfg<PolF32, 2, 8, 4, 5, 3>>(),
+      variant<PolF32, TbCfg<PolF32, 2, 4, 4, 5, 4>>(),
+      variant<PolF32, TbCfg<PolF32, 2, 2, 8, 6, 3>>(),
   };
   static const SweepVariant t4[] = {
       variant<PolF32, TbCfg<PolF32, 4, 4, 4, 7, 1>>(),
