@@ -4,10 +4,12 @@
 // One refinement cycle for every active instance:
 //   1. batch_resid_kernel<0>: r = f - A u in binary64 (the operations of
 //      stencil_residual, bitwise), per-item partial sums of r^2 and f^2;
+//      for binary32 inner storage also r rounded into the source buffer and
+//      the correction e zeroed;
 //   2. batch_check_kernel: per instance, the norms in item order, the
 //      convergence / budget / stall decisions, BF16 -> F32 escalation;
-//   3. batch_resid_kernel<1>: r again, rounded to the inner storage type,
-//      and the correction e zeroed;
+//   3. (bfloat16 runs) batch_resid_kernel<1>: r again, rounded, e zeroed,
+//      for the bfloat16 instances and those that escalated this cycle;
 //   4. sweeps_per_cycle Jacobi (or red-black Gauss-Seidel) sweeps of
 //      A e = r_lo: each pass is one persistent launch of jacobi_tb over the
 //      tiles of all active instances (a device table of per-instance TMA
@@ -109,9 +111,13 @@ struct SrcBatch {
   }
 };
 
-// MODE 0: per-item partial sums of r^2 and f^2.  MODE 1: r rounded to the
-// instance's inner storage (binary64 -> binary32 -> bfloat16, each to nearest
-// even) into its source buffer, and the interior of e (ping) zeroed.
+// MODE 0: per-item partial sums of r^2 and f^2; for the instances whose inner
+// storage is already binary32 (it can only change from bfloat16), also r
+// rounded to binary32 into the source buffer and the interior of e (ping)
+// zeroed, so r is computed once per cycle for them.  MODE 1 (after the
+// check): the same rounding and zeroing for the bfloat16 instances and for
+// those that switched to binary32 this cycle.  r is rounded binary64 ->
+// binary32 -> bfloat16, each to nearest even.
 template <int MODE>
 __global__ void __launch_bounds__(256) batch_resid_kernel(BatchTables tb) {
   const int64_t total = tb.rbase[tb.n];
@@ -120,6 +126,8 @@ __global__ void __launch_bounds__(256) batch_resid_kernel(BatchTables tb) {
     const int i = find_instance(tb.rbase, tb.n, item);
     const InstState& s = tb.state[i];
     if (!s.active) continue;
+    const bool write = MODE == 0 ? (s.dtype == STENCIL_F32) : (s.dtype == STENCIL_BF16 || s.escalated != 0);
+    if (MODE == 1 && !write) continue;
     const InstDesc& d = tb.desc[i];
     const int64_t rows = d.ny * d.nz;
     const int64_t r0 = (item - tb.rbase[i]) * kRowsPerItem;
@@ -144,7 +152,8 @@ __global__ void __launch_bounds__(256) batch_resid_kernel(BatchTables tb) {
         if (MODE == 0) {
           rr = fma(res, res, rr);
           ff = fma(fv, fv, ff);
-        } else {
+        }
+        if (write) {
           const int64_t o = x + j * d.esy[di] + k * d.esz[di];
           const float r32 = __double2float_rn(res);
           if (di == 0) {
@@ -678,9 +687,9 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
     batch_check_kernel<<<(n + 127) / 128, 128, 0, st>>>(tb, ca);
     if (use_bf16) {
       batch_rezero_kernel<<<4 * ctx->num_sms, 256, 0, st>>>(tb);
+      batch_resid_kernel<1><<<rblocks, dim3(32, 8), 0, st>>>(tb);
       batch_clear_flags_kernel<<<1, 256, 0, st>>>(tb);
     }
-    batch_resid_kernel<1><<<rblocks, dim3(32, 8), 0, st>>>(tb);
     for (int di = 0; di < (use_bf16 ? 2 : 1) && !crc; ++di) {
       const int passes = di == 0 ? passes0 : passes1;
       for (int p = 0; p < passes && !crc; ++p) crc = S.pass(di, p & 1);
