@@ -384,7 +384,7 @@ def run_ours(args, rank, world, local_rank):
     for dname, dt in (("f32", S.F32), ("bf16", S.BF16)):
         for T in (1, 2, 4):
             cases.append((f"{dname}_T{T}", dt, 0, T))
-    cases.append(("f32_redblack_x2", S.F32, 0, 2))
+    cases += [("f32_redblack", S.F32, 0, 1), ("bf16_redblack", S.BF16, 0, 1), ("f32_redblack_x2", S.F32, 0, 2)]
     for name, dt, flags, T in cases:
         a, b, c = fields(dt)
         if not args.no_tune and name.endswith("_T1") and name.split("_")[0] in ("f32", "bf16"):

@@ -245,6 +245,22 @@ STENCIL_API int stencil_sweep_config_select(stencil_ctx* ctx, int32_t dtype,
                                             int32_t T, int32_t index);
 
 /*
+ * The same for stencil_redblack_sweep: the compiled red-black tile
+ * configurations for `sweeps_per_pass` sweeps per pass (1 or 2), and the
+ * one ctx uses (index 0, the fastest measured at 512^3, unless selected).
+ * Errors: STENCIL_ERR_ARG (null count or ctx, index out of range),
+ * STENCIL_ERR_DTYPE.
+ */
+STENCIL_API int stencil_redblack_config_count(int32_t dtype, int32_t flags,
+                                              int32_t with_work,
+                                              int32_t sweeps_per_pass,
+                                              int32_t* count);
+STENCIL_API int stencil_redblack_config_select(stencil_ctx* ctx, int32_t dtype,
+                                               int32_t flags, int32_t with_work,
+                                               int32_t sweeps_per_pass,
+                                               int32_t index);
+
+/*
  * stencil_residual -- the residual of A u = f for the 7-point operator
  *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2,
  *     r = f - A u on the interior,

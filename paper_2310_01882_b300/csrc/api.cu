@@ -167,7 +167,7 @@ int stencil_ctx_create(int device, stencil_ctx** out) {
   c->device = device;
   c->num_sms = prop.multiProcessorCount;
   for (int p = 0; p < kNumPolicies; ++p) {
-    for (int t = 0; t <= kMaxPass; ++t) c->sweep_choice[p][t] = 0;
+    for (int t = 0; t <= kMaxPass; ++t) c->sweep_choice[p][t] = c->rb_choice[p][t] = 0;
     c->best_pass[p] = (p == kPolF32 || p == kPolBF16) ? 4 : 1;
   }
   c->scratch_bytes = kScratchBytes;
@@ -351,6 +351,35 @@ int stencil_sweep_config_select(stencil_ctx* ctx, int32_t dtype, int32_t flags, 
   if (index < 0 || index >= n)
     return set_error(STENCIL_ERR_ARG, "sweep_config_select: index %d out of range (%d configurations)", index, n);
   ctx->sweep_choice[policy][T] = index;
+  return STENCIL_OK;
+}
+
+int stencil_redblack_config_count(int32_t dtype, int32_t flags, int32_t with_work, int32_t sweeps_per_pass,
+                                  int32_t* count) {
+  if (!count) return set_error(STENCIL_ERR_ARG, "redblack_config_count: null count");
+  int policy = 0;
+  int rc = policy_for(dtype, flags, with_work, &policy);
+  if (rc) return rc;
+  const SweepVariant* v;
+  *count = (sweeps_per_pass >= 1 && 2 * sweeps_per_pass <= kMaxPass)
+               ? sweep_variants_rb(policy, 2 * sweeps_per_pass, &v)
+               : 0;
+  return STENCIL_OK;
+}
+
+int stencil_redblack_config_select(stencil_ctx* ctx, int32_t dtype, int32_t flags, int32_t with_work,
+                                   int32_t sweeps_per_pass, int32_t index) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "redblack_config_select: null ctx");
+  int policy = 0;
+  int rc = policy_for(dtype, flags, with_work, &policy);
+  if (rc) return rc;
+  const SweepVariant* v;
+  const int T = 2 * sweeps_per_pass;
+  const int n = (sweeps_per_pass >= 1 && T <= kMaxPass) ? sweep_variants_rb(policy, T, &v) : 0;
+  if (index < 0 || index >= n)
+    return set_error(STENCIL_ERR_ARG, "redblack_config_select: index %d out of range (%d configurations)", index,
+                     n);
+  ctx->rb_choice[policy][T] = index;
   return STENCIL_OK;
 }
 

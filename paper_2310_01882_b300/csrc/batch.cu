@@ -344,8 +344,14 @@ using BatchCfgs = CfgList<TbCfg<P, 1, 8, 4, 4, 3>, TbCfg<P, 1, 8, 8, 4, 2>, TbCf
                           TbCfg<P, 1, 4, 4, 5, 6>, TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>,
                           TbCfg<P, 2, 4, 8, 6, 2>, TbCfg<P, 2, 8, 4, 5, 3>, TbCfg<P, 2, 4, 4, 5, 4>>;
 template <class P>
-using BatchCfgsRB = CfgList<RbCfg<P, 2, 4, 8, 6, 1>, RbCfg<P, 4, 2, 4, 7, 1>>;
-int num_cfg(bool rb) { return rb ? 2 : 9; }
+using BatchCfgsRB = CfgList<RbCfg<P, 2, 4, 4, 4, 4>, RbCfg<P, 2, 8, 4, 4, 2>, RbCfg<P, 2, 4, 8, 6, 1>,
+                            RbCfg<P, 4, 4, 4, 6, 2>>;
+template <class... Cs>
+constexpr int list_size(CfgList<Cs...>) {
+  return static_cast<int>(sizeof...(Cs));
+}
+static_assert(list_size(BatchCfgs<PolF32>{}) == list_size(BatchCfgs<PolBF16>{}), "same shapes per storage");
+int num_cfg(bool rb) { return rb ? list_size(BatchCfgsRB<PolF32>{}) : list_size(BatchCfgs<PolF32>{}); }
 
 // Calls f(Cfg{}) for the c-th configuration of the list.
 template <class F, class... Cs>
@@ -619,7 +625,8 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
 
   // Autotune: per inner storage in use (F32 always: BF16 instances may
   // escalate to it), time one pass of every compiled configuration over the
-  // whole batch and keep the fastest per sweep.
+  // whole batch and keep the fastest per sweep (for BF16 Jacobi passes, the
+  // fastest of two sweeps or more).
   const bool use_bf16 = opts->inner_dtype == STENCIL_BF16;
   int Tsel[2] = {1, 1};
   for (int di = 0; di < (use_bf16 ? 2 : 1); ++di) {
@@ -628,6 +635,10 @@ extern "C" int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* prob
     for (int c = 0; c < num_cfg(S.rb); ++c) {
       const CfgInfo ci = cfg_info(di, S.rb, c);
       if (opts->sweeps_per_pass > 0 && ci.T != std::min(opts->sweeps_per_pass, 2)) continue;
+      // bfloat16 storage rounds the iterate once per pass: one-sweep passes
+      // round every sweep and cost more sweeps to the tolerance than they
+      // save per sweep, so the library's choice for it is a longer pass.
+      if (di == 1 && !S.rb && opts->sweeps_per_pass <= 0 && ci.T < 2) continue;
       rc = S.configure(di, c);
       if (rc) return rc;
       // for timing, every instance counts as storage di

@@ -21,6 +21,8 @@ struct stencil_ctx {
   // the pass length used when the caller asks for the library's choice
   int sweep_choice[stencil::kNumPolicies][stencil::kMaxPass + 1];
   int best_pass[stencil::kNumPolicies];
+  // red-black configuration index per policy and colour stages per pass
+  int rb_choice[stencil::kNumPolicies][stencil::kMaxPass + 1];
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)

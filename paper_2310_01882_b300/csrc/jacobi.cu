@@ -412,7 +412,8 @@ int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid&
     for (; T >= 2; T -= 2)
       if ((nv = sweep_variants_rb(P.policy, T, &vs)) > 0) break;
     if (nv < 1) return set_error(STENCIL_ERR_ARG, "no compiled red-black configuration");
-    rc = vs[0].fn(ctx, *a_in, *b_out, P.fi, P.a, st);
+    const int c = ctx->rb_choice[P.policy][T];
+    rc = vs[c < nv ? c : 0].fn(ctx, *a_in, *b_out, P.fi, P.a, st);
     if (rc) return rc;
     std::swap(a_in, b_out);
     left -= T / 2;

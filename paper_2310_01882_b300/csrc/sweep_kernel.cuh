@@ -23,6 +23,9 @@
 //   * cells that are not interior (the Dirichlet halo) keep their value
 //     through every stage, so the T sweeps equal T separate sweeps exactly.
 // Lanes T..31-T of stage T write the result: a tile is (32-2T) x (R*WY).
+// With one sweep per pass (EDGE) every lane writes: a tile is 32 columns
+// wide, and the x neighbours that fall outside the warp (left of lane 0,
+// right of lane 31) are read from the staged plane instead of shuffled.
 // No CTA barrier and no shared-memory exchange between warps.
 #pragma once
 
@@ -57,13 +60,20 @@ __device__ __forceinline__ Item decode_item(const SweepGeom& g, int64_t item) {
   return t;
 }
 
-template <class Pol, int T_, int R_, int WY_, int S_, int MINB_>
+template <class Pol, int T_, int R_, int WY_, int S_, int MINB_, bool EDGE_ = (T_ == 1)>
 struct TbCfg {
   static constexpr int T = T_, R = R_, WY = WY_, S = S_, MINB = MINB_;
   static constexpr bool RB = false;
+  static constexpr bool EDGE = EDGE_;
+  static_assert(!EDGE || T == 1, "edge reads serve a single sweep stage");
   static constexpr int A = 16 / Pol::kElem;      // TMA x granule in elements
-  static constexpr int BOXW = 32 + A;            // staged columns (any 0 <= off < A)
-  static constexpr int BXO = 32 - 2 * T;         // output columns per tile
+  // Staged columns from the tile's first column - T: 32 lanes (+ A - 1 for
+  // an unaligned start), or, with EDGE, the 34 columns xo-1 .. xo+32 (tiles
+  // start at xo = 1 + 32 k, so xo - 1 is always aligned).
+  static constexpr int BOXW = EDGE ? (34 + A - 1) / A * A : 32 + A;
+  static constexpr int BXO = EDGE ? 32 : 32 - 2 * T;  // output columns per tile
+  static constexpr int XL = EDGE ? 0 : T;        // lane l holds column xo - XL + l
+  static constexpr int COL0 = T - XL;            // staged column of lane 0 (after off)
   static constexpr int BYO = R * WY;             // output rows per tile
   static constexpr int NROW = R + 2 * T;         // rows a warp converts per plane
   static constexpr int UROWS = BYO + 2 * T;
@@ -172,7 +182,8 @@ template <class Pol, class Cfg, int ROT>
 __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename Pol::K& k,
                                         const unsigned char* ring, int slot, uint32_t seq, int j,
                                         int p, int row0, int lane, int off, bool xin, uint32_t ymask,
-                                        typename Pol::T* orow0, int64_t sy, int64_t sz, int nz) {
+                                        bool edge_halo, bool any_edge_halo, typename Pol::T* orow0,
+                                        int64_t sy, int64_t sz, int nz) {
   using T = typename Pol::T;
   using C = typename Pol::C;
   constexpr int TT = Cfg::T, S = Cfg::S;
@@ -181,7 +192,8 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
     const T* U = reinterpret_cast<const T*>(ring + slot * Cfg::STAGE);
     const bool zin_p = (p >= 1 && p <= nz);
 #pragma unroll
-    for (int q = 0; q < Cfg::NROW; ++q) st.W[0][NEW][q] = Pol::in(U[(row0 + q) * Cfg::BOXW + off + lane], k);
+    for (int q = 0; q < Cfg::NROW; ++q)
+      st.W[0][NEW][q] = Pol::in(U[(row0 + q) * Cfg::BOXW + off + Cfg::COL0 + lane], k);
     // Cells outside the interior (Dirichlet halo, or beyond the grid) may be
     // stored in a different form (PolResident keeps them binary64); only
     // warps that touch one take this branch.
@@ -189,7 +201,8 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
     if (__any_sync(0xffffffffu, (halo_rows & ((1u << Cfg::NROW) - 1u)) != 0u)) {
 #pragma unroll
       for (int q = 0; q < Cfg::NROW; ++q)
-        if ((halo_rows >> q) & 1u) st.W[0][NEW][q] = Pol::in_halo(U[(row0 + q) * Cfg::BOXW + off + lane], k);
+        if ((halo_rows >> q) & 1u)
+          st.W[0][NEW][q] = Pol::in_halo(U[(row0 + q) * Cfg::BOXW + off + Cfg::COL0 + lane], k);
     }
   }
 #pragma unroll
@@ -205,19 +218,31 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
     for (int rr = 0; rr < Cfg::R + 2 * (TT - 1); ++rr) {
       if (rr >= nr) break;
       const C c = st.W[t - 1][MID][rr + 1];
-      const C xm = __shfl_up_sync(0xffffffffu, c, 1);
-      const C xp = __shfl_down_sync(0xffffffffu, c, 1);
+      C xm = __shfl_up_sync(0xffffffffu, c, 1);
+      C xp = __shfl_down_sync(0xffffffffu, c, 1);
+      if constexpr (Cfg::EDGE) {
+        // Lane 0's left and lane 31's right neighbour, from the staged plane
+        // of stage 0's middle plane (held until this step ends); the other
+        // lanes read an in-range cell they do not use.  Its y and z are the
+        // updated cell's, so it is a halo cell only at x = 0 or x = nx + 1.
+        const T* Um = reinterpret_cast<const T*>(ring + ((seq - 1) % S) * Cfg::STAGE);
+        const T e = Um[(row0 + rr + 1) * Cfg::BOXW + off + (lane == 0 ? 0 : 33)];
+        C ec = Pol::in(e, k);
+        if (any_edge_halo && edge_halo) ec = Pol::in_halo(e, k);
+        if (lane == 0) xm = ec;
+        if (lane == 31) xp = ec;
+      }
       const int w = rr - (TT - t);  // warp row, -T..R+T-1
       const bool in = xin && zin && ((ymask >> (w + TT)) & 1u);
       C v = c;
       if (in) {
-        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + lane];
+        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + Cfg::COL0 + lane];
         v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2],
                         st.W[t - 1][OLD][rr + 1], st.W[t - 1][NEW][rr + 1], fv, k);
       }
       if (t < TT) {
         st.W[t][NEW][rr] = v;
-      } else if (in && lane >= TT && lane < 32 - TT) {
+      } else if (in && lane >= Cfg::XL && lane < 32 - Cfg::XL) {
         orow0[static_cast<int64_t>(q) * sz + rr * sy] = Pol::out(v, k);
       }
     }
@@ -265,8 +290,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     const Item& t = v.t;
     const int xa = align_down(t.xo - TT, Cfg::A);
     const int off = t.xo - TT - xa;
-    const int64_t x = t.xo - TT + lane;  // halo index of this lane's column
+    const int64_t x = t.xo - Cfg::XL + lane;  // halo index of this lane's column
     const bool xin = (x >= 1 && x <= v.nx);
+    // EDGE: is the neighbour this lane reads from the staged plane (lane 0:
+    // x - 1, lane 31: x + 1) a Dirichlet halo cell?
+    const bool edge_halo = lane == 0 ? (x - 1 < 1) : (x + 1 > v.nx);
+    const bool any_edge_halo = __any_sync(0xffffffffu, (lane == 0 || lane == 31) && edge_halo);
     uint32_t ymask = 0;                  // bit w+T: warp row w is interior
 #pragma unroll
     for (int w = -TT; w < Cfg::R + TT; ++w) {
@@ -296,7 +325,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     const int slot = wait(j);                                                                      \
     if (slot < 0) return;                                                                          \
     tb_step<Pol, Cfg, ROT>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off, xin,  \
-                           ymask, orow0, v.sy, v.sz, static_cast<int>(v.nz));                      \
+                           ymask, edge_halo, any_edge_halo, orow0, v.sy, v.sz,                      \
+                           static_cast<int>(v.nz));                                                 \
     if (j >= TT) release(seq0 + j - TT);                                                           \
     if (++j >= steps) break;                                                                       \
   }

@@ -5,21 +5,24 @@
 // With jacobi_tb's one column per lane the colours alternate along x, so
 // every warp instruction of a colour stage would cover both colours and
 // throw half of the arithmetic away.  Here lane l of a consumer warp owns
-// columns 2l and 2l+1 of a 64-column
-// tile (a tile is (64 - 2T) x (R * WY) outputs).  Along any row exactly one
-// of the two has the stage's colour, so each lane updates one point per row
-// and carries the other over:
-//   * the updated column phi = (colour + x0 + y + z) mod 2, x0 the parity of
-//     the lane's first column (the same for every lane);
-//   * its x neighbours are the lane's other column and the facing column of
-//     lane l-1 (phi = 0) or lane l+1 (phi = 1): one shuffle up of column 1
-//     and one shuffle down of column 0 per row serve both cases;
-//   * y and z neighbours are the lane's own registers (rows, rotating
-//     planes), as in jacobi_tb.
-// Stage t (1..T) handles colour (t-1) mod 2 on plane p - t when raw plane p
-// arrives; T stages make T/2 red-black sweeps per pass.  The producer, the
-// stage ring, the bounded waits and the work sources are those of
-// jacobi_tb (sweep_kernel.cuh).
+// columns 2l and 2l+1 of a 64-column tile (a tile is (64 - 2T) x (R * WY)
+// outputs).  Along any row exactly one of the two has a given colour, and
+// which one is the same for every lane of the warp (the lanes' first
+// columns share their parity).  The registers hold values by colour, not
+// by column: stage t keeps, for three planes and its rows, the one value
+// per row of the colour it computed (stage 0: the raw values of the colour
+// stage 1 does not update).  Stage t (1..T) computes colour (t-1) mod 2 on
+// plane p - t when raw plane p arrives:
+//   * the updated cell's x neighbours are the lane's own value of the other
+//     colour in that row (its other column) and the same register of lane
+//     l-1 or l+1 (one shuffle, warp-uniform direction);
+//   * y and z neighbours are the lane's stage t-1 registers of the adjacent
+//     rows and planes, as in jacobi_tb;
+//   * a cell that is not interior keeps its staged value (the Dirichlet
+//     halo; still staged, since a warp holds T+1 planes).
+// The last stage writes both colours of its plane.  T stages make T/2
+// red-black sweeps per pass.  The producer, the stage ring, the bounded
+// waits and the work sources are those of jacobi_tb (sweep_kernel.cuh).
 #pragma once
 
 #include "sweep_kernel.cuh"
@@ -55,7 +58,7 @@ struct RbCfg {
 template <class Pol, class Cfg>
 struct RbLaneState {
   using C = typename Pol::C;
-  C W[Cfg::T][3][Cfg::NROW][2];  // stage t's three planes, two columns
+  C W[Cfg::T][3][Cfg::NROW];  // stage t's values of its colour: three planes, its rows
 };
 
 template <class Pol, class Cfg, int ROT>
@@ -67,24 +70,26 @@ __device__ __forceinline__ void rb_step(RbLaneState<Pol, Cfg>& st, const typenam
   using C = typename Pol::C;
   constexpr int TT = Cfg::T, S = Cfg::S;
   constexpr int OLD = (0 + ROT) % 3, MID = (1 + ROT) % 3, NEW = (2 + ROT) % 3;
+  // Cell (column i of the lane, warp row w, plane q) is red iff
+  // pb + i + w + q is even; colour c (0 red, 1 black) of row w of plane q
+  // sits in column (pb + w + q + c) & 1.
   {
+    // stage 0: plane p's cells of colour 1 (black), rows -T .. R+T-1
     const T* U = reinterpret_cast<const T*>(ring + slot * Cfg::STAGE);
     const bool zin_p = (p >= 1 && p <= nz);
+    bool halo = false;
 #pragma unroll
     for (int q = 0; q < Cfg::NROW; ++q) {
-      const T* row = U + (row0 + q) * Cfg::BOXW + off + 2 * lane;
-      st.W[0][NEW][q][0] = Pol::in(row[0], k);
-      st.W[0][NEW][q][1] = Pol::in(row[1], k);
+      const int ic = (pb + q - TT + p + 1) & 1;
+      st.W[0][NEW][q] = Pol::in(U[(row0 + q) * Cfg::BOXW + off + 2 * lane + ic], k);
+      halo |= !((ic ? xin1 : xin0) && zin_p && ((ymask >> q) & 1u));
     }
-    const uint32_t rows_mask = (1u << Cfg::NROW) - 1u;
-    const uint32_t halo0 = (xin0 && zin_p) ? ~ymask : 0xffffffffu;
-    const uint32_t halo1 = (xin1 && zin_p) ? ~ymask : 0xffffffffu;
-    if (__any_sync(0xffffffffu, ((halo0 | halo1) & rows_mask) != 0u)) {
+    if (__any_sync(0xffffffffu, halo)) {
 #pragma unroll
       for (int q = 0; q < Cfg::NROW; ++q) {
-        const T* row = U + (row0 + q) * Cfg::BOXW + off + 2 * lane;
-        if ((halo0 >> q) & 1u) st.W[0][NEW][q][0] = Pol::in_halo(row[0], k);
-        if ((halo1 >> q) & 1u) st.W[0][NEW][q][1] = Pol::in_halo(row[1], k);
+        const int ic = (pb + q - TT + p + 1) & 1;
+        if (!((ic ? xin1 : xin0) && zin_p && ((ymask >> q) & 1u)))
+          st.W[0][NEW][q] = Pol::in_halo(U[(row0 + q) * Cfg::BOXW + off + 2 * lane + ic], k);
       }
     }
   }
@@ -94,39 +99,36 @@ __device__ __forceinline__ void rb_step(RbLaneState<Pol, Cfg>& st, const typenam
     const int q = p - t;   // plane this stage updates
     const bool zin = (q >= 1 && q <= nz);
     const T* F = reinterpret_cast<const T*>(ring + ((seq - t) % S) * Cfg::STAGE + Cfg::UB);
+    const T* Uq = reinterpret_cast<const T*>(ring + ((seq - t) % S) * Cfg::STAGE);
     const int nr = Cfg::R + 2 * (TT - t);
 #pragma unroll
     for (int rr = 0; rr < Cfg::R + 2 * (TT - 1); ++rr) {
       if (rr >= nr) break;
-      const C c0 = st.W[t - 1][MID][rr + 1][0];
-      const C c1 = st.W[t - 1][MID][rr + 1][1];
-      const C left = __shfl_up_sync(0xffffffffu, c1, 1);    // lane l-1, column 1
-      const C right = __shfl_down_sync(0xffffffffu, c0, 1); // lane l+1, column 0
-      const int w = rr - (TT - t);                           // warp row, -T..R+T-1
+      const int w = rr - (TT - t);  // warp row, -T..R+T-1
+      const int ic = (pb + w + q + ((t - 1) & 1)) & 1;  // column of this stage's colour
       const bool yzin = zin && ((ymask >> (w + TT)) & 1u);
-      const int phi = ((t - 1) + pb + w + q) & 1;            // the column of this stage's colour
-      const bool in = yzin && (phi ? xin1 : xin0);
-      C v = phi ? c1 : c0;
+      const bool in = yzin && (ic ? xin1 : xin0);
+      // the other colour in this row: own column 1 - ic, and the facing
+      // column of lane l-1 (ic = 0) or lane l+1 (ic = 1)
+      const C own = st.W[t - 1][MID][rr + 1];
+      const C other = __shfl_sync(0xffffffffu, own, (lane + (ic ? 1 : 31)) & 31);
+      C v;
       if (in) {
-        const C xm = phi ? c0 : left;
-        const C xp = phi ? right : c1;
-        const C ym = phi ? st.W[t - 1][MID][rr][1] : st.W[t - 1][MID][rr][0];
-        const C yp = phi ? st.W[t - 1][MID][rr + 2][1] : st.W[t - 1][MID][rr + 2][0];
-        const C zm = phi ? st.W[t - 1][OLD][rr + 1][1] : st.W[t - 1][OLD][rr + 1][0];
-        const C zp = phi ? st.W[t - 1][NEW][rr + 1][1] : st.W[t - 1][NEW][rr + 1][0];
-        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + 2 * lane + phi];
-        v = Pol::update(xm, xp, ym, yp, zm, zp, fv, k);
+        const C xm = ic ? own : other;
+        const C xp = ic ? other : own;
+        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + 2 * lane + ic];
+        v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2], st.W[t - 1][OLD][rr + 1],
+                        st.W[t - 1][NEW][rr + 1], fv, k);
+      } else {
+        v = Pol::in_halo(Uq[(row0 + w + TT) * Cfg::BOXW + off + 2 * lane + ic], k);
       }
-      const C n0 = phi ? c0 : v;
-      const C n1 = phi ? v : c1;
       if (t < TT) {
-        st.W[t][NEW][rr][0] = n0;
-        st.W[t][NEW][rr][1] = n1;
-      } else if (yzin) {
+        st.W[t][NEW][rr] = v;
+      } else if (yzin && 2 * lane >= TT && 2 * lane + 1 < 64 - TT) {
+        // both colours of plane q are final: this stage's and stage T-1's
         typename Pol::T* o = orow0 + static_cast<int64_t>(q) * sz + rr * sy;
-        // columns TT .. 63-TT of the lane pair space hold final values
-        if (xin0 && 2 * lane >= TT && 2 * lane < 64 - TT) o[0] = Pol::out(n0, k);
-        if (xin1 && 2 * lane + 1 >= TT && 2 * lane + 1 < 64 - TT) o[1] = Pol::out(n1, k);
+        if (in) o[ic] = Pol::out(v, k);
+        if (ic ? xin0 : xin1) o[ic ^ 1] = Pol::out(own, k);
       }
     }
   }

@@ -80,6 +80,10 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "stencil_sweep_config_select": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32], ctypes.c_int),
+    "stencil_redblack_config_count": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "stencil_redblack_config_select": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int32], ctypes.c_int),
     "wsnet_create": ([ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "wsnet_destroy": ([_P], ctypes.c_int),
@@ -269,6 +273,18 @@ def stencil_sweep_config_count(dtype, flags, with_work, T):
 def stencil_sweep_config_select(ctx, dtype, flags, with_work, T, index):
     return _check(lib().stencil_sweep_config_select(ctx.handle, int(dtype), int(flags), int(bool(with_work)),
                                                     int(T), int(index)))
+
+
+def stencil_redblack_config_count(dtype, flags, with_work, sweeps_per_pass):
+    c = ctypes.c_int32()
+    _check(lib().stencil_redblack_config_count(int(dtype), int(flags), int(bool(with_work)), int(sweeps_per_pass),
+                                               ctypes.byref(c)))
+    return c.value
+
+
+def stencil_redblack_config_select(ctx, dtype, flags, with_work, sweeps_per_pass, index):
+    return _check(lib().stencil_redblack_config_select(ctx.handle, int(dtype), int(flags), int(bool(with_work)),
+                                                       int(sweeps_per_pass), int(index)))
 
 
 def stencil_residual(ctx, u, f, h, norms_dev, r=None, stream=None):

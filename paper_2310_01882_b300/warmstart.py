@@ -1,7 +1,7 @@
 """Learned warm start for the Jacobi Poisson solve: data, training, evaluation.
 
     python -m paper_2310_01882_b300.warmstart [--n 128] [--train 200] [--test 20]
-        [--epochs 30] [--batch 4] [--lr 1e-3] [--together K] [--out DIR]
+        [--epochs 30] [--batch 4] [--lr 1e-3] [--together K] [--kinds LIST] [--out DIR]
 
 Pairs (f, u*): f a k^-3 Gaussian random field (seeds 10000+i for training,
 20000+i held out), u* from plain FP64 Jacobi (stencil_jacobi_sweep) from zero
@@ -84,10 +84,23 @@ class Solver:
                 sweeps[i] += chunk
 
 
+def make_fields(n, seeds, workers=None):
+    """Device Fields of the k^-3 GRFs for `seeds`, in seed order; the host
+    transforms run on several threads, a few fields ahead of the copies."""
+    from concurrent.futures import ThreadPoolExecutor
+    workers = workers or max(1, min(16, len(os.sched_getaffinity(0))))
+    out = []
+    with ThreadPoolExecutor(workers) as ex:
+        for b in range(0, len(seeds), 4 * workers):
+            chunk = seeds[b:b + 4 * workers]
+            out += [S.Field.from_numpy(a) for a in ex.map(lambda s: inputs.grf(n, seed=s), chunk)]
+    return out
+
+
 def generate_pairs(solver, seeds):
     """(f, u*) Field pairs for the given GRF seeds (u* from plain FP64 Jacobi)."""
     n = solver.n
-    fs = [S.Field.from_numpy(inputs.grf(n, seed=s)) for s in seeds]
+    fs = make_fields(n, seeds)
     us = [S.Field(n, n, n) for _ in seeds]
     info = solver.solve(us, fs)
     return fs, us, info
@@ -217,7 +230,7 @@ def evaluate_together(net, solver, seeds, kinds=("fp64", "f32", "bf16")):
     starts and from warm starts (inference of every field included)."""
     import torch
     n = solver.n
-    fs = [S.Field.from_numpy(inputs.grf(n, seed=s)) for s in seeds]
+    fs = make_fields(n, seeds)
     warm = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -277,6 +290,8 @@ def main():
     ap.add_argument("--load", default=None, help="evaluate saved parameters (.npy) instead of training")
     ap.add_argument("--together", type=int, default=0,
                     help="also time solving this many held-out fields as one job")
+    ap.add_argument("--kinds", default="fp64,f32,bf16",
+                    help="solvers of the --together comparison (fp64, fp64rb, f32, f32rb, bf16)")
     ap.add_argument("--out", default=".")
     args = ap.parse_args()
     import torch
@@ -305,7 +320,8 @@ def main():
     log(json.dumps(summary))
     together = None
     if args.together:
-        together = evaluate_together(net, solver, [20000 + i for i in range(args.together)])
+        together = evaluate_together(net, solver, [20000 + i for i in range(args.together)],
+                                     kinds=tuple(args.kinds.split(",")))
         log(json.dumps(together))
     result = {"n": args.n, "train_pairs": args.train, "test_fields": args.test, "epochs": args.epochs,
               "batch": args.batch, "lr": args.lr, "gen_seconds": gen_s, "train_seconds": train_s,

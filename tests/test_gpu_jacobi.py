@@ -238,10 +238,14 @@ CONFIG_CASES = [(S.F64, S.SWEEP_FP64_FIXED, True), (S.F64, S.SWEEP_FP64_FIXED, F
 
 
 @pytest.mark.parametrize("dtype,flags,with_work", CONFIG_CASES)
-def test_every_compiled_configuration(dtype, flags, with_work):
+@pytest.mark.parametrize("shape", [(70, 45, 23), (96, 40, 11)])
+def test_every_compiled_configuration(dtype, flags, with_work, shape):
     """Each compiled tile configuration (pinned with sweep_config_select) of
-    each pass length gives the oracle's sweeps on a ragged grid."""
-    u, f, h = rand_problem(70, 45, 23, seed=41)
+    each pass length gives the oracle's sweeps on a ragged grid, and on one
+    whose x extent is a whole number of 32-column tiles (the last column's
+    right neighbour is the Dirichlet halo, read from the staged plane by the
+    one-sweep tiles)."""
+    u, f, h = rand_problem(*shape, seed=41)
     n = 8
     if dtype == S.F64:
         ref = oracle.jacobi(u, f, h, n)

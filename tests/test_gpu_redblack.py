@@ -104,3 +104,44 @@ def test_arguments():
         S.stencil_redblack_sweep(ctx(), u, u.like(), u.like(), None, 0.1, 1, 5)  # sweeps_per_pass > 4
     with pytest.raises(S.StencilError):
         S.stencil_redblack_sweep(ctx(), u, u, u.like(), None, 0.1, 1, 0)  # u_tmp aliases u
+
+
+RB_CONFIG_CASES = [(S.F64, S.SWEEP_FP64_FIXED, True, 1), (S.F64, S.SWEEP_FP64_FIXED, False, 1),
+                   (S.F64, S.SWEEP_FP64_NATIVE, False, 1), (S.F32, 0, False, 1), (S.F32, 0, False, 2),
+                   (S.BF16, 0, False, 1), (S.BF16, 0, False, 2)]
+
+
+@pytest.mark.parametrize("dtype,flags,with_work,spp", RB_CONFIG_CASES)
+@pytest.mark.parametrize("shape", [(70, 45, 23), (120, 40, 11)])
+def test_every_compiled_configuration(dtype, flags, with_work, spp, shape):
+    """Each compiled red-black tile configuration (pinned with
+    redblack_config_select) gives the oracle's sweeps on a ragged grid and
+    on one whose x extent fills whole 60-column tiles."""
+    u, f, h = rand_problem(*shape, seed=43)
+    n = 4
+    if dtype == S.F64:
+        u_in, f_in = u, f
+        ref, tol = oracle.rbgs(u, f, h, n), 1e-13
+    elif dtype == S.F32:
+        u32, f32 = u.astype(np.float32), f.astype(np.float32)
+        u_in, f_in = u32.astype(np.float64), f32.astype(np.float64)
+        ref, tol = oracle.rbgs_f32(u32, f32, h, n).astype(np.float64), 1e-5 * n
+    else:
+        u_in = oracle.from_bf16(oracle.to_bf16(u.astype(np.float32))).astype(np.float64)
+        f_in = oracle.from_bf16(oracle.to_bf16(f.astype(np.float32))).astype(np.float64)
+        ref, tol = oracle.rbgs(u_in, f_in, h, n), (-(-n // spp)) * 2.0 ** -8
+    c = S.Context(0)
+    count = S.stencil_redblack_config_count(dtype, flags, with_work, spp)
+    assert count >= 1
+    for idx in range(count):
+        S.stencil_redblack_config_select(c, dtype, flags, with_work, spp, idx)
+        uf, ff = S.Field.from_numpy(u_in, dtype), S.Field.from_numpy(f_in, dtype)
+        w = S.Field(uf.nx, uf.ny, uf.nz) if with_work else None
+        S.stencil_redblack_sweep(c, uf, uf.like(), ff, w, h, n, spp, flags)
+        S.stencil_ctx_status(c)
+        got = uf.to_numpy()
+        assert rel_err(got, ref) <= tol, (idx, rel_err(got, ref))
+        assert halo_equal(got, u_in)
+    with pytest.raises(S.StencilError):
+        S.stencil_redblack_config_select(c, dtype, flags, with_work, spp, count)
+    c.close()
