@@ -42,36 +42,46 @@ ALGO_BYTES = {"f64": 24, "f32": 12, "bf16": 6}   # read u, read f, write u' per 
 # ncu DRAM bytes (read + write) per launch of the dominant kernel, measured on
 # a 320^3 launch of each one-sweep configuration and scaled by the lattice
 # points to 512^3 (the traffic grows with the points); keyed by the kernel
-# configuration the autotuner may keep.  Command, for index i = 0..4 of the
-# compiled one-sweep configurations:
+# configuration the autotuner may keep.  Command, for index i = 0..9 of the
+# compiled one-sweep configurations (32-column tiles):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       --clock-control none -k regex:jacobi_tb -s 2 -c 1
 #   python bench.py --grid 320 --sweeps 8 --only f64 --steps 1 --warmup 1 --no-cpu --f64-config i
 _SCALE_320 = (512 / 320) ** 3
 MEASURED_TRAFFIC = {
-    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (613374976 + 231496704) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (565770496 + 231974656) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (570426880 + 234036224) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (596441344 + 234272768) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (575960320 + 235593728) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (587434752 + 231388160) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (569373696 + 232077568) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (569324288 + 232129280) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (568562944 + 231546624) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (573722880 + 234918144) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=5>": (550198528 + 235312384) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=6>": (550281728 + 234866944) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=16,S=5>": (575207936 + 233568000) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=8,S=5>": (546770944 + 234200064) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=1,WY=16,S=5>": (563922432 + 237409024) * _SCALE_320,
 }
 
 
-def chosen_config(report, T, policy_name):
+def chosen_config(report, T, policy_name, with_index=False):
     """Name of the configuration the autotuner kept for pass length T (the
-    fastest line of that T in its report), or the library default."""
+    fastest line of that T in its report), or the library default; with
+    with_index, also its index among the T lines (the registry order)."""
     best = None
+    idx = -1
     for ln in report.splitlines():
         if f" T={T} " not in ln or "ms/sweep" not in ln:
             continue
+        idx += 1
         parts = dict(kv.split("=") for kv in ln.split(":")[0].split()[2:])
         t = float(ln.split(":")[1].split()[0])
         if best is None or t < best[0]:
-            best = (t, parts)
+            best = (t, parts, idx)
     if best is None:
-        return f"jacobi_tb<{policy_name},T={T},R=8,WY=4,S=4>"
-    p = best[1]
-    return f"jacobi_tb<{policy_name},T={T},R={p['R']},WY={p['WY']},S={p['S']}>"
+        name, index = f"jacobi_tb<{policy_name},T={T},R=8,WY=4,S=4>", 0
+    else:
+        p = best[1]
+        name, index = f"jacobi_tb<{policy_name},T={T},R={p['R']},WY={p['WY']},S={p['S']}>", best[2]
+    return (name, index) if with_index else name
 
 
 HEADLINE_METRIC = "GLUP/s and % HBM roofline at 1 B300 (512^3 FP64 Jacobi 7-point Poisson sweeps)"
@@ -353,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
     # The headline runs one sweep per pass: the HBM-bound configuration the
     # roofline refers to (the fused two-sweep pass is reported as a variant).
     T_head = args.spp if args.spp else 1
-    kernel_name = chosen_config(tune_reports.get("f64", ""), T_head, "PolResident")
+    kernel_name, kernel_index = chosen_config(tune_reports.get("f64", ""), T_head, "PolResident", with_index=True)
 
     def step64():
         S.stencil_jacobi_sweep(ctx, u, ut, f, work, h, SWEEPS, T_head, S.SWEEP_AUTO)
@@ -373,7 +383,9 @@ def run_ours(args, rank, world, local_rank):
     if args.only == "f64":
         if rank == 0:
             print(json.dumps({"metric": "GLUP/s (profiling run, FP64 step only)", "value": round(glups, 2),
-                              "unit": "GLUP/s", "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3)}))
+                              "unit": "GLUP/s", "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3),
+                              "kernel": kernel_name, "config_index": kernel_index,
+                              "autotune": tune_reports.get("f64", "").splitlines()}))
         ctx.close()
         return
     # ---- variants: FP32 / BF16 storage (sweeps per pass 1, 2, 4), FP64 ------

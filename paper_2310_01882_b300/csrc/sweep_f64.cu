@@ -7,12 +7,16 @@ namespace stencil {
 
 int sweep_variants_f64(int policy, int T, const SweepVariant** out) {
   static const SweepVariant res1[] = {
-      variant<PolResident, TbCfg<PolResident, 1, 8, 4, 4, 3>>(),
-      variant<PolResident, TbCfg<PolResident, 1, 4, 8, 5, 2>>(),
-      variant<PolResident, TbCfg<PolResident, 1, 8, 4, 6, 2>>(),
-      variant<PolResident, TbCfg<PolResident, 1, 4, 4, 6, 4>>(),
-      variant<PolResident, TbCfg<PolResident, 1, 8, 8, 4, 1>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 4, 16, 5, 1>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 2, 16, 6, 1>>(),
       variant<PolResident, TbCfg<PolResident, 1, 2, 16, 5, 1>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 2, 8, 5, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 4, 8, 5, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 8, 4, 4, 3>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 8, 4, 6, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 8, 8, 4, 1>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 1, 16, 5, 2>>(),
+      variant<PolResident, TbCfg<PolResident, 1, 4, 4, 6, 4>>(),
   };
   static const SweepVariant res2[] = {
       variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2>>(),
