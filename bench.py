@@ -337,18 +337,32 @@ def run_ours(args, rank, world, local_rank):
         ctx.close()
         return
 
+    if args.only == "redblack":
+        # red-black Gauss-Seidel sweeps on the FP64 fields (resident fixed
+        # point, the library's default shape), one sweep per pass
+        u, ut, f = fields(S.F64)
+        ms = timed_steps(lambda: S.stencil_redblack_sweep(ctx, u, ut, f, work, h, SWEEPS, 1), args.steps,
+                         args.warmup)
+        S.stencil_ctx_status(ctx)
+        if rank == 0:
+            print(json.dumps({"metric": "GLUP/s (profiling run, FP64 red-black step only)",
+                              "value": round(N ** 3 * SWEEPS / (ms * 1e-3) / 1e9, 2), "unit": "GLUP/s",
+                              "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3)}))
+        ctx.close()
+        return
+
     if args.only in ("f32", "bf16"):
         dt = S.F32 if args.only == "f32" else S.BF16
         u, ut, f = fields(dt)
-        if not args.no_tune:
-            S.stencil_autotune_sweep(ctx, u, ut, f, None, h)
+        rep = "" if args.no_tune else S.stencil_autotune_sweep(ctx, u, ut, f, None, h)
         ms = timed_steps(lambda: S.stencil_jacobi_sweep(ctx, u, ut, f, None, h, SWEEPS, args.spp, 0), args.steps,
                          args.warmup)
         S.stencil_ctx_status(ctx)
         if rank == 0:
             print(json.dumps({"metric": f"GLUP/s (profiling run, {args.only} step only)", "spp": args.spp,
                               "value": round(N ** 3 * SWEEPS / (ms * 1e-3) / 1e9, 2), "unit": "GLUP/s",
-                              "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3)}))
+                              "grid": N, "sweeps_per_step": SWEEPS, "ms_per_step": round(ms, 3),
+                              "autotune": [ln for ln in rep.splitlines() if "ms/sweep" in ln or ln.startswith("chosen")]}))
         ctx.close()
         return
 
@@ -651,7 +665,7 @@ def main():
                     help="pin the headline's FP64 one-sweep configuration (index; profiling runs)")
     ap.add_argument("--grid", type=int, default=None, help="grid extent (profiling runs; default 512)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step (profiling runs; default 1000)")
-    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet", "batch"],
+    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet", "batch", "redblack"],
                     help="run one dtype's step only (profiling runs)")
     ap.add_argument("--spp", type=int, default=0, help="sweeps per pass for --only runs (0 = library default)")
     ap.add_argument("--traffic", type=float, default=None,

@@ -4,7 +4,9 @@
 // sweep computes in, and four operations: `in` (storage -> register), `out`
 // (register -> storage), `update` (one Jacobi update from the six
 // neighbours and the source value) and `make` (per-launch constants,
-// evaluated on the device by every thread).
+// evaluated on the device by every thread).  Every `update` adds the two x
+// neighbours first (xm + xp): the red-black kernel relies on it to pass
+// them in either order.
 #pragma once
 
 #include <cuda_bf16.h>

@@ -10,9 +10,6 @@ int sweep_variants_bf16(int T, const SweepVariant** out) {
       variant<PolBF16, TbCfg<PolBF16, 1, 8, 4, 5, 3>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 4, 8, 6, 3>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 4, 4, 5, 6>>(),
-      variant<PolBF16, TbCfg<PolBF16, 1, 4, 16, 5, 1>>(),
-      variant<PolBF16, TbCfg<PolBF16, 1, 2, 16, 5, 2>>(),
-      variant<PolBF16, TbCfg<PolBF16, 1, 8, 16, 4, 1>>(),
   };
   static const SweepVariant t2[] = {
       variant<PolBF16, TbCfg<PolBF16, 2, 8, 4, 5, 1>>(),

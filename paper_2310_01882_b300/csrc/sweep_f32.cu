@@ -10,9 +10,6 @@ int sweep_variants_f32(int T, const SweepVariant** out) {
       variant<PolF32, TbCfg<PolF32, 1, 8, 4, 5, 3>>(),
       variant<PolF32, TbCfg<PolF32, 1, 4, 8, 6, 3>>(),
       variant<PolF32, TbCfg<PolF32, 1, 4, 4, 5, 6>>(),
-      variant<PolF32, TbCfg<PolF32, 1, 4, 16, 5, 1>>(),
-      variant<PolF32, TbCfg<PolF32, 1, 2, 16, 5, 2>>(),
-      variant<PolF32, TbCfg<PolF32, 1, 8, 16, 4, 1>>(),
   };
   static const SweepVariant t2[] = {
       variant<PolF32, TbCfg<PolF32, 2, 8, 4, 5, 1>>(),

@@ -114,10 +114,10 @@ __device__ __forceinline__ void rb_step(RbLaneState<Pol, Cfg>& st, const typenam
       const C other = __shfl_sync(0xffffffffu, own, (lane + (ic ? 1 : 31)) & 31);
       C v;
       if (in) {
-        const C xm = ic ? own : other;
-        const C xp = ic ? other : own;
+        // Every policy's update starts with xm + xp, and addition is
+        // commutative, so the two x neighbours go in without a select.
         const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + 2 * lane + ic];
-        v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2], st.W[t - 1][OLD][rr + 1],
+        v = Pol::update(other, own, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2], st.W[t - 1][OLD][rr + 1],
                         st.W[t - 1][NEW][rr + 1], fv, k);
       } else {
         v = Pol::in_halo(Uq[(row0 + w + TT) * Cfg::BOXW + off + 2 * lane + ic], k);
