@@ -10,6 +10,7 @@ namespace stencil {
 int sweep_variants_rb(int policy, int T, const SweepVariant** out) {
   static const SweepVariant res2[] = {
       variant<PolResident, RbCfg<PolResident, 2, 4, 4, 4, 2>>(),
+      variant<PolResident, RbCfg<PolResident, 2, 4, 4, 5, 2>>(),
       variant<PolResident, RbCfg<PolResident, 2, 4, 8, 5, 1>>(),
       variant<PolResident, RbCfg<PolResident, 2, 2, 8, 4, 2>>(),
       variant<PolResident, RbCfg<PolResident, 2, 2, 8, 6, 1>>(),
@@ -25,6 +26,8 @@ int sweep_variants_rb(int policy, int T, const SweepVariant** out) {
   };
   static const SweepVariant f322[] = {
       variant<PolF32, RbCfg<PolF32, 2, 4, 4, 4, 4>>(),
+      variant<PolF32, RbCfg<PolF32, 2, 4, 4, 5, 4>>(),
+      variant<PolF32, RbCfg<PolF32, 2, 4, 4, 6, 3>>(),
       variant<PolF32, RbCfg<PolF32, 2, 8, 4, 4, 2>>(),
       variant<PolF32, RbCfg<PolF32, 2, 8, 8, 4, 1>>(),
       variant<PolF32, RbCfg<PolF32, 2, 4, 8, 4, 2>>(),
@@ -38,6 +41,8 @@ int sweep_variants_rb(int policy, int T, const SweepVariant** out) {
   };
   static const SweepVariant b162[] = {
       variant<PolBF16, RbCfg<PolBF16, 2, 4, 4, 4, 4>>(),
+      variant<PolBF16, RbCfg<PolBF16, 2, 4, 4, 5, 4>>(),
+      variant<PolBF16, RbCfg<PolBF16, 2, 4, 4, 6, 3>>(),
       variant<PolBF16, RbCfg<PolBF16, 2, 8, 4, 4, 2>>(),
       variant<PolBF16, RbCfg<PolBF16, 2, 8, 8, 4, 1>>(),
       variant<PolBF16, RbCfg<PolBF16, 2, 4, 8, 4, 2>>(),
