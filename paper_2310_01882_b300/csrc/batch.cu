@@ -345,8 +345,8 @@ using BatchCfgs = CfgList<TbCfg<P, 1, 8, 4, 4, 3>, TbCfg<P, 1, 8, 8, 4, 2>, TbCf
                           TbCfg<P, 2, 4, 4, 5, 2>, TbCfg<P, 2, 8, 4, 5, 1>, TbCfg<P, 2, 4, 8, 6, 2>,
                           TbCfg<P, 2, 8, 4, 5, 3>, TbCfg<P, 2, 4, 4, 5, 4>>;
 template <class P>
-using BatchCfgsRB = CfgList<RbCfg<P, 2, 4, 4, 4, 4>, RbCfg<P, 2, 8, 4, 4, 2>, RbCfg<P, 2, 4, 8, 6, 1>,
-                            RbCfg<P, 4, 4, 4, 6, 2>>;
+using BatchCfgsRB = CfgList<RbCfg<P, 2, 4, 4, 5, 4>, RbCfg<P, 2, 4, 4, 4, 4>, RbCfg<P, 2, 8, 4, 4, 2>,
+                            RbCfg<P, 2, 4, 8, 6, 1>, RbCfg<P, 4, 4, 4, 6, 2>>;
 template <class... Cs>
 constexpr int list_size(CfgList<Cs...>) {
   return static_cast<int>(sizeof...(Cs));

@@ -25,8 +25,8 @@ int sweep_variants_rb(int policy, int T, const SweepVariant** out) {
       variant<PolF64, RbCfg<PolF64, 2, 2, 8, 6, 1>>(),
   };
   static const SweepVariant f322[] = {
-      variant<PolF32, RbCfg<PolF32, 2, 4, 4, 4, 4>>(),
       variant<PolF32, RbCfg<PolF32, 2, 4, 4, 5, 4>>(),
+      variant<PolF32, RbCfg<PolF32, 2, 4, 4, 4, 4>>(),
       variant<PolF32, RbCfg<PolF32, 2, 4, 4, 6, 3>>(),
       variant<PolF32, RbCfg<PolF32, 2, 8, 4, 4, 2>>(),
       variant<PolF32, RbCfg<PolF32, 2, 8, 8, 4, 1>>(),
