@@ -19,8 +19,10 @@ int sweep_variants_f64(int policy, int T, const SweepVariant** out) {
       variant<PolResident, TbCfg<PolResident, 1, 4, 4, 6, 4>>(),
   };
   static const SweepVariant res2[] = {
-      variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2>>(),
       variant<PolResident, TbCfg<PolResident, 2, 2, 4, 6, 3>>(),
+      // stage-1 edge reads (30-column tiles): faster than the 28-column form
+      // of this shape, 0.710 against 0.724 ms per sweep at 512^3
+      variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2, true>>(),
   };
   static const SweepVariant fix1[] = {variant<PolFixed, TbCfg<PolFixed, 1, 8, 4, 4, 3>>()};
   static const SweepVariant f641[] = {variant<PolF64, TbCfg<PolF64, 1, 8, 4, 4, 3>>()};

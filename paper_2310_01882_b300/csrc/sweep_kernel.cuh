@@ -17,15 +17,18 @@
 //     previous and next planes (three planes per sweep stage, rotated by a
 //     three-way unrolled loop, so no register moves);
 //   * sweep stage t (1..T) updates plane p - t when raw plane p arrives, on
-//     lanes t..31-t and rows -(T-t)..R-1+(T-t), from stage t-1's planes; its
-//     source term is read from the staged f plane, which is held until the
-//     last stage has used it;
+//     its valid lanes (below) and rows -(T-t)..R-1+(T-t), from stage t-1's
+//     planes; its source term is read from the staged f plane, which is
+//     held until the last stage has used it;
 //   * cells that are not interior (the Dirichlet halo) keep their value
 //     through every stage, so the T sweeps equal T separate sweeps exactly.
-// Lanes T..31-T of stage T write the result: a tile is (32-2T) x (R*WY).
-// With one sweep per pass (EDGE) every lane writes: a tile is 32 columns
-// wide, and the x neighbours that fall outside the warp (left of lane 0,
-// right of lane 31) are read from the staged plane instead of shuffled.
+// With EDGE (the default at one sweep per pass), stage 1 reads the x
+// neighbours that fall outside the warp (left of lane 0, right of lane 31)
+// from the staged raw plane instead of shuffling them, so it is valid on
+// all 32 lanes and stage t on lanes t-1..32-t: lanes T-1..32-T of stage T
+// write the result, a tile is (34-2T) x (R*WY) (32 columns at one sweep per
+// pass).  Without EDGE stage t is valid on lanes t..31-t and a tile is
+// (32-2T) x (R*WY).
 // No CTA barrier and no shared-memory exchange between warps.
 #pragma once
 
@@ -60,19 +63,22 @@ __device__ __forceinline__ Item decode_item(const SweepGeom& g, int64_t item) {
   return t;
 }
 
+// EDGE is the default at one sweep per pass only: with two sweeps per pass
+// it gains two output columns per tile but stages a wider box (40 instead of
+// 36 FP32 columns), and measured slower on a 512^3 grid and on the batch.
 template <class Pol, int T_, int R_, int WY_, int S_, int MINB_, bool EDGE_ = (T_ == 1)>
 struct TbCfg {
   static constexpr int T = T_, R = R_, WY = WY_, S = S_, MINB = MINB_;
   static constexpr bool RB = false;
   static constexpr bool EDGE = EDGE_;
-  static_assert(!EDGE || T == 1, "edge reads serve a single sweep stage");
   static constexpr int A = 16 / Pol::kElem;      // TMA x granule in elements
-  // Staged columns from the tile's first column - T: 32 lanes (+ A - 1 for
-  // an unaligned start), or, with EDGE, the 34 columns xo-1 .. xo+32 (tiles
-  // start at xo = 1 + 32 k, so xo - 1 is always aligned).
-  static constexpr int BOXW = EDGE ? (34 + A - 1) / A * A : 32 + A;
-  static constexpr int BXO = EDGE ? 32 : 32 - 2 * T;  // output columns per tile
-  static constexpr int XL = EDGE ? 0 : T;        // lane l holds column xo - XL + l
+  // Staged columns from xo - T rounded down to the TMA granule: the 32 lanes
+  // (+ A - 1 for an unaligned start), or, with EDGE, the 34 columns
+  // lane 0 - 1 .. lane 31 + 1 (+ A - 1; at one sweep per pass tiles start
+  // at xo = 1 + 32 k, so xo - 1 is always aligned).
+  static constexpr int BOXW = !EDGE ? 32 + A : (T == 1 ? (34 + A - 1) / A * A : (33 + A + A - 1) / A * A);
+  static constexpr int BXO = EDGE ? 34 - 2 * T : 32 - 2 * T;  // output columns per tile
+  static constexpr int XL = EDGE ? T - 1 : T;    // lane l holds column xo - XL + l
   static constexpr int COL0 = T - XL;            // staged column of lane 0 (after off)
   static constexpr int BYO = R * WY;             // output rows per tile
   static constexpr int NROW = R + 2 * T;         // rows a warp converts per plane
@@ -220,7 +226,7 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
       const C c = st.W[t - 1][MID][rr + 1];
       C xm = __shfl_up_sync(0xffffffffu, c, 1);
       C xp = __shfl_down_sync(0xffffffffu, c, 1);
-      if constexpr (Cfg::EDGE) {
+      if (Cfg::EDGE && t == 1) {
         // Lane 0's left and lane 31's right neighbour, from the staged plane
         // of stage 0's middle plane (held until this step ends); the other
         // lanes read an in-range cell they do not use.  Its y and z are the
