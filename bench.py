@@ -9,11 +9,13 @@ sweeps through stencil_jacobi_sweep.  Metric: GLUP/s (10^9 lattice-site
 updates per second) and the fraction of the measured HBM roofline.
 
 Side measurements on the same line: the same step with FP32 and BF16
-storage, the FP64 residual and the PW advection (512x512x256) throughput,
-the time to relative residual 1e-8 of 16 Poisson problems of 128^3 (plain
-FP64 Jacobi against the mixed-precision batch solve), an end-to-end run
-from pinned host buffers, and the CPU oracle on the host cores (a bounded
-sample).  Inputs (1.1 GB per FP64 field) are larger
+storage, other pass lengths and red-black sweeps; the FP64 residual, the PW
+advection (512x512x256), the 2D average (8192^2), the general linear apply
+(7 terms, 512^3) and the z-slab decomposition (4 virtual ranks) throughput;
+the warm-start net; the 256-instance batch; the time to relative residual
+1e-8 of 16 Poisson problems of 128^3 (plain FP64 Jacobi against the
+mixed-precision batch solve); an end-to-end run from pinned host buffers;
+and the CPU oracle on the host cores (a bounded sample).  Inputs (1.1 GB per FP64 field) are larger
 than the 126 MB L2, so no flush is needed between timed iterations.
 
 Multi-GPU: one process per GPU (torchrun); the work is replicated, not
@@ -481,6 +483,39 @@ def run_ours(args, rank, world, local_rank):
         "frac_of_measured_hbm": round(16 * pts2 / (a2ms * 1e-3) / 1e9 / hbm_peak, 4),
         "note": "binary64 in the order written (bitwise the definition): 4 FP64 instructions per update"}
     del a2, a2t
+    torch.cuda.empty_cache()
+
+    # ---- general linear apply: the 7-point operator as 7 (offset, coefficient)
+    # terms on 512^3, binary64 in the order written -------------------------------
+    li = S.Field.from_numpy(u0, S.F64, device=dev)
+    lo = li.like()
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    coefs = [-6.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0]
+    lms = timed_steps(lambda: S.stencil_apply_linear(ctx, li, lo, offs, coefs), 5, 2)
+    components["apply_linear_7pt_512cubed_f64"] = {
+        "ms": round(lms, 3), "gpts": round(N ** 3 / (lms * 1e-3) / 1e9, 2),
+        "hbm_gbs": round(16 * N ** 3 / (lms * 1e-3) / 1e9, 1),
+        "frac_of_measured_hbm": round(16 * N ** 3 / (lms * 1e-3) / 1e9 / hbm_peak, 4),
+        "note": "one rounded multiply and one rounded add per term in the order given (bitwise the "
+                "definition): 14 FP64 instructions per point, FP64-pipe bound"}
+    del li, lo
+    torch.cuda.empty_cache()
+
+    # ---- z-slab decomposition: 4 virtual ranks on this GPU, one halo-plane
+    # exchange and one sweep of every slab per step, against the whole grid -----
+    from paper_2310_01882_b300 import zslab
+    zus, zex, zfns = zslab.gpu_slabs(u0, f_np, h, 4, ctx=ctx)
+    zsteps = 20
+    zms = timed_steps(lambda: zslab.run([zex], zfns, zsteps), 2, 1)
+    wu = S.Field.from_numpy(u0, S.F64, device=dev)
+    wf = S.Field.from_numpy(f_np, S.F64, device=dev)
+    wt = wu.like()
+    wms = timed_steps(lambda: [S.stencil_jacobi_sweep(ctx, wu, wt, wf, None, h, 1, 1) for _ in range(zsteps)], 2, 1)
+    components["zslab_4_virtual_ranks_512cubed"] = {
+        "glups": round(N ** 3 * zsteps / (zms * 1e-3) / 1e9, 2),
+        "whole_grid_glups": round(N ** 3 * zsteps / (wms * 1e-3) / 1e9, 2),
+        "note": "one sweep per exchange (per-pass fixed point, no work grid), as the whole-grid row beside it"}
+    del zus, zex, zfns, wu, wf, wt
     torch.cuda.empty_cache()
 
     # ---- warm-start network (BF16 tensor-core convolutions) -----------------------
