@@ -9,7 +9,7 @@
  *     a stencil apply is (Section 2.2);
  *   - the Piacsek-Williams flux-form advection of u, v, w (Section 4.1,
  *     three stencils fused into one region, 63 operations per cell);
- * plus the FP64 residual used to judge convergence.
+ * plus the FP64 residual that decides convergence.
  *
  * Conventions (Section 2.2: first index fastest, offsets relative to the
  * cell; Section 3: data crosses the boundary as raw pointers, and, with the
@@ -264,7 +264,7 @@ STENCIL_API int stencil_redblack_config_select(stencil_ctx* ctx, int32_t dtype,
  * stencil_residual -- the residual of A u = f for the 7-point operator
  *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2,
  *     r = f - A u on the interior,
- * always in binary64 (the convergence judge of the iterative solve).
+ * always in binary64 (it decides convergence of the iterative solve).
  *   u, f      F64 grids of equal extents (u's halo is the boundary).
  *   r         NULL, or an F64 grid of the same extents: its interior
  *             receives r (halo untouched).
@@ -352,7 +352,7 @@ STENCIL_API int stencil_batch_solve(stencil_ctx* ctx, const stencil_problem* pro
  * Learned warm start (wsnet_*).  A small 3D U-Net maps the source f of a
  * Poisson problem on an n^3 grid to a starting iterate u0 for the Jacobi
  * solve; the solve (plain Jacobi or stencil_batch_solve) then removes the
- * remaining error, and its residual judges the result.  The paper has no
+ * remaining error, and its residual decides the result.  The paper has no
  * learned component: this is the warm-start pattern layered on the solver.
  * Architecture (levels L <= 4 with per-level channels in {16, 32, 64}): two
  * 3x3x3 convolutions with ReLU per level, 2x2x2 average pooling between

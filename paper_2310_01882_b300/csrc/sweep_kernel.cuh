@@ -217,8 +217,6 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
     const int q = p - t;   // plane this stage updates
     const bool zin = (q >= 1 && q <= nz);
     const T* F = reinterpret_cast<const T*>(ring + ((seq - t) % S) * Cfg::STAGE + Cfg::UB);
-    constexpr int dummy = 0;
-    (void)dummy;
     const int nr = Cfg::R + 2 * (TT - t);  // rows this stage updates
 #pragma unroll
     for (int rr = 0; rr < Cfg::R + 2 * (TT - 1); ++rr) {

@@ -11,8 +11,8 @@ learning-rate decay; on the held-out fields the sweeps and wall time to
 relative residual 1e-8 are measured for a zero start and for the warm start,
 with plain FP64 Jacobi and with the mixed-precision solve
 (stencil_batch_solve, FP32 inner storage).  The residual computed in FP64 is
-the judge throughout.  The warm start's own residual is recorded; the
-"selected" figures use it only when, after `judge_sweeps` plain sweeps from
+the arbiter throughout.  The warm start's own residual is recorded; the
+"selected" figures use it only when, after `check_sweeps` plain sweeps from
 each start, its residual is below the zero start's (the fallback is plain
 Jacobi from zero).  With --together K, K held-out fields are also solved as
 one job (throughput): plain FP64 Jacobi over several streams against the
@@ -181,7 +181,7 @@ def train(net, fs, us, epochs, batch, lr0, seed=0, log=None):
     return hist
 
 
-def evaluate(net, solver, seeds, chunk=200, judge_sweeps=50):
+def evaluate(net, solver, seeds, chunk=200, check_sweeps=50):
     """Sweeps / seconds to RTOL from a zero start and from the warm start,
     with plain FP64 Jacobi and with the mixed-precision batch solve."""
     import torch
@@ -192,7 +192,7 @@ def evaluate(net, solver, seeds, chunk=200, judge_sweeps=50):
         f_np = inputs.grf(n, seed=s)
         f = S.Field.from_numpy(f_np)
         r = {"seed": s}
-        # warm start (inference timed), judged by its FP64 residual
+        # warm start (inference timed), checked by its FP64 residual
         u_w = S.Field(n, n, n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -221,17 +221,17 @@ def evaluate(net, solver, seeds, chunk=200, judge_sweeps=50):
             torch.cuda.synchronize()
             r[f"mixed_{name}"] = {"sweeps": res[0]["sweeps"], "seconds": time.perf_counter() - t0,
                                   "rel": res[0]["rel_residual"], "status": res[0]["status"]}
-        # judge: residual after judge_sweeps plain sweeps from each start
+        # check: residual after check_sweeps plain sweeps from each start
         rels = {}
         for name, start in (("zero", None), ("warm", warm0)):
             u = S.Field(n, n, n)
             if start is not None:
                 u.storage.copy_(start)
-            S.stencil_jacobi_sweep(ctx, u, solver.tmp[0], f, None, h, judge_sweeps, 0, S.SWEEP_AUTO)
+            S.stencil_jacobi_sweep(ctx, u, solver.tmp[0], f, None, h, check_sweeps, 0, S.SWEEP_AUTO)
             S.stencil_residual(ctx, u, f, h, solver.norms[0])
             nrm = solver.norms[0].cpu().numpy()
             rels[name] = float(nrm[0] / nrm[1])
-        r["judge_rel"] = rels
+        r["check_rel"] = rels
         r["fallback"] = not (rels["warm"] < rels["zero"])
         rows.append(r)
     return rows
@@ -271,7 +271,7 @@ def solve_together(solver, fs, starts, kind, chunk=200, sweeps_per_cycle=400):
         sweeps = [r["sweeps"] for r in res]
         rels = [r["rel_residual"] for r in res]
         ok = all(r["status"] == 0 and r["rel_residual"] <= RTOL for r in res)
-    # the FP64 residual of every returned u is the judge
+    # the FP64 residual of every returned u decides
     worst = 0.0
     for u, f in zip(us, fs):
         S.stencil_residual(solver.ctxs[0], u, f, h, solver.norms[0])
@@ -323,7 +323,7 @@ def summarise(rows):
                                    for k in ("fp64_warm", "mixed_zero", "mixed_warm")}
     out["warm_rel0_median"] = float(np.median([r["warm_rel0"] for r in rows]))
     out["fallbacks"] = int(sum(1 for r in rows if r.get("fallback")))
-    # with the fallback applied: the warm start only where the judge accepted it
+    # with the fallback applied: the warm start only where the check accepted it
     sel = []
     for r in rows:
         k = "mixed_zero" if r.get("fallback") else "mixed_warm"
