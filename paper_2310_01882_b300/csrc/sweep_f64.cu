@@ -24,8 +24,8 @@ int sweep_variants_f64(int policy, int T, const SweepVariant** out) {
       // of this shape, 0.710 against 0.724 ms per sweep at 512^3
       variant<PolResident, TbCfg<PolResident, 2, 4, 4, 5, 2, true>>(),
   };
-  static const SweepVariant fix1[] = {variant<PolFixed, TbCfg<PolFixed, 1, 8, 4, 4, 3>>(),
-                                      variant<PolFixed, TbCfg<PolFixed, 1, 2, 16, 5, 1>>()};
+  static const SweepVariant fix1[] = {variant<PolFixed, TbCfg<PolFixed, 1, 2, 16, 5, 1>>(),
+                                      variant<PolFixed, TbCfg<PolFixed, 1, 8, 4, 4, 3>>()};
   static const SweepVariant f641[] = {variant<PolF64, TbCfg<PolF64, 1, 8, 4, 4, 3>>()};
   if (policy == kPolResident && T == 1) { *out = res1; return sizeof(res1) / sizeof(res1[0]); }
   if (policy == kPolResident && T == 2) { *out = res2; return sizeof(res2) / sizeof(res2[0]); }
