@@ -71,9 +71,19 @@ def test_chosen_config_parses_autotune_report():
            "chosen: T=2\n")
     assert bench.chosen_config(rep, 1, "PolResident") == "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>"
     assert bench.chosen_config(rep, 2, "PolResident") == "jacobi_tb<PolResident,T=2,R=2,WY=4,S=6>"
-    # every one-sweep key of the measured-traffic table names a compiled shape
-    for key in bench.MEASURED_TRAFFIC:
-        assert key.startswith("jacobi_tb<PolResident,T=1,")
+    # the index is the position among that pass length's lines (registry order)
+    assert bench.chosen_config(rep, 1, "PolResident", with_index=True)[1] == 2
+    assert bench.chosen_config(rep, 2, "PolResident", with_index=True)[1] == 0
+    assert bench.chosen_config("", 1, "PolResident", with_index=True)[1] == 0
+    # the measured-traffic table covers exactly the compiled one-sweep shapes
+    # of the resident fixed-point policy
+    import re
+    src = open(os.path.join(ROOT, "paper_2310_01882_b300", "csrc", "sweep_f64.cu")).read()
+    block = src[src.index("res1[] = {"):src.index("};", src.index("res1[] = {"))]
+    shapes = {f"jacobi_tb<PolResident,T=1,R={r},WY={wy},S={st}>"
+              for r, wy, st in re.findall(r"TbCfg<PolResident, 1, (\d+), (\d+), (\d+), \d+>", block)}
+    assert len(shapes) >= 2
+    assert set(bench.MEASURED_TRAFFIC) == shapes
 
 
 def test_wsnet_flops_matches_layer_count():
