@@ -501,21 +501,26 @@ def run_ours(args, rank, world, local_rank):
     del li, lo
     torch.cuda.empty_cache()
 
-    # ---- z-slab decomposition: 4 virtual ranks on this GPU, one halo-plane
-    # exchange and one sweep of every slab per step, against the whole grid -----
+    # ---- z-slab decomposition: 4 virtual ranks on this GPU, a halo exchange
+    # every `depth` sweeps, against the whole grid swept in calls of as many
+    # sweeps --------------------------------------------------------------------
     from paper_2310_01882_b300 import zslab
-    zus, zex, zfns = zslab.gpu_slabs(u0, f_np, h, 4, ctx=ctx)
-    zsteps = 20
-    zms = timed_steps(lambda: zslab.run([zex], zfns, zsteps), 2, 1)
     wu = S.Field.from_numpy(u0, S.F64, device=dev)
     wf = S.Field.from_numpy(f_np, S.F64, device=dev)
-    wt = wu.like()
-    wms = timed_steps(lambda: [S.stencil_jacobi_sweep(ctx, wu, wt, wf, None, h, 1, 1) for _ in range(zsteps)], 2, 1)
-    components["zslab_4_virtual_ranks_512cubed"] = {
-        "glups": round(N ** 3 * zsteps / (zms * 1e-3) / 1e9, 2),
-        "whole_grid_glups": round(N ** 3 * zsteps / (wms * 1e-3) / 1e9, 2),
-        "note": "one sweep per exchange (per-pass fixed point, no work grid), as the whole-grid row beside it"}
-    del zus, zex, zfns, wu, wf, wt
+    wt, ww = wu.like(), S.Field(N, N, N, S.F64, dev)
+    zrow = {"ranks": 4, "note": "virtual ranks: slabs of one GPU, plane copies in stream order; the whole-grid "
+                                "figure sweeps the same number of sweeps per call"}
+    for depth, zsw in ((1, 16), (8, 32)):
+        zus, zex, zfns = zslab.gpu_slabs(u0, f_np, h, 4, ctx=ctx, depth=depth)
+        zms = timed_steps(lambda: zslab.run([zex], zfns, zsw, depth), 2, 1)
+        wms = timed_steps(lambda: [S.stencil_jacobi_sweep(ctx, wu, wt, wf, ww, h, depth, 0)
+                                   for _ in range(zsw // depth)], 2, 1)
+        zrow[f"depth{depth}"] = {"glups": round(N ** 3 * zsw / (zms * 1e-3) / 1e9, 2),
+                                 "whole_grid_glups": round(N ** 3 * zsw / (wms * 1e-3) / 1e9, 2)}
+        del zus, zex, zfns
+        torch.cuda.empty_cache()
+    components["zslab_4_virtual_ranks_512cubed"] = zrow
+    del wu, wf, wt, ww
     torch.cuda.empty_cache()
 
     # ---- warm-start network (BF16 tensor-core convolutions) -----------------------
