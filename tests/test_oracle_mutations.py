@@ -1,7 +1,8 @@
 """The oracle's pins must catch plausible mistakes.
 
 Each case plants one mistake in a copy of oracle.c (on the CPU: a swapped
-neighbour, a sign, a transposed axis, a swapped coefficient, a dropped term),
+neighbour, a sign, a transposed axis, a swapped coefficient, a dropped term,
+a correction solve that does not restart from zero, a wrong escalation),
 builds it into a temporary library and runs the pin suites against it in a
 subprocess (ORACLE_LIB).  The pins must fail for every mutant."""
 import os
@@ -13,7 +14,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
 PINS = ["tests/test_oracle_jacobi.py", "tests/test_oracle_residual.py", "tests/test_oracle_advect.py",
-        "tests/test_oracle_rbgs.py", "tests/test_oracle_average2d.py", "tests/test_oracle_apply_linear.py"]
+        "tests/test_oracle_rbgs.py", "tests/test_oracle_average2d.py", "tests/test_oracle_apply_linear.py",
+        "tests/test_oracle_refine.py"]
 
 MUTANTS = {
     "sweep_z_as_y": ("s += AT(u, i, j, k + 1);\n        s += hh", "s += AT(u, i, j + 1, k);\n        s += hh"),
@@ -37,6 +39,14 @@ MUTANTS = {
                            "AT(in, i + offsets[3 * p + 1], j + offsets[3 * p], k + offsets[3 * p + 2])"),
     "rb_drop_source": ("s += hh * AT(f, i, j, k);\n            AT(u, i, j, k) = s / 6.0;",
                        "s += 0.0 * AT(f, i, j, k);\n            AT(u, i, j, k) = s / 6.0;"),
+    # mixed-precision refinement
+    "refine_no_restart_f64": ("memset(e64, 0, len * sizeof(double));", ";"),
+    "refine_correction_sign": ("AT(u, i, j, k) = AT(u, i, j, k) + AT(e, i, j, k);",
+                               "AT(u, i, j, k) = AT(u, i, j, k) - AT(e, i, j, k);"),
+    "refine_absolute_residual": ("double rel = norms[1] > 0.0 ? norms[0] / norms[1] : norms[0];",
+                                 "double rel = norms[0];"),
+    "refine_escalate_to_f64": ("if (cur == 2) {\n        cur = 1;", "if (cur == 2) {\n        cur = 0;"),
+    "refine_f32_start_from_r": ("r32[q] = (float)r[q]; e32[q] = 0.0f;", "r32[q] = (float)r[q]; e32[q] = r32[q];"),
 }
 
 
