@@ -65,3 +65,68 @@ def test_pins_catch_mutant(name, tmp_path):
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", *PINS],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"mutant {name} survived the pins:\n{res.stdout[-2000:]}"
+
+
+NET_SRC = os.path.join(ROOT, "oracle", "net.py")
+NET_MUTANTS = {
+    "conv_tap_flipped": ("out += pad[dz:dz + D, dy:dy + H, dx:dx + Wd, :] @ W[dz, dy, dx]",
+                         "out += pad[dz:dz + D, dy:dy + H, dx:dx + Wd, :] @ W[2 - dz, dy, dx]"),
+    "conv_bwd_wrong_tap": ("dpad[dz:dz + D, dy:dy + H, dx:dx + Wd, :] += g @ W[dz, dy, dx].T",
+                           "dpad[dz:dz + D, dy:dy + H, dx:dx + Wd, :] += g @ W[dz, dy, 2 - dx].T"),
+    "pool_bwd_scale": ("0), 2, 1), 2, 2) / 8.0", "0), 2, 1), 2, 2) / 4.0"),
+    "skip_dropped_in_backward": ("g = g + gskip[l]", "g = g"),
+    "relu_mask_of_other_layer": ('g = g * (cache[f"enc{l}b.out"] > 0)', 'g = g * (cache[f"enc{l}a.out"] > 0)'),
+    "filter_weights": ("y = 0.25 * p[sl(0, n)] + 0.5 * p[sl(1, n + 1)] + 0.25 * p[sl(2, n + 2)]",
+                       "y = 0.25 * p[sl(0, n)] + 0.5 * p[sl(1, n + 1)] + 0.2 * p[sl(2, n + 2)]"),
+    "mse_grad_half": ("return float(np.mean(d * d)), 2.0 * d / d.size", "return float(np.mean(d * d)), d / d.size"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(NET_MUTANTS))
+def test_net_pins_catch_mutant(name, tmp_path):
+    """The same for the FP64 network oracle (oracle/net.py): a copy of the
+    oracle package with one planted mistake shadows the real one on the
+    pins' import path."""
+    import shutil
+    import oracle
+    old, new = NET_MUTANTS[name]
+    src = open(NET_SRC).read()
+    assert src.count(old) >= 1, name
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so", "_build"))
+    (pkg / "net.py").write_text(src.replace(old, new, 1))
+    env = dict(os.environ, ORACLE_LIB=oracle.lib()._name,
+               PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT, os.environ.get("PYTHONPATH", "")]))
+    # run from the copy's parent, so that it comes first on the import path
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_net.py")], cwd=str(tmp_path), env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"mutant {name} survived the pins:\n{res.stdout[-2000:]}"
+
+
+def test_net_mutation_harness_passes_unmutated(tmp_path):
+    """Control: the shadowing copy without a mutation passes the pins (so a
+    failure above is the planted mistake's)."""
+    import shutil
+    import oracle
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so", "_build"))
+    env = dict(os.environ, ORACLE_LIB=oracle.lib()._name,
+               PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT, os.environ.get("PYTHONPATH", "")]))
+    res = subprocess.run([sys.executable, "-c", "import oracle, sys; print(oracle.__file__)"], cwd=str(tmp_path),
+                         env=env, capture_output=True, text=True, timeout=120)
+    assert str(tmp_path) in res.stdout, res.stdout + res.stderr
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_net.py")], cwd=str(tmp_path), env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:]
+    # and it is the copy that the pins import
+    probe = tmp_path / "probe_test.py"
+    probe.write_text("import oracle\n\ndef test_probe():\n    assert oracle.__file__.startswith(%r)\n"
+                     % str(tmp_path))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", "-c",
+                          os.path.join(ROOT, "pytest.ini"), "--rootdir", ROOT, str(probe)], cwd=str(tmp_path),
+                         env=env, capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stdout[-2000:]
