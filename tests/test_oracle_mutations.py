@@ -47,6 +47,10 @@ MUTANTS = {
                                  "double rel = norms[0];"),
     "refine_escalate_to_f64": ("if (cur == 2) {\n        cur = 1;", "if (cur == 2) {\n        cur = 0;"),
     "refine_f32_start_from_r": ("r32[q] = (float)r[q]; e32[q] = 0.0f;", "r32[q] = (float)r[q]; e32[q] = r32[q];"),
+    # reduced-precision storage
+    "bf16_truncates": ("x += 0x7fffu + lsb;", "x += 0u * lsb;"),
+    "f32_sweep_z_as_y": ("        s += AT(u, i, j, k + 1);\n        s += hh * AT(f, i, j, k);\n        AT(out, i, j, k) = s / 6.0f;",
+                         "        s += AT(u, i, j + 1, k);\n        s += hh * AT(f, i, j, k);\n        AT(out, i, j, k) = s / 6.0f;"),
 }
 
 
