@@ -47,3 +47,22 @@ def test_host_side_validation_without_gpu(lib):
     assert rc == -1
     assert b"null ctx" in lib.stencil_last_error()
     assert lib.stencil_version().startswith(b"b300-stencil")
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """include/stencil.h is plain C: a C99 program that takes the address of
+    every declared entry point compiles with -Wall -Werror and links against
+    the library (nothing is called: no GPU needed)."""
+    import subprocess
+    names = sorted(declared_symbols())
+    src = tmp_path / "use_abi.c"
+    body = "\n".join(f"  fns[{i}] = (void (*)(void)){n};" for i, n in enumerate(names))
+    src.write_text('#include "stencil.h"\n#include <stddef.h>\n'
+                   f"void (*fns[{len(names)}])(void);\n"
+                   "int main(void) {\n" + body + "\n  return fns[0] == NULL;\n}\n")
+    libdir = os.path.dirname(lib._name)
+    res = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-Wno-pedantic", "-I",
+                          os.path.join(ROOT, "include"), str(src), "-o", str(tmp_path / "use_abi"),
+                          "-L", libdir, "-lstencil", f"-Wl,-rpath,{libdir}"],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
