@@ -1,0 +1,120 @@
+"""Canary guard zones (memory safety without a sanitizer): every caller
+buffer sits inside a larger allocation whose bytes before and after it, and
+the padding columns at the end of each of its rows, hold a known pattern.
+After each library call the pattern must be intact: no kernel writes outside
+the cells it owns (interior, or halo for scratch grids), whatever the tile
+shape, pass length, precision or grid raggedness."""
+import numpy as np
+import pytest
+
+from paper_2310_01882_b300 import inputs
+from paper_2310_01882_b300 import stencil as S
+from tests.gpu_util import ctx
+
+pytestmark = pytest.mark.gpu
+
+CANARY = 0xA5
+GUARD_BYTES = 4096
+SHAPES = [(37, 19, 11), (64, 32, 9), (3, 2, 5)]
+
+
+class Guarded:
+    """A Field placed in the middle of a canary-filled buffer."""
+
+    def __init__(self, nx, ny, nz, dtype=S.F64, values=None):
+        import torch
+        tdt = {S.F64: torch.float64, S.F32: torch.float32, S.BF16: torch.bfloat16}[dtype]
+        elem = S.ELEM[dtype]
+        g = 16 // elem
+        sy = (nx + 2 + g - 1) // g * g
+        self.n = (nz + 2) * (ny + 2) * sy
+        self.G = GUARD_BYTES // elem
+        self.buf = torch.empty(self.G + self.n + self.G, dtype=tdt, device="cuda")
+        self.buf.view(torch.uint8).fill_(CANARY)
+        storage = self.buf[self.G:self.G + self.n].view(nz + 2, ny + 2, sy)
+        self.field = S.Field(nx, ny, nz, dtype, storage=storage)
+        if values is not None:
+            self.field.cells.copy_(torch.from_numpy(np.ascontiguousarray(values)).to("cuda", tdt))
+
+    def intact(self):
+        import torch
+        torch.cuda.synchronize()
+        raw = self.buf.view(torch.uint8)
+        elem = self.buf.element_size()
+        before = raw[:self.G * elem]
+        after = raw[(self.G + self.n) * elem:]
+        pad = self.field.storage[:, :, self.field.nx + 2:]
+        ok = bool((before == CANARY).all()) and bool((after == CANARY).all())
+        if pad.shape[-1]:
+            ok = ok and bool((pad.contiguous().view(torch.uint8) == CANARY).all())
+        return ok
+
+
+def problem(shape, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    return u, f, 1.0 / (max(shape) + 1)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype,flags,work,spp", [
+    (S.F64, S.SWEEP_FP64_FIXED, True, 0), (S.F64, S.SWEEP_FP64_FIXED, True, 2),
+    (S.F64, S.SWEEP_FP64_FIXED, False, 1), (S.F64, S.SWEEP_FP64_NATIVE, False, 1),
+    (S.F32, 0, False, 1), (S.F32, 0, False, 2), (S.F32, 0, False, 4), (S.BF16, 0, False, 1), (S.BF16, 0, False, 2)])
+@pytest.mark.parametrize("redblack", [False, True])
+def test_sweeps_stay_in_bounds(shape, dtype, flags, work, spp, redblack):
+    if redblack and spp > 2:
+        pytest.skip("red-black passes hold one or two sweeps")
+    if redblack and spp == 2 and dtype == S.F64:
+        pytest.skip("FP64 red-black passes hold one sweep")
+    u, f, h = problem(shape, seed=sum(shape))
+    gu, gt, gf = Guarded(*shape, dtype, u), Guarded(*shape, dtype), Guarded(*shape, dtype, f)
+    gw = Guarded(*shape) if work else None
+    fn = S.stencil_redblack_sweep if redblack else S.stencil_jacobi_sweep
+    fn(ctx(), gu.field, gt.field, gf.field, gw.field if gw else None, h, 7, spp, flags)
+    S.stencil_ctx_status(ctx())
+    for g in (gu, gt, gf) + ((gw,) if gw else ()):
+        assert g.intact()
+    assert np.isfinite(gu.field.to_numpy()).all()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_residual_advect_average_apply_stay_in_bounds(shape):
+    import torch
+    u, f, h = problem(shape, seed=3)
+    gu, gf, gr = Guarded(*shape, values=u), Guarded(*shape, values=f), Guarded(*shape)
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    S.stencil_residual(ctx(), gu.field, gf.field, h, norms, r=gr.field)
+    assert gu.intact() and gf.intact() and gr.intact()
+    nx, ny, nz = shape
+    winds = inputs.winds(nx, ny, nz, seeds=(4, 5, 6))
+    gin = [Guarded(*shape, values=a) for a in winds]
+    gout = [Guarded(*shape) for _ in range(3)]
+    t1 = torch.from_numpy(inputs.tzc(nz, 7)).cuda()
+    t2 = torch.from_numpy(inputs.tzc(nz, 8)).cuda()
+    S.stencil_advect_uvw(ctx(), *(g.field for g in gin), *(g.field for g in gout), t1, t2, 0.25, 0.25)
+    assert all(g.intact() for g in gin + gout)
+    ga, gb = Guarded(*shape, values=u), Guarded(*shape)
+    S.stencil_average2d(ctx(), ga.field, gb.field, 3)
+    assert ga.intact() and gb.intact()
+    gi, go = Guarded(*shape, values=u), Guarded(*shape)
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 1), (1, 1, -1)]
+    S.stencil_apply_linear(ctx(), gi.field, go.field, offs, [1.0, -2.0, 0.5, 0.25, 3.0])
+    assert gi.intact() and go.intact()
+
+
+def test_batch_solve_stays_in_bounds():
+    sizes = [(37, 19, 11), (20, 20, 20), (5, 3, 2)]
+    gus, gfs = [], []
+    for i, s in enumerate(sizes):
+        u, f, _ = problem(s, seed=40 + i)
+        gus.append(Guarded(*s, values=np.zeros_like(u)))
+        gfs.append(Guarded(*s, values=f))
+    for inner in (S.F32, S.BF16):
+        res = S.stencil_batch_solve(ctx(), [g.field for g in gus], [g.field for g in gfs],
+                                    [1.0 / (max(s) + 1) for s in sizes], 1e-8, inner_dtype=inner,
+                                    sweeps_per_cycle=100)
+        assert all(r["status"] == 0 for r in res)
+        assert all(g.intact() for g in gus + gfs)
