@@ -395,11 +395,15 @@ STENCIL_API int wsnet_infer(wsnet* net, const stencil_grid* f,
 STENCIL_API int wsnet_train_step(wsnet* net, const stencil_grid* f,
                                  const stencil_grid* u, int32_t count,
                                  float lr, double* loss, void* stream);
-/* Save the net's configuration and FP32 parameters to a file (8-byte magic
- * "WSNET01", int32 levels, int32 channels[levels], int32 n, int64
- * parameter count, the parameters in wsnet_get_params order; little
- * endian); load them into a net created with the same levels, channels and
- * n (STENCIL_ERR_ARG on a mismatch or an unreadable file; the net is then
+/* Save a training checkpoint: the net's configuration, FP32 parameters and
+ * Adam state (8-byte magic "WSNET02", int32 levels, int32
+ * channels[levels], int32 n, int64 parameter count, the parameters in
+ * wsnet_get_params order, int64 Adam step count, the first and second
+ * moments in the same order; little endian).  Load one into a net created
+ * with the same levels, channels and n: training then continues exactly as
+ * if it had not stopped.  Files with the magic "WSNET01" (parameters only,
+ * no optimiser state) load too, with the optimiser restarted.
+ * STENCIL_ERR_ARG on a mismatch or an unreadable file (the net is then
  * unchanged).  Synchronous. */
 STENCIL_API int wsnet_save(wsnet* net, const char* path);
 STENCIL_API int wsnet_load(wsnet* net, const char* path);

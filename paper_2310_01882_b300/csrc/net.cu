@@ -1307,27 +1307,40 @@ extern "C" int wsnet_set_params(wsnet* w, const float* host, int64_t count) {
   return rc;
 }
 
-// File layout of wsnet_save / wsnet_load (little endian): 8 bytes "WSNET01\0",
+// File layout of wsnet_save / wsnet_load (little endian): 8 bytes magic,
 // int32 levels, int32 channels[levels], int32 n, int64 parameter count,
-// then the FP32 parameters in wsnet_get_params order.
-static const char kWsMagic[8] = {'W', 'S', 'N', 'E', 'T', '0', '1', 0};
+// the FP32 parameters in wsnet_get_params order; with the magic "WSNET02"
+// (what wsnet_save writes) the optimiser state follows: int64 Adam step
+// count, then the FP32 first and second moments in the same order.  Files
+// with the magic "WSNET01" hold the parameters only; loading one starts the
+// optimiser afresh (zero moments, step 0).
+static const char kWsMagic1[8] = {'W', 'S', 'N', 'E', 'T', '0', '1', 0};
+static const char kWsMagic2[8] = {'W', 'S', 'N', 'E', 'T', '0', '2', 0};
 
 extern "C" int wsnet_save(wsnet* w, const char* path) {
   if (!w || !path) return set_error(STENCIL_ERR_ARG, "wsnet_save: bad arguments");
-  std::vector<float> host(static_cast<size_t>(w->nparams));
+  const size_t np = static_cast<size_t>(w->nparams);
+  std::vector<float> host(3 * np);
   int rc = wsnet_get_params(w, host.data(), w->nparams);
+  if (rc) return rc;
+  DevGuard dg(w->device);
+  rc = check_cuda(cudaMemcpy(host.data() + np, w->m, sizeof(float) * np, cudaMemcpyDeviceToHost), "wsnet_save m");
+  if (!rc) rc = check_cuda(cudaMemcpy(host.data() + 2 * np, w->v, sizeof(float) * np, cudaMemcpyDeviceToHost),
+                           "wsnet_save v");
   if (rc) return rc;
   FILE* fp = fopen(path, "wb");
   if (!fp) return set_error(STENCIL_ERR_ARG, "wsnet_save: cannot open %s", path);
   const int32_t hdr[2] = {w->L, w->n};
-  bool ok = fwrite(kWsMagic, 1, 8, fp) == 8 && fwrite(&hdr[0], 4, 1, fp) == 1;
+  bool ok = fwrite(kWsMagic2, 1, 8, fp) == 8 && fwrite(&hdr[0], 4, 1, fp) == 1;
   for (int l = 0; l < w->L && ok; ++l) {
     const int32_t c = w->C[l];
     ok = fwrite(&c, 4, 1, fp) == 1;
   }
   const int64_t cnt = w->nparams;
+  const int64_t step = w->step;
   ok = ok && fwrite(&hdr[1], 4, 1, fp) == 1 && fwrite(&cnt, 8, 1, fp) == 1 &&
-       fwrite(host.data(), sizeof(float), host.size(), fp) == host.size();
+       fwrite(host.data(), sizeof(float), np, fp) == np && fwrite(&step, 8, 1, fp) == 1 &&
+       fwrite(host.data() + np, sizeof(float), 2 * np, fp) == 2 * np;
   ok = (fclose(fp) == 0) && ok;
   return ok ? STENCIL_OK : set_error(STENCIL_ERR_ARG, "wsnet_save: write to %s failed", path);
 }
@@ -1338,22 +1351,34 @@ extern "C" int wsnet_load(wsnet* w, const char* path) {
   if (!fp) return set_error(STENCIL_ERR_ARG, "wsnet_load: cannot open %s", path);
   char magic[8];
   int32_t L = 0, n = 0;
-  int64_t cnt = 0;
-  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kWsMagic, 8) == 0 && fread(&L, 4, 1, fp) == 1 &&
-            L == w->L;
+  int64_t cnt = 0, step = 0;
+  bool ok = fread(magic, 1, 8, fp) == 8;
+  const bool v1 = ok && memcmp(magic, kWsMagic1, 8) == 0;
+  const bool v2 = ok && memcmp(magic, kWsMagic2, 8) == 0;
+  ok = (v1 || v2) && fread(&L, 4, 1, fp) == 1 && L == w->L;
   for (int l = 0; l < L && ok; ++l) {
     int32_t c = 0;
     ok = fread(&c, 4, 1, fp) == 1 && c == w->C[l];
   }
   ok = ok && fread(&n, 4, 1, fp) == 1 && n == w->n && fread(&cnt, 8, 1, fp) == 1 && cnt == w->nparams;
+  const size_t np = static_cast<size_t>(w->nparams);
   std::vector<float> host;
   if (ok) {
-    host.resize(static_cast<size_t>(cnt));
-    ok = fread(host.data(), sizeof(float), host.size(), fp) == host.size();
+    host.assign(3 * np, 0.0f);  // parameters, then the moments (zero for a parameters-only file)
+    ok = fread(host.data(), sizeof(float), np, fp) == np;
+    if (ok && v2)
+      ok = fread(&step, 8, 1, fp) == 1 && step >= 0 && fread(host.data() + np, sizeof(float), 2 * np, fp) == 2 * np;
   }
   fclose(fp);
   if (!ok) return set_error(STENCIL_ERR_ARG, "wsnet_load: %s is not a file of a net of this configuration", path);
-  return wsnet_set_params(w, host.data(), cnt);
+  int rc = wsnet_set_params(w, host.data(), cnt);
+  if (rc) return rc;
+  DevGuard dg(w->device);
+  rc = check_cuda(cudaMemcpy(w->m, host.data() + np, sizeof(float) * np, cudaMemcpyHostToDevice), "wsnet_load m");
+  if (!rc) rc = check_cuda(cudaMemcpy(w->v, host.data() + 2 * np, sizeof(float) * np, cudaMemcpyHostToDevice),
+                           "wsnet_load v");
+  if (!rc) w->step = step;
+  return rc;
 }
 
 extern "C" int wsnet_infer(wsnet* w, const stencil_grid* f, const stencil_grid* u, void* stream) {

@@ -161,13 +161,26 @@ def generate_pairs(solver, seeds):
     return fs, us, info
 
 
-def train(net, fs, us, epochs, batch, lr0, seed=0, log=None):
-    """Adam with a cosine decay from lr0 to lr0/20 over all steps."""
+def train(net, fs, us, epochs, batch, lr0, seed=0, log=None, ckpt_dir=None, stop_after=None):
+    """Adam with a cosine decay from lr0 to lr0/20 over all steps.  With
+    ckpt_dir, a checkpoint is written after every epoch (the net with its
+    Adam state, wsnet_save; the epoch, step count, loss history and the
+    batch-order generator's state) and, if one is there already, training
+    resumes after its epoch exactly as if it had not stopped.  stop_after:
+    return after that many epochs (of `epochs`) in this call."""
     rng = np.random.default_rng(seed)
     steps = epochs * max(1, len(fs) // batch)
     hist = []
     step = 0
-    for ep in range(epochs):
+    ep0 = 0
+    state_path = os.path.join(ckpt_dir, "train_state.json") if ckpt_dir else None
+    if state_path and os.path.exists(state_path):
+        with open(state_path) as fh:
+            st = json.load(fh)
+        S.wsnet_load(net, os.path.join(ckpt_dir, "wsnet.ckpt"))
+        rng.bit_generator.state = st["rng"]
+        hist, step, ep0 = st["hist"], st["step"], st["epoch"] + 1
+    for ep in range(ep0, epochs if stop_after is None else min(epochs, stop_after)):
         order = rng.permutation(len(fs))
         losses = []
         for b in range(0, len(fs) - batch + 1, batch):
@@ -178,6 +191,13 @@ def train(net, fs, us, epochs, batch, lr0, seed=0, log=None):
         hist.append(float(np.mean(losses)))
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.4e}")
+        if ckpt_dir:
+            os.makedirs(ckpt_dir, exist_ok=True)
+            S.wsnet_save(net, os.path.join(ckpt_dir, "wsnet.ckpt.tmp"))
+            os.replace(os.path.join(ckpt_dir, "wsnet.ckpt.tmp"), os.path.join(ckpt_dir, "wsnet.ckpt"))
+            with open(state_path + ".tmp", "w") as fh:
+                json.dump({"epoch": ep, "step": step, "hist": hist, "rng": rng.bit_generator.state}, fh)
+            os.replace(state_path + ".tmp", state_path)
     return hist
 
 
@@ -347,6 +367,8 @@ def main():
                     help="also time solving this many held-out fields as one job")
     ap.add_argument("--kinds", default="fp64,f32,bf16",
                     help="solvers of the --together comparison (fp64, fp64rb, f32, f32rb, bf16)")
+    ap.add_argument("--checkpoint", default=None,
+                    help="directory for per-epoch training checkpoints (resumes from one found there)")
     ap.add_argument("--out", default=".")
     args = ap.parse_args()
     import torch
@@ -365,7 +387,7 @@ def main():
         gen_s = time.perf_counter() - t0
         log(f"generated {args.train} pairs in {gen_s:.1f} s; sweeps median {np.median([s for s, _ in info])}")
         t0 = time.perf_counter()
-        hist = train(net, fs, us, args.epochs, args.batch, args.lr, log=log)
+        hist = train(net, fs, us, args.epochs, args.batch, args.lr, log=log, ckpt_dir=args.checkpoint)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         del fs, us

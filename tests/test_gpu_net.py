@@ -187,3 +187,34 @@ def test_save_load_roundtrip(tmp_path):
     assert np.array_equal(before, c.get_params())
     for net in (a, b, c):
         net.close()
+
+
+def test_checkpoint_resumes_training_exactly(tmp_path):
+    """A checkpoint holds the parameters and the Adam state (moments and
+    step count): training k steps, saving, loading into a fresh net and
+    training k more gives bit for bit the parameters of 2k uninterrupted
+    steps; a parameters-only load (the older file kind) does not."""
+    n = 16
+    fs = [S.Field.from_numpy(inputs.grf(n, seed=60 + i)) for i in range(4)]
+    us = [S.Field.from_numpy(0.01 * inputs.grf(n, seed=70 + i)) for i in range(4)]
+
+    def steps(net, first, last):
+        for s in range(first, last):
+            S.wsnet_train_step(net, fs[2 * (s % 2):2 * (s % 2) + 2], us[2 * (s % 2):2 * (s % 2) + 2], 1e-3)
+
+    ref = S.WsNet(2, [16, 32], n, seed=31)
+    steps(ref, 0, 6)
+    a = S.WsNet(2, [16, 32], n, seed=31)
+    steps(a, 0, 3)
+    path = str(tmp_path / "ckpt.bin")
+    S.wsnet_save(a, path)
+    b = S.WsNet(2, [16, 32], n, seed=99)
+    S.wsnet_load(b, path)
+    steps(b, 3, 6)
+    assert np.array_equal(b.get_params(), ref.get_params())
+    c = S.WsNet(2, [16, 32], n, seed=99)
+    c.set_params(a.get_params())   # parameters only: the optimiser restarts
+    steps(c, 3, 6)
+    assert not np.array_equal(c.get_params(), ref.get_params())
+    for net in (ref, a, b, c):
+        net.close()

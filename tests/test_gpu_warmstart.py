@@ -43,3 +43,22 @@ def test_solve_together_every_kind(solver, kind):
                                                      sweeps_per_cycle=100)
     assert ok and worst <= warmstart.RTOL
     assert len(sweeps) == 2 and min(sweeps) > 0
+
+
+def test_training_checkpoint_resumes_exactly(tmp_path):
+    """Three epochs in one go, and a run stopped after one epoch then
+    resumed from its checkpoint (in a fresh net) for the other two, give the
+    same parameters and loss history bit for bit."""
+    n = 16
+    fs = warmstart.make_fields(n, [700 + i for i in range(6)])
+    us = [S.Field.from_numpy(0.01 * inputs.grf(n, seed=800 + i)) for i in range(6)]
+    ref = S.WsNet(2, [16, 32], n, seed=5)
+    h_ref = warmstart.train(ref, fs, us, 3, 2, 1e-3, seed=3)
+    a = S.WsNet(2, [16, 32], n, seed=5)
+    warmstart.train(a, fs, us, 3, 2, 1e-3, seed=3, ckpt_dir=str(tmp_path), stop_after=1)
+    b = S.WsNet(2, [16, 32], n, seed=77)
+    h = warmstart.train(b, fs, us, 3, 2, 1e-3, seed=3, ckpt_dir=str(tmp_path))
+    assert np.array_equal(b.get_params(), ref.get_params())
+    assert h == h_ref
+    for net in (ref, a, b):
+        net.close()
