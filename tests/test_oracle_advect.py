@@ -114,3 +114,34 @@ def test_self_term_telescopes_on_periodic_line():
     assert np.max(np.abs(interior(su).sum(axis=2))) <= 1e-13 * np.max(np.abs(su))
     _, sv, _ = run(z, u, z, t1, t2)
     assert np.max(np.abs(interior(sv).sum(axis=1))) <= 1e-13 * np.max(np.abs(sv))
+
+
+def test_self_terms_antisymmetric_under_reflection():
+    """Reflecting a direction and negating the advected component maps each
+    self-advection term to minus its value at the mirrored cell: with
+    u'[i] = -u[N+1-i] along a periodic x line (v = w = 0), su'(i) =
+    -su(N+1-i); likewise sv along a periodic y line, and sw along z with
+    zero halo planes and tzc1 = tzc2 constant.  Exact in binary64 (the
+    same products, negated)."""
+    rng = np.random.default_rng(12)
+    z = np.zeros((NZ + 2, NY + 2, NX + 2))
+    t = np.full(NZ, 0.8)
+    # x: periodic halo, random interior
+    u = inputs.fill_periodic_xy(np.pad(rng.standard_normal((NZ, NY, NX)), 1))
+    ur = -u[:, :, ::-1].copy()
+    su, _, _ = run(u, z, z, t, t)
+    sur, _, _ = run(ur, z, z, t, t)
+    np.testing.assert_array_equal(interior(sur), -interior(su)[:, :, ::-1])
+    # y
+    v = inputs.fill_periodic_xy(np.pad(rng.standard_normal((NZ, NY, NX)), 1))
+    vr = -v[:, ::-1, :].copy()
+    _, sv, _ = run(z, v, z, t, t)
+    _, svr, _ = run(z, vr, z, t, t)
+    np.testing.assert_array_equal(interior(svr), -interior(sv)[:, ::-1, :])
+    # z: zero halo planes stay zero under the reflection
+    w = np.pad(rng.standard_normal((NZ, NY, NX)), 1)
+    w[:, 0, :], w[:, -1, :], w[:, :, 0], w[:, :, -1] = 0, 0, 0, 0
+    wr = -w[::-1, :, :].copy()
+    _, _, sw = run(z, z, w, t, t)
+    _, _, swr = run(z, z, wr, t, t)
+    np.testing.assert_array_equal(interior(swr), -interior(sw)[::-1, :, :])
