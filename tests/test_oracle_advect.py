@@ -145,3 +145,22 @@ def test_self_terms_antisymmetric_under_reflection():
     _, _, sw = run(z, z, w, t, t)
     _, _, swr = run(z, z, wr, t, t)
     np.testing.assert_array_equal(interior(swr), -interior(sw)[::-1, :, :])
+
+
+def test_operation_count_is_the_papers_63():
+    """The oracle's formula has exactly the paper's 63 floating-point
+    operations per cell (Section 4.1): counting + - * in the three
+    tendencies' statements, with every field access AT(...) as one operand,
+    gives 21 per component (6 for x, 6 for y, 7 for z, 2 to combine)."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                            "oracle.c")).read()
+    body = src[src.index("void oracle_advect_uvw"):]
+    body = body[body.index("/* u component"):body.index("AT(sw, i, j, k) = tx + ty + tz;") + 40]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    body = re.sub(r"AT\([^()]*\)", "X", body)
+    parts = body.split("X = tx + ty + tz;")
+    per = [len(re.findall(r"[+\-*]", p)) + 2 for p in parts[:3]]  # + the two adds that combine
+    assert per == [21, 21, 21], per
+    assert len(re.findall(r"[+\-*]", body)) == 63
