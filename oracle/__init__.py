@@ -85,6 +85,17 @@ def jacobi(u, f, h, nsweeps, nthreads=1):
     return u
 
 
+def jacobi_run(u, tmp, f, h, nsweeps, nthreads=1):
+    """nsweeps FP64 Jacobi sweeps on caller-owned C-contiguous float64
+    buffers: the result ends in u, tmp is scratch (the timed CPU baselines
+    reuse their buffers across calls)."""
+    assert u.dtype == np.float64 and u.flags.c_contiguous and tmp.shape == u.shape and f.shape == u.shape
+    assert tmp.dtype == np.float64 and tmp.flags.c_contiguous and f.dtype == np.float64 and f.flags.c_contiguous
+    nx, ny, nz = _dims(u)
+    lib().oracle_jacobi_f64(_ptr(u), _ptr(tmp), _ptr(f), nx, ny, nz, h, nsweeps, nthreads)
+    return u
+
+
 def f32_coeff(h):
     """The FP32 coefficient h*h used by FP32-arithmetic sweeps (rounded once)."""
     return np.float32(np.float64(h) * np.float64(h))

@@ -157,3 +157,35 @@ def test_bf16_sweep_within_bf16_bound():
     o64 = oracle.jacobi_sweep(oracle.from_bf16(u16).astype(np.float64),
                               oracle.from_bf16(f16).astype(np.float64), h)
     assert np.max(np.abs(o16 - o64)) / np.max(np.abs(o64)) <= 2.0 ** -8
+
+
+@pytest.mark.parametrize("nsweeps", [0, 1, 7, 60])
+def test_closed_form_sweeps_match_the_loops(nsweeps):
+    """exact.jacobi_sweeps (the sweep's modal closed form) equals nsweeps
+    sweeps of the loop oracle on a non-cubic grid with a random start and
+    source (zero halo)."""
+    nx, ny, nz = 13, 9, 11
+    rng = np.random.default_rng(40 + nsweeps)
+    u0 = np.zeros((nz + 2, ny + 2, nx + 2))
+    u0[1:-1, 1:-1, 1:-1] = rng.random((nz, ny, nx))
+    f = np.zeros_like(u0)
+    f[1:-1, 1:-1, 1:-1] = rng.standard_normal((nz, ny, nx))
+    h = 1.0 / 14
+    ref = oracle.jacobi(u0, f, h, nsweeps)
+    got = exact.jacobi_sweeps(u0, f, h, nsweeps)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_closed_form_sweeps_mode_and_limit():
+    """A single sine mode with f = 0 decays by mu^n; with a source, many
+    sweeps approach the discrete solution."""
+    nx, ny, nz = 10, 7, 12
+    h = 1.0 / 13
+    e0 = sss(nx, ny, nz, 2, 1, 3)
+    mu = (np.cos(2 * np.pi / (nx + 1)) + np.cos(np.pi / (ny + 1)) + np.cos(3 * np.pi / (nz + 1))) / 3
+    got = exact.jacobi_sweeps(e0, np.zeros_like(e0), h, 25)
+    assert np.max(np.abs(got - mu ** 25 * e0)) <= 1e-14
+    f = inputs.grf(nx, seed=8, ny=ny, nz=nz)
+    far = exact.jacobi_sweeps(np.zeros_like(f), f, h, 100000)
+    ud = exact.solve(f, h)
+    assert np.max(np.abs(far - ud)) <= 1e-12 * np.max(np.abs(ud))
