@@ -140,15 +140,21 @@ STENCIL_API int stencil_ctx_status(stencil_ctx* ctx, void* stream);
  *
  * dtype F64: binary64 storage.  FP64_NATIVE computes each sweep in binary64
  * (adds in the order written, h*h*f fused, then a multiply by 1/6).
- * FP64_FIXED (the default) computes in 64-bit fixed point with one scale per
- * call, 2^-S, chosen from max|u| and max|f| with the maximum-principle bound
- * of the iteration so that no sum can overflow (S = 58 - ceil(log2 B), B
- * the bound on the six-neighbour sum); sums are exact, the division by 6 is
- * rounded to the nearest 2^-S, and values are rounded to binary64 once per
- * pass (without `work`) or once per call (with `work`).  The error is below
- * that of binary64 arithmetic on the same sweeps.  FIXED needs finite inputs
- * with |values| < 2^900 (otherwise the interior is set to NaN and the ctx
- * status reports STENCIL_ERR_NONFINITE or STENCIL_ERR_RANGE).
+ * FP64_FIXED (the default) computes in 64-bit fixed point with a scale
+ * 2^-S chosen for every pass from a bound M on the values that pass can
+ * produce: the largest value the previous pass wrote (max|u| for the
+ * first), the Dirichlet values, plus the source's share over the pass
+ * (h*h*max|f|/6 per sweep); S = 58 - ceil(log2(6M + h*h*max|f|)), so no sum
+ * can overflow.  Sums are exact and each update is rounded once to the
+ * nearest 2^-S: at most 2^-54 (M + h*h*max|f|/6) per update, the order of
+ * one binary64 rounding of the six-neighbour sum, and since a sweep does not
+ * amplify errors in the max norm, n sweeps add at most n such errors.  The
+ * resolution follows the iterate, so a solution far below its initial
+ * bound (zero start with an oscillating or point source) keeps the same
+ * relative accuracy.  Values are rounded to binary64 once per pass (without
+ * `work`) or once per call (with `work`).  FIXED needs finite inputs with
+ * |values| < 2^900 (otherwise the interior is set to NaN and the ctx status
+ * reports STENCIL_ERR_NONFINITE or STENCIL_ERR_RANGE).
  * dtype F32: binary32 storage and arithmetic.  dtype BF16: bfloat16
  * storage, binary32 arithmetic; each pass rounds to bfloat16 once
  * (round-to-nearest-even), intermediate sweeps of a pass stay binary32.
@@ -266,8 +272,9 @@ STENCIL_API int stencil_redblack_config_select(stencil_ctx* ctx, int32_t dtype,
  *     r = f - A u on the interior,
  * always in binary64 (it decides convergence of the iterative solve).
  *   u, f      F64 grids of equal extents (u's halo is the boundary).
- *   r         NULL, or an F64 grid of the same extents: its interior
- *             receives r (halo untouched).
+ *   r         NULL, or an F64 grid of the same extents, distinct from u and
+ *             f (STENCIL_ERR_ARG if it is either): its interior receives r
+ *             (halo untouched).
  *   norms_dev DEVICE pointer to 2 doubles: ||r||_2 and ||f||_2 over the
  *             interior (unweighted).  The sum order is fixed (per-block
  *             partial sums combined in block order), so the result is
@@ -444,8 +451,9 @@ STENCIL_API int wsnet_loss_grad(wsnet* net, const float* x, const float* t,
  *   r values are bitwise those of stencil_residual; the norms use a
  *   different (fixed) partition of the sum, so they agree to rounding and
  *   are reproducible run to run.
- *   The first call on a device looks up the array's device address (once
- *   per device, with that device current); make that first call before any
+ *   The first call in each CUDA context on a device looks up the array's
+ *   device address (with that device current; again after the context is
+ *   replaced, e.g. by cudaDeviceReset); make that first call before any
  *   stream capture.  Every call on a device shares the one array: calls
  *   that overlap on the GPU (different streams, or threads without
  *   ordering) race and give wrong norms.  Each call overwrites every

@@ -95,6 +95,8 @@ struct SrcBatch {
   __device__ __forceinline__ SrcBatch(const Params* pp, bool) : p(pp) {}
   __device__ __forceinline__ int64_t items() const { return p->base[p->n]; }
   __device__ __forceinline__ uint32_t* status() const { return p->status; }
+  __device__ __forceinline__ void fx_begin() const {}
+  __device__ __forceinline__ void fx_end(uint32_t) const {}
   __device__ __forceinline__ bool view(int64_t item, ItemView<Pol>& v) const {
     const int i = find_instance(p->base, p->n, item);
     const InstState& s = p->state[i];

@@ -4,10 +4,13 @@
 // about 64 for 32-bit integer operations, so a binary64 sweep is bound by
 // arithmetic at a quarter of the HBM roofline.  The fixed-point sweep keeps
 // binary64 storage and does its arithmetic on integers instead: a value x is
-// represented by round(x * 2^S) with one scale S per call, chosen so that
-// every sum of the sweep stays below 2^58 in magnitude.  Sums are then exact,
-// the division by 6 is rounded to the nearest unit 2^-S, and the result is
-// rounded to binary64 once per pass.
+// represented by round(x * 2^S).  The scale S is chosen afresh for every pass
+// from a bound on the magnitudes that pass can produce (the largest value the
+// previous pass wrote, the Dirichlet values and the source's contribution),
+// so the resolution 2^-S follows the iterate rather than an a-priori bound
+// for the whole call.  Sums of six neighbours and the source then stay below
+// 2^58 and are exact, the division by 6 is rounded to the nearest unit
+// 2^-S, and the result is rounded to binary64 once per call (or per pass).
 #pragma once
 
 #include <stdint.h>
@@ -20,15 +23,21 @@ namespace stencil {
 // 2^63 and the division by 6 needs no sign handling:
 //   (sum of 6 (K + q_i) + G + 3) / 6 = K + round((sum q_i + G) / 6).
 constexpr uint64_t kFxBias = 1ull << 59;
+// Scale marking a failed call: set once a pass sees a non-finite input or a
+// bound beyond the representable range; every later pass keeps it.
+constexpr int kFxBadScale = 4000;
 
-// Per-launch constants, computed identically by every thread from max|u|
-// and max|f| (see fx_params).
+// Per-pass constants, computed identically by every thread (policies.cuh).
 struct FixedParams {
-  int S;        // values are q * 2^-S
-  int Cu;       // 1085 - S: shift base of the u conversion
-  int Cg;       // 1085 - S - eh: shift base of the source conversion
-  uint64_t H;   // mh * 2^64 where hh = mh * 2^eh, mh in [0.5, 1)
-  int bad;      // 1: input not finite, 2: beyond range -> write NaN
+  int S;          // values of this pass are q * 2^-S (resident: its output's scale)
+  int Cu;         // 1085 - S: shift base of the u conversion (resident: of the
+                  // computing scale, that of the stored input)
+  int Cg;         // 1085 - S - eh: shift base of the per-pass source conversion
+  uint64_t H;     // mh * 2^64 where hh = mh * 2^eh, mh in [0.5, 1)
+  int bad;        // 1: input not finite, 2: beyond range -> write NaN
+  int dshift;     // resident: S - (scale of the stored input); 0 almost always
+  int fpath;      // resident: the stored source is not at the computing scale;
+                  // this pass reads f itself and stores the source afresh
 };
 
 // 64-bit logical right shift with PTX semantics: amounts >= 64 give 0.
@@ -38,30 +47,37 @@ __device__ __forceinline__ uint64_t shr64(uint64_t v, unsigned n) {
   return r;
 }
 
-// binary64 -> K + round(x * 2^S), ties up.  The 53-bit significand is
-// left-aligned at bit 63 and shifted right by (1085 - S - e), keeping one
-// extra bit for the rounding; zeros and subnormals (e = 0) shift out to 0.
+// Rounding of y = |x| 2^S to nearest, halves away from zero, with the sign
+// of x, from t = floor(2y) and the sign mask s (all ones if x < 0):
+//   x >= 0:  floor((t + 1) / 2) = (t + 1) >> 1
+//   x <  0: -floor((t + 1) / 2) = floor(-t / 2) = (~t + 1) >> 1 (arithmetic)
+// i.e. ((t ^ s) + 1) >> 1 in both cases; with the bias K folded in,
+// ((t ^ s) + 2K + 1) >> 1 (logical: the sum is positive).
+__device__ __forceinline__ uint64_t fx_sign_mask(uint64_t b) {
+  return static_cast<uint64_t>(static_cast<int64_t>(b) >> 63);
+}
+
+// binary64 -> K + round(x * 2^S), halves away from zero.  The 53-bit
+// significand is left-aligned at bit 63 and shifted right by (1085 - S - e),
+// which leaves t = floor(2 |x| 2^S).  Zeros and subnormals (e = 0) shift out
+// to 0.
 __device__ __forceinline__ uint64_t fx_in(double x, int Cu) {
   const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
   const int e = static_cast<int>((b >> 52) & 0x7ffu);
   const uint64_t m63 = (b << 11) | 0x8000000000000000ull;
-  const uint64_t t = shr64(m63, static_cast<unsigned>(Cu - e));  // 2|x| 2^S
-  const uint64_t sgn = static_cast<uint64_t>(static_cast<int64_t>(b) >> 63);
-  const uint64_t w = ((t ^ sgn) - sgn) + (2 * kFxBias + 1);
-  return w >> 1;
+  const uint64_t t = shr64(m63, static_cast<unsigned>(Cu - e));  // floor(2|x| 2^S)
+  return ((t ^ fx_sign_mask(b)) + (2 * kFxBias + 1)) >> 1;
 }
 
-// Source term G = round(f * hh * 2^S) (signed, unbiased), ties up: the
-// significand of f times the significand of hh (high 64 bits of the
-// product), then the same aligned shift.
+// Source term G = round(f * hh * 2^S) (signed, unbiased), halves away from
+// zero: the significand of f times the significand of hh (high 64 bits of
+// the product), then the same aligned shift.
 __device__ __forceinline__ int64_t fx_source(double f, int Cg, uint64_t H) {
   const uint64_t b = static_cast<uint64_t>(__double_as_longlong(f));
   const int e = static_cast<int>((b >> 52) & 0x7ffu);
   const uint64_t m63 = (b << 11) | 0x8000000000000000ull;
   const uint64_t t = shr64(__umul64hi(m63, H), static_cast<unsigned>(Cg - e));
-  const uint64_t sgn = static_cast<uint64_t>(static_cast<int64_t>(b) >> 63);
-  const int64_t w = static_cast<int64_t>((t ^ sgn) - sgn) + 1;
-  return w >> 1;
+  return static_cast<int64_t>((t ^ fx_sign_mask(b)) + 1) >> 1;
 }
 
 // (sum + 3) / 6 for 0 <= sum + 3 < 2^64: multiply by ceil(2^65 / 3), take
@@ -80,37 +96,44 @@ __device__ __forceinline__ double fx_out(uint64_t U, int S) {
   return q == 0 ? 0.0 : __longlong_as_double(bits);
 }
 
-// Scale selection.  maxu = max|u| over every cell (halo included), maxf =
-// max|f| over the interior, n = sweeps this call does, lmin = (smallest
-// extent + 1) * h.  Bound on every iterate (maximum principle of the sweep):
-//   |u_n| <= M = min(maxu + n hh maxf / 6,  3 maxu + maxf lmin^2 / 4);
-// the largest magnitude before the division by 6 is B = 6 M + hh maxf, and
-// S = 58 - ceil(log2 B) keeps it below 2^58 (capped at 1022).
-__device__ __forceinline__ FixedParams fx_params(double maxu, double maxf, double hh, double n,
-                                                 double lmin) {
-  FixedParams p;
-  p.bad = 0;
-  p.S = 0; p.Cu = 0; p.Cg = 0; p.H = 0;
-  if (!(maxu <= 1.0e300) || !(maxf <= 1.0e300)) {  // NaN, Inf or absurdly large
-    p.bad = 1;
-    return p;
+// A stored iterate U at scale S_old, brought to scale S_old + d: an exact
+// left shift (d > 0) or a right shift rounded to nearest, halves up (d < 0).
+__device__ __forceinline__ uint64_t fx_rescale(uint64_t U, int d) {
+  const int64_t q = static_cast<int64_t>(U - kFxBias);
+  int64_t r;
+  if (d > 0) {
+    r = static_cast<int64_t>(static_cast<uint64_t>(q) << d);
+  } else {
+    const int n = -d;
+    r = (q + (1ll << (n - 1))) >> n;
   }
-  const double lin = maxu + n * hh * maxf / 6.0;
-  const double cmp = 3.0 * maxu + maxf * lmin * lmin / 4.0;
-  const double M = lin < cmp ? lin : cmp;
-  const double B = 6.0 * M + hh * maxf;
+  return static_cast<uint64_t>(r) + kFxBias;
+}
+
+// Scale for a pass whose values (and six-neighbour sums plus the source) are
+// bounded by B: S = 58 - ceil(log2 B), capped at 1022; bad = 2 if B is out
+// of range, 1 if it is not a number.
+__device__ __forceinline__ int fx_scale_for(double B, int* bad) {
+  if (!(B <= 1.0e300)) {
+    *bad = (B != B) ? 1 : 2;
+    return 0;
+  }
   int e = 0;
   if (B > 0.0) frexp(B, &e);  // B = m 2^e, m in [0.5, 1), so B <= 2^e
   int S = 58 - e;
   if (S > 1022) S = 1022;
-  if (S < -900) p.bad = 2;
+  if (S < -900) *bad = 2;
+  return S;
+}
+
+// Conversion constants for scale S and source factor hh.
+__device__ __forceinline__ void fx_conv(FixedParams& p, int S, double hh) {
   int eh = 0;
   const double mh = frexp(hh, &eh);
   p.S = S;
   p.Cu = 1085 - S;
   p.Cg = 1085 - S - eh;
   p.H = (static_cast<uint64_t>(__double_as_longlong(mh)) << 11) | 0x8000000000000000ull;
-  return p;
 }
 
 }  // namespace stencil

@@ -39,9 +39,11 @@ constexpr uint32_t kStatusRange = 4u;
 
 // Layout of the ctx scratch block (device memory).
 constexpr size_t kScratchStatus = 0;      // uint32 status bits
-constexpr size_t kScratchMaxU = 16;       // uint64 bits of max|u| (incl. halo)
-constexpr size_t kScratchMaxF = 24;       // uint64 bits of max|f| (interior)
 constexpr size_t kScratchAdvRange = 32;   // 5 x uint64: max|u|, max|v|, max|w|, max and min nonzero |coef|
+constexpr size_t kScratchRange = 176;     // 3 x uint64 bits: max|u| halo, max|f|, max|u| interior
+constexpr size_t kScratchFxMag = 208;     // 4 x uint32: fixed-point magnitude keys (ring of 3)
+constexpr size_t kScratchFxScale = 224;   // 4 x int32: fixed-point scales (ring of 3)
+constexpr size_t kScratchFxGScale = 240;  // 4 x int32: scale of the stored source (ring of 3)
 constexpr size_t kScratchPartials = 256;  // residual partial sums
 constexpr int kMaxPartials = 2048;        // blocks of the residual kernel
 constexpr size_t kScratchBytes = kScratchPartials + sizeof(double) * 2 * kMaxPartials;

@@ -14,14 +14,14 @@
 
 namespace stencil {
 
-// max|u| over every cell (halo included) and max|f| over the interior, as
-// the bit patterns of non-negative doubles (their integer order is their
+// max|u| over the halo cells, max|f| and max|u| over the interior, as the
+// bit patterns of non-negative doubles (their integer order is their
 // numeric order; NaN sorts above Inf, so a NaN anywhere is seen).
 __global__ void range_kernel(const double* __restrict__ u, const double* __restrict__ f,
                              int64_t nx, int64_t ny, int64_t nz, int64_t usy, int64_t usz,
                              int64_t fsy, int64_t fsz, unsigned long long* maxbits) {
   const int64_t rows = (ny + 2) * (nz + 2);
-  unsigned long long mu = 0, mf = 0;
+  unsigned long long mh = 0, mf = 0, mu = 0;
   for (int64_t row = blockIdx.x * int64_t(blockDim.y) + threadIdx.y; row < rows;
        row += int64_t(gridDim.x) * blockDim.y) {
     const int64_t k = row / (ny + 2);
@@ -31,25 +31,60 @@ __global__ void range_kernel(const double* __restrict__ u, const double* __restr
       const unsigned long long bu =
           static_cast<unsigned long long>(__double_as_longlong(u[i + j * usy + k * usz])) &
           0x7fffffffffffffffull;
-      mu = bu > mu ? bu : mu;
       if (inner && i >= 1 && i <= nx) {
         const unsigned long long bf =
             static_cast<unsigned long long>(__double_as_longlong(f[i + j * fsy + k * fsz])) &
             0x7fffffffffffffffull;
         mf = bf > mf ? bf : mf;
+        mu = bu > mu ? bu : mu;
+      } else {
+        mh = bu > mh ? bu : mh;
       }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mu, o);
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mh, o);
     const unsigned long long b = __shfl_xor_sync(0xffffffffu, mf, o);
-    mu = a > mu ? a : mu;
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, mu, o);
+    mh = a > mh ? a : mh;
     mf = b > mf ? b : mf;
+    mu = c > mu ? c : mu;
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(&maxbits[0], mu);
+    atomicMax(&maxbits[0], mh);
     atomicMax(&maxbits[1], mf);
+    atomicMax(&maxbits[2], mu);
   }
+}
+
+// Slot 0 of the fixed-point state, read by pass 1: the scale the first pass
+// would choose from the caller's u (RESIDENT: the scale the interior is packed
+// at) and the magnitude key of u's interior, so that pass 1 normally keeps
+// that scale.  One thread.
+template <bool RESIDENT>
+__global__ void fx_init_kernel(SweepArgs a) {
+  const double mu = bits_as_double(a.maxbits[2]);
+  const double mh = bits_as_double(a.maxbits[0]);
+  const double mf = bits_as_double(a.maxbits[1]);
+  int bad = 0;
+  int S = 0;
+  if (!(mu <= 1.0e300) || !(mh <= 1.0e300) || !(mf <= 1.0e300)) {
+    bad = (mu - mu == 0.0 && mh - mh == 0.0 && mf - mf == 0.0) ? 2 : 1;
+  } else {
+    const double hmf = a.hh * mf;
+    S = fx_scale_for(6.0 * (fmax(mu, mh) + static_cast<double>(a.stages) * hmf / 6.0) + hmf, &bad);
+  }
+  uint32_t key;
+  if (RESIDENT) {  // largest |q| of the packed interior is below (key + 1) 2^32
+    key = bad ? 0u : static_cast<uint32_t>(ldexp(mu, S - 32));
+  } else {         // high word of max|u| over the interior
+    key = static_cast<uint32_t>(a.maxbits[2] >> 32);
+  }
+  a.fxmag[0] = key;
+  a.fxmag[1] = 0u;
+  a.fxscale[0] = bad ? kFxBadScale + bad : S;
+  if (RESIDENT) a.fxgscale[0] = S;  // the set-up packs the source at S
+  if (bad) atomicOr(a.status, bad == 1 ? kStatusNonFinite : kStatusRange);
 }
 
 // Copy the halo cells of src into dst (same extents).
@@ -95,12 +130,16 @@ __global__ void interior_copy_kernel(const T* __restrict__ src, T* __restrict__ 
 }
 
 // Resident fixed point: convert the interior of u (in place) to the biased
-// integers U and the interior of f to G = round(h*h*f*2^S) in work.
+// integers U, and the interior of f to G = round(h*h*f*2^S) in work, both at
+// the scale S of slot 0.
 __global__ void fx_pack_kernel(double* __restrict__ u, const double* __restrict__ f,
                                unsigned long long* __restrict__ work, int64_t nx, int64_t ny,
                                int64_t nz, int64_t usy, int64_t usz, int64_t fsy, int64_t fsz,
                                int64_t wsy, int64_t wsz, SweepArgs a) {
-  const FixedParams k = PolResident::make(a);
+  const int S0 = a.fxscale[0];
+  if (S0 >= kFxBadScale) return;  // reported by the set-up; the result will be NaN
+  FixedParams k;
+  fx_conv(k, S0, a.hh);
   const int64_t rows = ny * nz;
   for (int64_t row = blockIdx.x * int64_t(blockDim.y) + threadIdx.y; row < rows;
        row += int64_t(gridDim.x) * blockDim.y) {
@@ -116,13 +155,13 @@ __global__ void fx_pack_kernel(double* __restrict__ u, const double* __restrict_
   }
 }
 
-// Back to binary64: the interior of src (U) into the interior of u.
+// Back to binary64: the interior of src (U, at the scale the last pass,
+// a.pass, published) into the interior of u; NaN if the call failed.
 __global__ void fx_unpack_kernel(const unsigned long long* __restrict__ src, double* __restrict__ u,
                                  int64_t nx, int64_t ny, int64_t nz, int64_t ssy, int64_t ssz,
                                  int64_t usy, int64_t usz, SweepArgs a) {
-  const FixedParams k = PolResident::make(a);
-  if (k.bad && threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == 0)
-    atomicOr(a.status, k.bad == 1 ? kStatusNonFinite : kStatusRange);
+  const int S = a.fxscale[a.pass % 3];
+  const bool bad = S >= kFxBadScale;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   const int64_t rows = ny * nz;
   for (int64_t row = blockIdx.x * int64_t(blockDim.y) + threadIdx.y; row < rows;
@@ -131,7 +170,7 @@ __global__ void fx_unpack_kernel(const unsigned long long* __restrict__ src, dou
     const int64_t j = 1 + row - (kz - 1) * ny;
     const unsigned long long* sr = src + j * ssy + kz * ssz;
     double* ur = u + j * usy + kz * usz;
-    for (int64_t i = 1 + threadIdx.x; i <= nx; i += blockDim.x) ur[i] = k.bad ? nan : fx_out(sr[i], k.S);
+    for (int64_t i = 1 + threadIdx.x; i <= nx; i += blockDim.x) ur[i] = bad ? nan : fx_out(sr[i], S);
   }
 }
 
@@ -214,7 +253,7 @@ struct Prepared {
 };
 
 int prepare(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,
-            int64_t nsweeps, int flags, bool pack, cudaStream_t st, Prepared* P) {
+            int64_t nsweeps, int first_stages, int flags, bool pack, cudaStream_t st, Prepared* P) {
   const bool fixed = (u.dtype == STENCIL_F64) && (flags != STENCIL_SWEEP_FP64_NATIVE);
   const bool resident = fixed && work != nullptr && nsweeps >= kResidentMinSweeps;
   P->policy = policy_of(u.dtype, fixed, resident);
@@ -222,19 +261,32 @@ int prepare(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, cons
   if (rc) return rc;
   SweepArgs& a = P->a;
   a.hh = h * h;
-  a.nsw = static_cast<double>(nsweeps);
-  a.lmin = static_cast<double>(std::min(std::min(u.nx, u.ny), u.nz) + 1) * h;
-  a.maxbits = reinterpret_cast<const unsigned long long*>(ctx->scratch + kScratchMaxU);
+  a.maxbits = reinterpret_cast<const unsigned long long*>(ctx->scratch + kScratchRange);
   a.status = reinterpret_cast<uint32_t*>(ctx->scratch + kScratchStatus);
+  a.fxmag = reinterpret_cast<uint32_t*>(ctx->scratch + kScratchFxMag);
+  a.fxscale = reinterpret_cast<int32_t*>(ctx->scratch + kScratchFxScale);
+  a.pass = 1;
+  a.stages = first_stages;
+  a.fsrc64 = resident ? static_cast<const double*>(f.data) : nullptr;
+  a.fsy = f.sy;
+  a.fsz = f.sz;
+  a.fxgscale = resident ? reinterpret_cast<int32_t*>(ctx->scratch + kScratchFxGScale) : nullptr;
+  a.gdst = resident ? static_cast<unsigned long long*>(work->data) : nullptr;
+  a.gsy = resident ? work->sy : 0;
+  a.gsz = resident ? work->sz : 0;
   if (fixed) {
-    rc = check_cuda(cudaMemsetAsync(ctx->scratch + kScratchMaxU, 0, 16, st), "memset range");
+    rc = check_cuda(cudaMemsetAsync(ctx->scratch + kScratchRange, 0, 24, st), "memset range");
     if (rc) return rc;
     const int64_t rows = (u.ny + 2) * (u.nz + 2);
     const int blocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
     range_kernel<<<blocks, dim3(32, 8), 0, st>>>(
         static_cast<const double*>(u.data), static_cast<const double*>(f.data), u.nx, u.ny, u.nz,
-        u.sy, u.sz, f.sy, f.sz, reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchMaxU));
+        u.sy, u.sz, f.sy, f.sz, reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchRange));
     rc = check_cuda(cudaGetLastError(), "range kernel");
+    if (rc) return rc;
+    if (resident) fx_init_kernel<true><<<1, 1, 0, st>>>(a);
+    else fx_init_kernel<false><<<1, 1, 0, st>>>(a);
+    rc = check_cuda(cudaGetLastError(), "fixed-point set-up kernel");
     if (rc) return rc;
   }
   P->ui = u;
@@ -264,13 +316,16 @@ namespace {
 
 // After the last pass: the iterate is in `last` (u's buffer or u_tmp's);
 // bring it back into u (the resident policy unpacks the fixed point).
-int finish(stencil_ctx* ctx, const Prepared& P, const Grid& u, const Grid& last, bool in_tmp, cudaStream_t st) {
+int finish(stencil_ctx* ctx, const Prepared& P, const Grid& u, const Grid& last, bool in_tmp, int passes,
+           cudaStream_t st) {
   if (P.policy == kPolResident) {
+    SweepArgs a = P.a;
+    a.pass = passes;
     const int64_t rows = u.ny * u.nz;
     const int cblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 16 * ctx->num_sms));
     fx_unpack_kernel<<<cblocks, dim3(32, 8), 0, st>>>(
         static_cast<const unsigned long long*>(last.data), static_cast<double*>(u.data), u.nx, u.ny, u.nz,
-        last.sy, last.sz, u.sy, u.sz, P.a);
+        last.sy, last.sz, u.sy, u.sz, a);
     return check_cuda(cudaGetLastError(), "unpack kernel");
   }
   return in_tmp ? copy_interior_any(last, u, st) : STENCIL_OK;
@@ -374,21 +429,28 @@ int launch_average2d(stencil_ctx* ctx, const Grid& u, const Grid& ut, int64_t ns
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
   if (nsweeps == 0) return STENCIL_OK;
+  const int policy = policy_of(u.dtype, u.dtype == STENCIL_F64 && flags != STENCIL_SWEEP_FP64_NATIVE,
+                               u.dtype == STENCIL_F64 && flags != STENCIL_SWEEP_FP64_NATIVE && work != nullptr &&
+                                   nsweeps >= kResidentMinSweeps);
+  const int want = spp > 0 ? spp : ctx->best_pass[policy];
+  const int T1 = supported_t(policy, static_cast<int>(std::min<int64_t>(nsweeps, want)));
   Prepared P;
-  int rc = prepare(ctx, u, ut, f, work, h, nsweeps, flags, true, st, &P);
+  int rc = prepare(ctx, u, ut, f, work, h, nsweeps, T1, flags, true, st, &P);
   if (rc) return rc;
-  const int want = spp > 0 ? spp : ctx->best_pass[P.policy];
   const Grid* a_in = &P.ui;
   const Grid* b_out = &P.ti;
   int64_t left = nsweeps;
+  int pass = 0;
   while (left > 0) {
     const int T = supported_t(P.policy, static_cast<int>(std::min<int64_t>(left, want)));
+    P.a.pass = ++pass;
+    P.a.stages = T;
     rc = run_pass(ctx, P.policy, T, *a_in, *b_out, P.fi, P.a, st);
     if (rc) return rc;
     std::swap(a_in, b_out);
     left -= T;
   }
-  return finish(ctx, P, u, *a_in, a_in != &P.ui, st);
+  return finish(ctx, P, u, *a_in, a_in != &P.ui, pass, st);
 }
 
 // nsweeps red-black Gauss-Seidel sweeps: passes of T = 2 x (sweeps per
@@ -398,13 +460,15 @@ int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f
 int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                     double h, int64_t nsweeps, int spp, int flags, cudaStream_t st) {
   if (nsweeps == 0) return STENCIL_OK;
-  Prepared P;
-  int rc = prepare(ctx, u, ut, f, work, h, 2 * nsweeps, flags, true, st, &P);
-  if (rc) return rc;
   const int want = spp > 0 ? spp : 1;
+  Prepared P;
+  int rc = prepare(ctx, u, ut, f, work, h, 2 * nsweeps, 2 * static_cast<int>(std::min<int64_t>(nsweeps, want)),
+                   flags, true, st, &P);
+  if (rc) return rc;
   const Grid* a_in = &P.ui;
   const Grid* b_out = &P.ti;
   int64_t left = nsweeps;
+  int pass = 0;
   while (left > 0) {
     int T = 2 * static_cast<int>(std::min<int64_t>(left, want));
     const SweepVariant* vs = nullptr;
@@ -413,12 +477,14 @@ int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid&
       if ((nv = sweep_variants_rb(P.policy, T, &vs)) > 0) break;
     if (nv < 1) return set_error(STENCIL_ERR_ARG, "no compiled red-black configuration");
     const int c = ctx->rb_choice[P.policy][T];
+    P.a.pass = ++pass;
+    P.a.stages = T;
     rc = vs[c < nv ? c : 0].fn(ctx, *a_in, *b_out, P.fi, P.a, st);
     if (rc) return rc;
     std::swap(a_in, b_out);
     left -= T / 2;
   }
-  return finish(ctx, P, u, *a_in, a_in != &P.ui, st);
+  return finish(ctx, P, u, *a_in, a_in != &P.ui, pass, st);
 }
 
 int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work, double h,
@@ -427,7 +493,7 @@ int autotune_sweep(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& 
   // changed; the resident policy's trials read u's binary64 interior as if
   // it were packed, which costs the same).
   Prepared P;
-  int rc = prepare(ctx, u, ut, f, work, h, 1000, flags, false, st, &P);
+  int rc = prepare(ctx, u, ut, f, work, h, 1000, 1, flags, false, st, &P);
   if (rc) return rc;
   std::string rep;
   char line[256];

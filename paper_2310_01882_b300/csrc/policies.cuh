@@ -19,10 +19,111 @@ namespace stencil {
 // Arguments every sweep launch passes to its policy's `make`.
 struct SweepArgs {
   double hh;                              // h*h
-  double nsw;                             // sweeps of the whole call (fixed-point bound)
-  double lmin;                            // (smallest extent + 1) * h
-  const unsigned long long* maxbits;      // [max|u|, max|f|] bit patterns (fixed point)
+  const unsigned long long* maxbits;      // fixed point: bit patterns of [max|u| over the halo,
+                                          //   max|f| over the interior, max|u| over the interior]
   uint32_t* status;                       // device status word
+  uint32_t* fxmag;                        // fixed point: [3] magnitude keys of recent passes' outputs
+  int32_t* fxscale;                       // fixed point: [3] scales of recent passes' outputs
+  int32_t* fxgscale;                      // resident fixed point: [3] scale of the stored source
+                                          //   after recent passes
+  int pass;                               // fixed point: index of this pass in the call (1, 2, ...)
+  int stages;                             // sweeps (Jacobi) or colour stages (red-black) per pass
+  const double* fsrc64;                   // resident fixed point: the binary64 source f ...
+  int64_t fsy, fsz;                       //   ... and its strides (host side: its tensor map)
+  unsigned long long* gdst;               // resident fixed point: the stored source (work grid) ...
+  int64_t gsy, gsz;                       //   ... and its strides
+};
+
+__device__ __forceinline__ double bits_as_double(unsigned long long b) {
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
+// Scale of pass a.pass of a fixed-point call.  Pass p reads slot (p-1) mod 3
+// of the state (the scale its input is stored at and the magnitude key of
+// that input -- what the previous pass wrote; the set-up kernel fills slot 0
+// for pass 1) and publishes slot p mod 3.  Every value the pass produces is
+// bounded by
+//   M = max(bound of its input, max|halo|) + stages * hh max|f| / 6
+// (one sweep, or one colour stage, averages values below the running bound
+// and adds at most hh max|f| / 6: the maximum principle of the update), and
+// a six-neighbour sum plus the source by B = 6 M + hh max|f|, which fixes
+// S = fx_scale_for(B).
+// PER-PASS (not RESIDENT): the pass converts its binary64 input and the
+// source at S, computes and rounds back to binary64.
+// RESIDENT: the pass computes at the scale its input is stored at (Sprev)
+// and writes its output at S, the scale the next pass computes at:
+// S = Sprev unless the bound needs a coarser scale or allows one at least
+// two steps finer (most passes rescale nothing: dshift = 0); a pass that
+// does rescale shifts each value it writes.  The source is stored in the
+// work grid at one scale (slot's fxgscale); when that is not the computing
+// scale (fpath: the pass after a rescale), every tile of the pass loads the
+// binary64 f instead, converts it at the computing scale, and stores the
+// source afresh for its own cells -- no tile reads the work grid during that
+// pass, so rewriting it races with nothing.  Computing at Sprev cannot overflow: Sprev leaves
+// room for values up to 2^58 / 6 (a bound B_prev >= 6 M_prev + hh max|f|
+// below 2^(58 - Sprev)), the biased sums hold up to 2^60 / 6, and this
+// pass's values stay below M_prev + stages hh max|f| / 6 <= 2 M_prev.
+template <bool RESIDENT>
+__device__ __forceinline__ FixedParams fx_pass_params(const SweepArgs& a) {
+  FixedParams p;
+  p.bad = 0; p.dshift = 0; p.fpath = 0;
+  const int prev = (a.pass + 2) % 3;
+  const int Sprev = a.fxscale[prev];
+  const double mh = bits_as_double(a.maxbits[0]);
+  const double mf = bits_as_double(a.maxbits[1]);
+  if (Sprev >= kFxBadScale) {  // an earlier pass (or the set-up) failed
+    p.bad = Sprev - kFxBadScale;
+    fx_conv(p, 0, a.hh);
+    return p;
+  }
+  if (!(mh <= 1.0e300) || !(mf <= 1.0e300)) {
+    p.bad = (mh - mh == 0.0 && mf - mf == 0.0) ? 2 : 1;
+    fx_conv(p, 0, a.hh);
+    return p;
+  }
+  const uint32_t key = a.fxmag[prev];
+  const double mi = RESIDENT ? ldexp(static_cast<double>(key) + 1.0, 32 - Sprev)
+                             : bits_as_double((static_cast<unsigned long long>(key) << 32) | 0xffffffffull);
+  const double hmf = a.hh * mf;
+  const double M = fmax(mi, mh) + static_cast<double>(a.stages) * hmf / 6.0;
+  int S = fx_scale_for(6.0 * M + hmf, &p.bad);
+  if (RESIDENT && !p.bad) {
+    if (S >= Sprev && S < Sprev + 2) S = Sprev;
+    p.dshift = max(-62, min(62, S - Sprev));
+    p.fpath = a.fxgscale[prev] != Sprev;
+    fx_conv(p, Sprev, a.hh);  // conversions (Dirichlet values, source) at the computing scale
+    p.S = S;                  // the output's scale
+    return p;
+  }
+  fx_conv(p, S, a.hh);
+  return p;
+}
+
+// Block 0, thread 0 of pass a.pass: publish its scale (or the failure), clear
+// the magnitude slot the next pass accumulates into, report a new failure.
+__device__ __forceinline__ void fx_pass_publish(const SweepArgs& a, const FixedParams& p) {
+  if (blockIdx.x != 0 || threadIdx.x != 0 || threadIdx.y != 0) return;
+  const int prev = (a.pass + 2) % 3;
+  const bool sticky = a.fxscale[prev] >= kFxBadScale;
+  a.fxscale[a.pass % 3] = p.bad ? kFxBadScale + p.bad : p.S;
+  if (a.fxgscale) a.fxgscale[a.pass % 3] = p.fpath ? 1085 - p.Cu : a.fxgscale[prev];
+  a.fxmag[(a.pass + 1) % 3] = 0u;
+  if (p.bad && !sticky) atomicOr(a.status, p.bad == 1 ? kStatusNonFinite : kStatusRange);
+}
+
+// Combine the magnitude keys of a warp's active lanes into the pass's slot.
+__device__ __forceinline__ void fx_track_commit(const SweepArgs& a, uint32_t key) {
+  const uint32_t mask = __activemask();
+  const uint32_t m = __reduce_max_sync(mask, key);
+  if ((threadIdx.x & 31) == static_cast<uint32_t>(__ffs(mask) - 1) && m) atomicMax(a.fxmag + a.pass % 3, m);
+}
+
+// Output magnitude tracking of the policies that do not track.
+template <class T>
+struct NoTrack {
+  __device__ __forceinline__ void add(T) {}
+  __device__ __forceinline__ void add2(T, T) {}
+  __device__ __forceinline__ uint32_t key() const { return 0u; }
 };
 
 // binary64 storage and arithmetic: adds in the order of the definition,
@@ -32,6 +133,9 @@ struct PolF64 {
   using C = double;
   static constexpr int kElem = 8;
   static constexpr bool kFixed = false;
+  static constexpr bool kTrack = false;
+  static constexpr bool kResident = false;
+  using Track = NoTrack<double>;
   struct K { double hh; };
   __device__ static __forceinline__ K make(const SweepArgs& a) { return K{a.hh}; }
   __device__ static __forceinline__ C in(T v, const K&) { return v; }
@@ -53,6 +157,9 @@ struct PolF32 {
   using C = float;
   static constexpr int kElem = 4;
   static constexpr bool kFixed = false;
+  static constexpr bool kTrack = false;
+  static constexpr bool kResident = false;
+  using Track = NoTrack<float>;
   struct K { float hh; };
   __device__ static __forceinline__ K make(const SweepArgs& a) { return K{static_cast<float>(a.hh)}; }
   __device__ static __forceinline__ C in(T v, const K&) { return v; }
@@ -75,6 +182,9 @@ struct PolBF16 {
   using C = float;
   static constexpr int kElem = 2;
   static constexpr bool kFixed = false;
+  static constexpr bool kTrack = false;
+  static constexpr bool kResident = false;
+  using Track = NoTrack<__nv_bfloat16>;
   struct K { float hh; };
   __device__ static __forceinline__ K make(const SweepArgs& a) { return K{static_cast<float>(a.hh)}; }
   __device__ static __forceinline__ C in(T v, const K&) { return __bfloat162float(v); }
@@ -90,20 +200,32 @@ struct PolBF16 {
   }
 };
 
-// binary64 storage, 64-bit fixed-point arithmetic (fixed.cuh).
+// binary64 storage, 64-bit fixed-point arithmetic (fixed.cuh), converted in
+// every pass at that pass's scale.  The magnitude key of an output is the
+// high word of |x|'s bit pattern: the pass's largest |x| is at most the
+// double with that high word and an all-ones low word.
 struct PolFixed {
   using T = double;
   using C = uint64_t;
   static constexpr int kElem = 8;
   static constexpr bool kFixed = true;
+  static constexpr bool kTrack = true;
+  static constexpr bool kResident = false;
   using K = FixedParams;
-  __device__ static __forceinline__ K make(const SweepArgs& a) {
-    K k = fx_params(__longlong_as_double(static_cast<long long>(a.maxbits[0])),
-                    __longlong_as_double(static_cast<long long>(a.maxbits[1])), a.hh, a.nsw, a.lmin);
-    if (k.bad && threadIdx.x == 0 && blockIdx.x == 0)
-      atomicOr(a.status, k.bad == 1 ? kStatusNonFinite : kStatusRange);
-    return k;
-  }
+  struct Track {
+    uint32_t m = 0;
+    __device__ __forceinline__ void add(double o) {
+      m = max(m, static_cast<uint32_t>(static_cast<unsigned long long>(__double_as_longlong(o)) >> 32) &
+                     0x7fffffffu);
+    }
+    __device__ __forceinline__ void add2(double a, double b) {
+      add(a);
+      add(b);
+    }
+    __device__ __forceinline__ uint32_t key() const { return m; }
+  };
+  __device__ static __forceinline__ K make(const SweepArgs& a) { return fx_pass_params<false>(a); }
+  __device__ static __forceinline__ void publish(const SweepArgs& a, const K& k) { fx_pass_publish(a, k); }
   __device__ static __forceinline__ C in(T v, const K& k) { return fx_in(v, k.Cu); }
   __device__ static __forceinline__ C in_halo(T v, const K& k) { return in(v, k); }
   __device__ static __forceinline__ T out(C v, const K& k) {
@@ -117,24 +239,54 @@ struct PolFixed {
 };
 
 // binary64 storage, 64-bit fixed point resident for the whole call: the
-// interior of the iterate buffers holds the biased integers U (fixed.cuh) and
-// the work buffer holds the pre-scaled source G = round(h*h*f*2^S), both
-// converted once per call.  Halo cells stay binary64 (the Dirichlet values
-// are never rewritten); the kernel converts them as it loads them.
+// interior of the iterate buffers holds the biased integers U (fixed.cuh) at
+// the scale the pass that wrote them chose, and the work buffer holds the
+// source G = round(h*h*f*2^S) at that same scale (written by the set-up,
+// rewritten by every pass that changes the scale).  Halo cells stay binary64
+// (the Dirichlet values are never rewritten); the kernel converts them as it
+// loads them.  The magnitude key of a pass: the largest and smallest high
+// word of its outputs U (two 32-bit min/max per output); the largest |q| is
+// below (max(hi_max - 2^27, 2^27 - hi_min) + 1) * 2^32.
 struct PolResident {
   using T = uint64_t;
   using C = uint64_t;
   static constexpr int kElem = 8;
   static constexpr bool kFixed = true;
+  static constexpr bool kTrack = true;
+  static constexpr bool kResident = true;
   using K = FixedParams;
-  __device__ static __forceinline__ K make(const SweepArgs& a) {
-    return fx_params(__longlong_as_double(static_cast<long long>(a.maxbits[0])),
-                     __longlong_as_double(static_cast<long long>(a.maxbits[1])), a.hh, a.nsw, a.lmin);
-  }
+  struct Track {
+    uint32_t mx = 0u, mn = 0xffffffffu;
+    __device__ __forceinline__ void add(uint64_t U) {
+      const uint32_t hi = static_cast<uint32_t>(U >> 32);
+      mx = max(mx, hi);
+      mn = min(mn, hi);
+    }
+    // two outputs: one three-way max and one three-way min
+    __device__ __forceinline__ void add2(uint64_t a, uint64_t b) {
+      const uint32_t ha = static_cast<uint32_t>(a >> 32), hb = static_cast<uint32_t>(b >> 32);
+      mx = __vimax3_u32(mx, ha, hb);
+      mn = __vimin3_u32(mn, ha, hb);
+    }
+    __device__ __forceinline__ uint32_t key() const {
+      constexpr int32_t kb = static_cast<int32_t>(kFxBias >> 32);
+      if (mx < mn) return 0u;  // wrote nothing
+      const int32_t a = static_cast<int32_t>(mx) - kb, b = kb - static_cast<int32_t>(mn);
+      return static_cast<uint32_t>(max(0, max(a, b)));
+    }
+  };
+  __device__ static __forceinline__ K make(const SweepArgs& a) { return fx_pass_params<true>(a); }
+  __device__ static __forceinline__ void publish(const SweepArgs& a, const K& k) { fx_pass_publish(a, k); }
   __device__ static __forceinline__ C in(T v, const K&) { return v; }
   __device__ static __forceinline__ C in_halo(T v, const K& k) {
     return fx_in(__longlong_as_double(static_cast<long long>(v)), k.Cu);
   }
+  __device__ static __forceinline__ bool needs_rescale(const K& k) { return k.dshift != 0 || k.fpath != 0; }
+  // an fpath pass: the staged binary64 source (its bit pattern) at the computing scale
+  __device__ static __forceinline__ T source_at(T f_bits, const K& k) {
+    return static_cast<uint64_t>(fx_source(__longlong_as_double(static_cast<long long>(f_bits)), k.Cg, k.H));
+  }
+  __device__ static __forceinline__ C rescale(C v, const K& k) { return fx_rescale(v, k.dshift); }
   __device__ static __forceinline__ T out(C v, const K&) { return v; }
   __device__ static __forceinline__ C update(C xm, C xp, C ym, C yp, C zm, C zp, T g, const K&) {
     return fx_div6(xm + xp + ym + yp + zm + zp + g + 3ull);

@@ -117,6 +117,7 @@ template <class Pol>
 struct SingleParams {
   CUtensorMap tm_u;
   CUtensorMap tm_f;
+  CUtensorMap tm_f64;  // resident fixed point: the binary64 source (read by fpath passes)
   typename Pol::T* out;
   SweepGeom g;
   SweepArgs a;
@@ -127,16 +128,34 @@ struct SrcGrid {
   using Params = SingleParams<Pol>;
   const Params* p;
   typename Pol::K k;
+  bool f64src = false;  // resident fixed point: this pass loads the binary64 source
   __device__ __forceinline__ SrcGrid(const Params* pp, bool need_k) : p(pp) {
     if (need_k) k = Pol::make(pp->a);
+    if constexpr (Pol::kResident) {
+      const int prev = (pp->a.pass + 2) % 3;
+      f64src = pp->a.fxgscale[prev] != pp->a.fxscale[prev];
+    }
   }
   __device__ __forceinline__ int64_t items() const { return p->g.items; }
   __device__ __forceinline__ uint32_t* status() const { return p->a.status; }
+  // Fixed point: publish this pass's scale (block 0), and combine the
+  // magnitude keys of what a warp wrote.
+  __device__ __forceinline__ void fx_begin() const {
+    if constexpr (Pol::kTrack) Pol::publish(p->a, k);
+  }
+  __device__ __forceinline__ void fx_end(uint32_t key) const {
+    if constexpr (Pol::kTrack) fx_track_commit(p->a, key);
+  }
+  // Resident fixed point, an fpath pass: store the source of cell (x, y, z).
+  __device__ __forceinline__ void store_source(int64_t x, int64_t y, int64_t z, unsigned long long g) const {
+    const SweepArgs& a = p->a;
+    a.gdst[x + y * a.gsy + z * a.gsz] = g;
+  }
   __device__ __forceinline__ bool view(int64_t item, ItemView<Pol>& v) const {
     v.t = decode_item(p->g, item);
     v.nx = p->g.nx; v.ny = p->g.ny; v.nz = p->g.nz; v.sy = p->g.sy; v.sz = p->g.sz;
     v.tm_u = &p->tm_u;
-    v.tm_f = &p->tm_f;
+    v.tm_f = f64src ? &p->tm_f64 : &p->tm_f;
     v.out = p->out;
     v.k = k;
     return true;
@@ -183,13 +202,18 @@ struct LaneState {
 };
 
 // One z step with the three plane slots rotated by ROT: raw plane p (sequence
-// number seq) has arrived in stage slot `slot`.
-template <class Pol, class Cfg, int ROT>
+// number seq) has arrived in stage slot `slot`.  RS (resident fixed point,
+// rare passes): the pass writes its output at a new scale (k.dshift: each
+// written value is shifted) and/or its ring holds the binary64 source
+// (k.fpath: converted at the computing scale as it is used, and stored in
+// the work grid for the cells this lane writes).
+template <class Pol, class Cfg, class Src, int ROT, bool RS>
 __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename Pol::K& k,
                                         const unsigned char* ring, int slot, uint32_t seq, int j,
                                         int p, int row0, int lane, int off, bool xin, uint32_t ymask,
                                         bool edge_halo, bool any_edge_halo, typename Pol::T* orow0,
-                                        int64_t sy, int64_t sz, int nz) {
+                                        int64_t sy, int64_t sz, int nz, const Src& src, int64_t x,
+                                        int64_t y0, typename Pol::Track& trk) {
   using T = typename Pol::T;
   using C = typename Pol::C;
   constexpr int TT = Cfg::T, S = Cfg::S;
@@ -239,51 +263,36 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
       const int w = rr - (TT - t);  // warp row, -T..R+T-1
       const bool in = xin && zin && ((ymask >> (w + TT)) & 1u);
       C v = c;
+      T fv{};
       if (in) {
-        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + Cfg::COL0 + lane];
+        fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + Cfg::COL0 + lane];
+        if constexpr (RS) {
+          if (k.fpath) fv = Pol::source_at(fv, k);
+        }
         v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2],
                         st.W[t - 1][OLD][rr + 1], st.W[t - 1][NEW][rr + 1], fv, k);
       }
       if (t < TT) {
         st.W[t][NEW][rr] = v;
       } else if (in && lane >= Cfg::XL && lane < 32 - Cfg::XL) {
-        orow0[static_cast<int64_t>(q) * sz + rr * sy] = Pol::out(v, k);
+        T o = Pol::out(v, k);
+        if constexpr (RS) {
+          if (k.dshift) o = Pol::rescale(o, k);
+          if (k.fpath) src.store_source(x, y0 + rr, q, fv);
+        }
+        orow0[static_cast<int64_t>(q) * sz + rr * sy] = o;
+        trk.add(o);
       }
     }
   }
 }
 
-template <class Pol, class Cfg, class Src>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
-    jacobi_tb(const __grid_constant__ typename Src::Params params) {
-  constexpr int S = Cfg::S, TT = Cfg::T, WY = Cfg::WY;
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ int abort_flag;
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  const uint32_t bar_full = smem_addr(base);
-  const uint32_t bar_empty = bar_full + 8 * S;
-  unsigned char* ring = base + 128;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, WY);
-    }
-    abort_flag = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  if (warp == WY) {
-    if (lane == 0) {
-      const Src src(&params, false);
-      produce<Pol, Cfg, Src>(src, bar_full, bar_empty, smem_addr(ring), &abort_flag);
-    }
-    return;
-  }
-  const Src src(&params, true);
+// The work items of one consumer warp; false if a bounded wait expired.
+template <class Pol, class Cfg, class Src, bool RS>
+__device__ __forceinline__ bool tb_consume(const Src& src, const unsigned char* ring, uint32_t bar_full,
+                                           uint32_t bar_empty, volatile int* abort_flag, int warp, int lane,
+                                           typename Pol::Track& trk) {
+  constexpr int S = Cfg::S, TT = Cfg::T;
   uint32_t* status = src.status();
   const int row0 = warp * Cfg::R;
   LaneState<Pol, Cfg> st;
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
       const uint32_t seq = seq0 + jj;
       const uint32_t s = seq % S;
       if (!mbar_wait_bounded(bar_full + 8 * s, (seq / S) & 1u, status)) {
-        abort_flag = 1;
+        *abort_flag = 1;
         return -1;
       }
       return static_cast<int>(s);
@@ -327,10 +336,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
 #define STENCIL_TB_STEP(ROT)                                                                       \
   {                                                                                                \
     const int slot = wait(j);                                                                      \
-    if (slot < 0) return;                                                                          \
-    tb_step<Pol, Cfg, ROT>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off, xin,  \
-                           ymask, edge_halo, any_edge_halo, orow0, v.sy, v.sz,                      \
-                           static_cast<int>(v.nz));                                                 \
+    if (slot < 0) return false;                                                                    \
+    tb_step<Pol, Cfg, Src, ROT, RS>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane,   \
+                                    off, xin, ymask, edge_halo, any_edge_halo, orow0, v.sy, v.sz,  \
+                                    static_cast<int>(v.nz), src, x, t.yo + row0, trk);             \
     if (j >= TT) release(seq0 + j - TT);                                                           \
     if (++j >= steps) break;                                                                       \
   }
@@ -343,6 +352,53 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
       if (q >= 0) release(seq0 + q);
     it = seq0 + steps;
   }
+  return true;
+}
+
+template <class Pol, class Cfg, class Src>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
+    jacobi_tb(const __grid_constant__ typename Src::Params params) {
+  constexpr int S = Cfg::S, WY = Cfg::WY;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int abort_flag;
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const uint32_t bar_full = smem_addr(base);
+  const uint32_t bar_empty = bar_full + 8 * S;
+  unsigned char* ring = base + 128;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, WY);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  if (warp == WY) {
+    if (lane == 0) {
+      const Src src(&params, false);
+      produce<Pol, Cfg, Src>(src, bar_full, bar_empty, smem_addr(ring), &abort_flag);
+    }
+    return;
+  }
+  const Src src(&params, true);
+  src.fx_begin();
+  typename Pol::Track trk;
+  bool ok;
+  if constexpr (Pol::kResident) {
+    // the rare passes that change the scale, or that follow such a pass, run
+    // their own instantiation, so the common one carries none of that code
+    ok = Pol::needs_rescale(src.k)
+             ? tb_consume<Pol, Cfg, Src, true>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk)
+             : tb_consume<Pol, Cfg, Src, false>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk);
+  } else {
+    ok = tb_consume<Pol, Cfg, Src, false>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk);
+  }
+  if (ok) src.fx_end(trk.key());
 }
 
 }  // namespace stencil

@@ -59,6 +59,17 @@ int run_tb(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, con
   if (rc) return rc;
   rc = make_tensor_map(&prm.tm_f, f, Cfg::BOXW, Cfg::FROWS);
   if (rc) return rc;
+  if (a.fsrc64) {  // resident fixed point: the caller's binary64 source, same box
+    Grid f64 = f;
+    f64.data = const_cast<double*>(a.fsrc64);
+    f64.sy = a.fsy;
+    f64.sz = a.fsz;
+    f64.dtype = STENCIL_F64;
+    rc = make_tensor_map(&prm.tm_f64, f64, Cfg::BOXW, Cfg::FROWS);
+    if (rc) return rc;
+  } else {
+    prm.tm_f64 = prm.tm_f;
+  }
   int grid = 0, per_sm = 0;
   const int64_t txy = ((in.nx + Cfg::BXO - 1) / Cfg::BXO) * ((in.ny + Cfg::BYO - 1) / Cfg::BYO);
   rc = grid_for(kern, Cfg::THREADS, Cfg::SMEM, txy * in.nz, ctx->num_sms, &grid, &per_sm);

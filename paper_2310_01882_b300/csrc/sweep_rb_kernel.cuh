@@ -61,11 +61,13 @@ struct RbLaneState {
   C W[Cfg::T][3][Cfg::NROW];  // stage t's values of its colour: three planes, its rows
 };
 
-template <class Pol, class Cfg, int ROT>
+// RS: the pass writes the resident fixed point at a new scale (see tb_step).
+template <class Pol, class Cfg, class Src, int ROT, bool RS>
 __device__ __forceinline__ void rb_step(RbLaneState<Pol, Cfg>& st, const typename Pol::K& k,
                                         const unsigned char* ring, int slot, uint32_t seq, int j, int p, int row0,
                                         int lane, int off, bool xin0, bool xin1, uint32_t ymask, int pb,
-                                        typename Pol::T* orow0, int64_t sy, int64_t sz, int nz) {
+                                        typename Pol::T* orow0, int64_t sy, int64_t sz, int nz,
+                                        const Src& src, int64_t x, int64_t y0, typename Pol::Track& trk) {
   using T = typename Pol::T;
   using C = typename Pol::C;
   constexpr int TT = Cfg::T, S = Cfg::S;
@@ -116,7 +118,16 @@ __device__ __forceinline__ void rb_step(RbLaneState<Pol, Cfg>& st, const typenam
       if (in) {
         // Every policy's update starts with xm + xp, and addition is
         // commutative, so the two x neighbours go in without a select.
-        const T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + 2 * lane + ic];
+        T fv = F[(row0 + rr + t - 1) * Cfg::BOXW + off + 2 * lane + ic];
+        if constexpr (RS) {
+          // fpath: the source converted here; stored once, by the tile that
+          // owns the cell, at the stage that updates it
+          if (k.fpath) {
+            fv = Pol::source_at(fv, k);
+            if (w >= 0 && w < Cfg::R && 2 * lane >= TT && 2 * lane + 1 < 64 - TT)
+              src.store_source(x + ic, y0 + w, q, fv);
+          }
+        }
         v = Pol::update(other, own, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2], st.W[t - 1][OLD][rr + 1],
                         st.W[t - 1][NEW][rr + 1], fv, k);
       } else {
@@ -127,44 +138,32 @@ __device__ __forceinline__ void rb_step(RbLaneState<Pol, Cfg>& st, const typenam
       } else if (yzin && 2 * lane >= TT && 2 * lane + 1 < 64 - TT) {
         // both colours of plane q are final: this stage's and stage T-1's
         typename Pol::T* o = orow0 + static_cast<int64_t>(q) * sz + rr * sy;
-        if (in) o[ic] = Pol::out(v, k);
-        if (ic ? xin0 : xin1) o[ic ^ 1] = Pol::out(own, k);
+        // both outputs' magnitudes in one step; a cell that is not interior
+        // keeps its staged value, which the other output's stands in for
+        T ov = Pol::out(v, k);
+        T oo = Pol::out(own, k);
+        if constexpr (RS) {
+          if (k.dshift) {
+            ov = Pol::rescale(ov, k);
+            oo = Pol::rescale(oo, k);
+          }
+        }
+        const bool wo = ic ? xin0 : xin1;
+        if (in) o[ic] = ov;
+        if (wo) o[ic ^ 1] = oo;
+        if (in || wo) trk.add2(in ? ov : oo, wo ? oo : ov);
+
       }
     }
   }
 }
 
-template <class Pol, class Cfg, class Src>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
-    redblack_tb(const __grid_constant__ typename Src::Params params) {
-  constexpr int S = Cfg::S, TT = Cfg::T, WY = Cfg::WY;
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ int abort_flag;
-  unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  const uint32_t bar_full = smem_addr(base);
-  const uint32_t bar_empty = bar_full + 8 * S;
-  unsigned char* ring = base + 128;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, WY);
-    }
-    abort_flag = 0;
-    fence_mbar_init();
-  }
-  __syncthreads();
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  if (warp == WY) {
-    if (lane == 0) {
-      const Src src(&params, false);
-      produce<Pol, Cfg, Src>(src, bar_full, bar_empty, smem_addr(ring), &abort_flag);
-    }
-    return;
-  }
-  const Src src(&params, true);
+// The work items of one consumer warp; false if a bounded wait expired.
+template <class Pol, class Cfg, class Src, bool RS>
+__device__ __forceinline__ bool rb_consume(const Src& src, const unsigned char* ring, uint32_t bar_full,
+                                           uint32_t bar_empty, volatile int* abort_flag, int warp, int lane,
+                                           typename Pol::Track& trk) {
+  constexpr int S = Cfg::S, TT = Cfg::T;
   uint32_t* status = src.status();
   const int row0 = warp * Cfg::R;
   RbLaneState<Pol, Cfg> st;
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
       const uint32_t seq = seq0 + jj;
       const uint32_t s = seq % S;
       if (!mbar_wait_bounded(bar_full + 8 * s, (seq / S) & 1u, status)) {
-        abort_flag = 1;
+        *abort_flag = 1;
         return -1;
       }
       return static_cast<int>(s);
@@ -202,14 +201,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
       if (lane == 0) mbar_arrive(bar_empty + 8 * (seq % S));
     };
     for (;;) {
-#define STENCIL_RB_STEP(ROT)                                                                       \
-  {                                                                                                \
-    const int slot = wait(j);                                                                      \
-    if (slot < 0) return;                                                                          \
-    rb_step<Pol, Cfg, ROT>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off, xin0, \
-                           xin1, ymask, pb, orow0, v.sy, v.sz, static_cast<int>(v.nz));            \
-    if (j >= TT) release(seq0 + j - TT);                                                           \
-    if (++j >= steps) break;                                                                       \
+#define STENCIL_RB_STEP(ROT)                                                                         \
+  {                                                                                                  \
+    const int slot = wait(j);                                                                        \
+    if (slot < 0) return false;                                                                      \
+    rb_step<Pol, Cfg, Src, ROT, RS>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off,  \
+                                    xin0, xin1, ymask, pb, orow0, v.sy, v.sz, static_cast<int>(v.nz),  \
+                                    src, x, t.yo + row0, trk);                                         \
+    if (j >= TT) release(seq0 + j - TT);                                                             \
+    if (++j >= steps) break;                                                                         \
   }
       STENCIL_RB_STEP(0)
       STENCIL_RB_STEP(1)
@@ -220,6 +220,51 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
       if (q >= 0) release(seq0 + q);
     it = seq0 + steps;
   }
+  return true;
+}
+
+template <class Pol, class Cfg, class Src>
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
+    redblack_tb(const __grid_constant__ typename Src::Params params) {
+  constexpr int S = Cfg::S, WY = Cfg::WY;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int abort_flag;
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const uint32_t bar_full = smem_addr(base);
+  const uint32_t bar_empty = bar_full + 8 * S;
+  unsigned char* ring = base + 128;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, WY);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  if (warp == WY) {
+    if (lane == 0) {
+      const Src src(&params, false);
+      produce<Pol, Cfg, Src>(src, bar_full, bar_empty, smem_addr(ring), &abort_flag);
+    }
+    return;
+  }
+  const Src src(&params, true);
+  src.fx_begin();
+  typename Pol::Track trk;
+  bool ok;
+  if constexpr (Pol::kResident) {
+    ok = Pol::needs_rescale(src.k)
+             ? rb_consume<Pol, Cfg, Src, true>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk)
+             : rb_consume<Pol, Cfg, Src, false>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk);
+  } else {
+    ok = rb_consume<Pol, Cfg, Src, false>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk);
+  }
+  if (ok) src.fx_end(trk.key());
 }
 
 // The kernel a configuration runs: redblack_tb for RbCfg, jacobi_tb for
