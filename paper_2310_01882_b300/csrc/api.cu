@@ -421,6 +421,9 @@ int stencil_residual(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid
   if (r && (rc = same_extents(gu, gr, "u", "r"))) return rc;
   if (gu.dtype != STENCIL_F64 || gf.dtype != STENCIL_F64 || (r && gr.dtype != STENCIL_F64))
     return set_error(STENCIL_ERR_DTYPE, "residual: u, f and r must be F64");
+  if (r && (gr.data == gu.data || gr.data == gf.data))
+    return set_error(STENCIL_ERR_ARG, "residual: r aliases %s (r is written while u and f are read)",
+                     gr.data == gu.data ? "u" : "f");
   if (!norms_dev) return set_error(STENCIL_ERR_ARG, "residual: null norms pointer");
   if (!(h > 0.0) || !(h < 1.0e150)) return set_error(STENCIL_ERR_ARG, "residual: h must be positive and finite");
   DeviceGuard dg(ctx->device);

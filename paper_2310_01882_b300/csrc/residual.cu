@@ -10,6 +10,8 @@
 // per block by a fixed shuffle tree, written to per-block partials in ctx
 // scratch, and summed in block order by a single-block kernel, so the norms
 // are reproducible bit for bit from run to run.
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -135,21 +137,58 @@ constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[2 * kNoAllocMaxPartials];
 
-// Device address of g_noalloc_partials, looked up once per device (with that
-// device current) on the first call made on it.
+// Device address of g_noalloc_partials in the CUDA context current on the
+// calling thread.  The address belongs to one context (and one load of this
+// library's module into it): it is looked up with the device current on the
+// first call in each context and kept per device together with that
+// context's unique id, so a new context on the device -- after
+// cudaDeviceReset, or one the caller created with the driver API -- gets its
+// own lookup instead of a stale address.
 static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+static unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the context current on this thread (0 if there is none).
+static int current_ctx_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  if (!get_current || !get_id) return set_error(STENCIL_ERR_CUDA, "residual_noalloc: context query unavailable");
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS) return set_error(STENCIL_ERR_CUDA, "residual_noalloc: cuCtxGetCurrent failed");
+  *id = 0;
+  if (c && get_id(c, id) != CUDA_SUCCESS) return set_error(STENCIL_ERR_CUDA, "residual_noalloc: cuCtxGetId failed");
+  return STENCIL_OK;
+}
 
 static int noalloc_scratch(int device, double** out) {
   if (device < 0 || device >= kNoAllocMaxDevices)
     return set_error(STENCIL_ERR_ARG, "residual_noalloc: device %d out of range", device);
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[device]) {
+  unsigned long long id = 0;
+  int rc = current_ctx_id(&id);
+  if (rc) return rc;
+  if (!g_noalloc_ptr[device] || id == 0 || id != g_noalloc_ctx[device]) {
     void* p = nullptr;
-    int rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials),
-                        "residual_noalloc: cudaGetSymbolAddress");
+    rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials), "residual_noalloc: cudaGetSymbolAddress");
+    if (rc) return rc;
+    rc = current_ctx_id(&id);  // the lookup makes the device's primary context current if none was
     if (rc) return rc;
     g_noalloc_ptr[device] = static_cast<double*>(p);
+    g_noalloc_ctx[device] = id;
   }
   *out = g_noalloc_ptr[device];
   return STENCIL_OK;
@@ -169,6 +208,9 @@ extern "C" int stencil_residual_noalloc(const stencil_grid* u, const stencil_gri
   if (r && (rc = same_extents(gu, gr, "u", "r"))) return rc;
   if (gu.dtype != STENCIL_F64 || gf.dtype != STENCIL_F64 || (r && gr.dtype != STENCIL_F64))
     return set_error(STENCIL_ERR_DTYPE, "residual_noalloc: u, f and r must be F64");
+  if (r && (gr.data == gu.data || gr.data == gf.data))
+    return set_error(STENCIL_ERR_ARG, "residual_noalloc: r aliases %s (r is written while u and f are read)",
+                     gr.data == gu.data ? "u" : "f");
   if (!norms_dev) return set_error(STENCIL_ERR_ARG, "residual_noalloc: null norms pointer");
   if (!(h > 0.0) || !(h < 1.0e150))
     return set_error(STENCIL_ERR_ARG, "residual_noalloc: h must be positive and finite");
