@@ -190,3 +190,18 @@ def loss_and_grads(p, x, t, channels):
     y, cache = forward(p, x, channels)
     loss, gy = mse(y, t)
     return loss, backward(p, cache, gy, channels), y
+
+
+def adam_step(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba) of the parameters p with gradient g,
+    first and second moments m, v, t the step number counted from 1, in
+    binary64: m' = b1 m + (1 - b1) g, v' = b2 v + (1 - b2) g^2, bias
+    corrections c1 = 1 - b1^t, c2 = 1 - b2^t, and
+    p' = p - lr (m' / c1) / (sqrt(v' / c2) + eps).
+    Returns (p', m', v')."""
+    p, g, m, v = (np.asarray(a, dtype=np.float64) for a in (p, g, m, v))
+    m1 = b1 * m + (1.0 - b1) * g
+    v1 = b2 * v + (1.0 - b2) * g * g
+    c1 = 1.0 - b1 ** t
+    c2 = 1.0 - b2 ** t
+    return p - lr * (m1 / c1) / (np.sqrt(v1 / c2) + eps), m1, v1

@@ -83,6 +83,8 @@ NET_MUTANTS = {
     "filter_weights": ("y = 0.25 * p[sl(0, n)] + 0.5 * p[sl(1, n + 1)] + 0.25 * p[sl(2, n + 2)]",
                        "y = 0.25 * p[sl(0, n)] + 0.5 * p[sl(1, n + 1)] + 0.2 * p[sl(2, n + 2)]"),
     "mse_grad_half": ("return float(np.mean(d * d)), 2.0 * d / d.size", "return float(np.mean(d * d)), d / d.size"),
+    "adam_eps_inside_sqrt": ("(np.sqrt(v1 / c2) + eps)", "np.sqrt(v1 / c2 + eps)"),
+    "adam_no_bias_correction": ("c1 = 1.0 - b1 ** t", "c1 = 1.0"),
 }
 
 

@@ -107,3 +107,41 @@ def test_network_gradient_finite_differences(channels):
             assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-4), (name, idx, fd, an)
             checked += 1
     assert checked >= 20
+
+
+# ---- Adam (the optimiser of the warm-start training) -----------------------
+
+def test_adam_first_step_closed_form():
+    """From zero moments the bias corrections make m_hat = g and
+    v_hat = g^2 exactly, so the first step moves each parameter by
+    lr * g / (|g| + eps): about lr in the gradient's sign, and visibly less
+    for a gradient near eps (1e-8 here: half of lr)."""
+    g = np.array([0.3, -2.0, 1e-8, -1e-3, 0.0])
+    p0 = np.array([1.0, -1.0, 0.5, 0.25, 2.0])
+    p1, m1, v1 = net.adam_step(p0, g, np.zeros(5), np.zeros(5), 1, lr=0.01)
+    want = p0 - 0.01 * g / (np.abs(g) + 1e-8)
+    np.testing.assert_allclose(p1, want, rtol=1e-14, atol=1e-17)
+    assert abs((p0[2] - p1[2]) - 0.005) <= 1e-12          # g = eps: half a step
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-15)
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-14)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """With a constant gradient, m_t / c1 = g and v_t / c2 = g^2 for every
+    t: each step moves by lr * g / (|g| + eps)."""
+    g = np.array([0.7, -0.05])
+    p = np.array([0.0, 0.0])
+    m = v = np.zeros(2)
+    for t in range(1, 6):
+        p, m, v = net.adam_step(p, g, m, v, t, lr=0.1)
+    np.testing.assert_allclose(p, -5 * 0.1 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_adam_alternating_gradient_second_step():
+    """g then -g: m_2 / c1 = -(1 - b1) / (1 + b1) g and v_2 / c2 = g^2,
+    so the second step moves back by lr (1 - b1)/(1 + b1) g / (|g| + eps)."""
+    g = np.array([0.2, -3.0])
+    p1, m1, v1 = net.adam_step(np.zeros(2), g, np.zeros(2), np.zeros(2), 1, lr=0.05)
+    p2, _, _ = net.adam_step(p1, -g, m1, v1, 2, lr=0.05)
+    step2 = 0.05 * (0.1 / 1.9) * g / (np.abs(g) + 1e-8)
+    np.testing.assert_allclose(p2 - p1, step2, rtol=1e-12)
