@@ -148,14 +148,15 @@ def average2d(u, nsweeps):
 
 
 def apply_linear(u, offsets, coeffs, out=None):
-    """out(x) = sum_p coeffs[p] * u(x + offsets[p]) on the interior (offsets:
-    (npoints, 3) ints dx, dy, dz in [-1, 1]); the halo of out is out's own
-    (zeros if out is None)."""
+    """out(x) = sum_p coeffs[p] * u(x + offsets[p]) on the interior points
+    whose reads lie in the field (offsets: (npoints, 3) ints dx, dy, dz in
+    [-3, 3]; with r = max |d|, indices r .. n + 1 - r); the rest of out is
+    out's own (zeros if out is None)."""
     u = _c64(u)
     out = np.zeros_like(u) if out is None else np.array(out, dtype=np.float64, order="C", copy=True)
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
     c = _c64(np.asarray(coeffs, dtype=np.float64).reshape(-1))
-    assert off.shape[0] == c.size and np.all(np.abs(off) <= 1)
+    assert off.shape[0] == c.size and np.all(np.abs(off) <= 3)
     nx, ny, nz = _dims(u)
     lib().oracle_apply_linear(_ptr(u), _ptr(out), nx, ny, nz, _ptr(off), _ptr(c), c.size)
     return out

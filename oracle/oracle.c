@@ -189,18 +189,25 @@ void oracle_average2d(double* u, double* tmp, int64_t nx, int64_t ny, int64_t nz
 
 /*
  * A general linear stencil apply (Section 2.2: a stencil.apply reads an
- * input field at constant offsets and writes one output value per point;
- * here the body is a linear combination):
+ * input field at constant offsets and writes one output value per point of
+ * its bounds; here the body is a linear combination):
  *   out(x, y, z) = sum_p c_p * in(x + dx_p, y + dy_p, z + dz_p)
- * over the interior, terms added in the listed order (each product rounded,
- * then added), offsets within the one-cell halo (|d| <= 1 per axis).  The
- * halo of out is not written.  offsets: 3 * npoints ints (dx, dy, dz).
+ * terms added in the listed order (each product rounded, then added).  The
+ * output bounds are the interior points whose every read lies in the field
+ * (halo included): with r = max |d| over the offsets, indices r .. n + 1 - r
+ * per axis -- the whole interior for offsets within the one-cell halo.
+ * Nothing else of out is written.  offsets: 3 * npoints ints (dx, dy, dz).
  */
 void oracle_apply_linear(const double* in, double* out, int64_t nx, int64_t ny, int64_t nz,
                          const int* offsets, const double* coeffs, int npoints) {
-  for (int64_t k = 1; k <= nz; ++k)
-    for (int64_t j = 1; j <= ny; ++j)
-      for (int64_t i = 1; i <= nx; ++i) {
+  int64_t r = 1;
+  for (int p = 0; p < 3 * npoints; ++p) {
+    const int64_t a = offsets[p] < 0 ? -offsets[p] : offsets[p];
+    if (a > r) r = a;
+  }
+  for (int64_t k = r; k <= nz + 1 - r; ++k)
+    for (int64_t j = r; j <= ny + 1 - r; ++j)
+      for (int64_t i = r; i <= nx + 1 - r; ++i) {
         double acc = 0.0;
         for (int p = 0; p < npoints; ++p) {
           const double term = coeffs[p] * AT(in, i + offsets[3 * p], j + offsets[3 * p + 1], k + offsets[3 * p + 2]);

@@ -59,3 +59,64 @@ def test_dense_matrix():
                 n += 1
     ref = (M @ flat).reshape(nz, ny, nx)
     assert np.max(np.abs(got[1:-1, 1:-1, 1:-1] - ref)) <= 1e-13
+
+
+@pytest.mark.parametrize("d", [(2, 0, 0), (0, -2, 1), (-3, 1, 2), (1, 3, -3)])
+def test_wide_unit_term_is_a_shift_on_the_shrunken_bounds(d):
+    """Offsets beyond the one-cell halo: the output covers indices r .. n+1-r
+    (r = max |d|), where every read lies in the field; nothing else is
+    written."""
+    u = field((9, 8, 7), 6)
+    sentinel = np.full(u.shape, 7.5)
+    got = oracle.apply_linear(u, [d], [1.0], out=sentinel)
+    r = max(abs(v) for v in d)
+    dx, dy, dz = d
+    nz, ny, nx = (s - 2 for s in u.shape)
+    core = (slice(r, nz + 2 - r), slice(r, ny + 2 - r), slice(r, nx + 2 - r))
+    ref = u[r + dz:nz + 2 - r + dz, r + dy:ny + 2 - r + dy, r + dx:nx + 2 - r + dx]
+    assert np.array_equal(got[core], ref)
+    mask = np.ones(u.shape, dtype=bool)
+    mask[core] = False
+    assert np.all(got[mask] == 7.5)
+
+
+def test_fourth_order_laplacian_exact_on_quintics():
+    """The 13-point fourth-order Laplacian ((-1, 16, -30, 16, -1)/12 along
+    each axis, unit spacing) is exact for polynomials of degree <= 5 in each
+    variable: u = i^4 + 2 j^5 - k^3 gives 12 i^2 + 40 j^3 - 6 k on the
+    points two cells inside."""
+    nx, ny, nz = 10, 9, 8
+    k, j, i = np.meshgrid(np.arange(nz + 2), np.arange(ny + 2), np.arange(nx + 2), indexing="ij")
+    u = (i.astype(float) ** 4 + 2.0 * j.astype(float) ** 5 - k.astype(float) ** 3)
+    w = [-1.0 / 12, 16.0 / 12, -30.0 / 12, 16.0 / 12, -1.0 / 12]
+    offs, coef = [], []
+    for axis in range(3):
+        for s, c in zip(range(-2, 3), w):
+            d = [0, 0, 0]
+            d[axis] = s
+            offs.append(tuple(d))
+            coef.append(c)
+    got = oracle.apply_linear(u, offs, coef)
+    exact = 12.0 * i ** 2 + 40.0 * j ** 3 - 6.0 * k
+    core = (slice(2, nz), slice(2, ny), slice(2, nx))
+    assert np.max(np.abs(got[core] - exact[core])) <= 1e-9 * np.max(np.abs(u))
+
+
+def test_dense_matrix_radius_two():
+    rng = np.random.default_rng(8)
+    u = field((6, 5, 5), 9)
+    offs = [tuple(int(v) for v in rng.integers(-2, 3, 3)) for _ in range(11)] + [(2, 2, 2)]
+    coef = rng.standard_normal(12)
+    got = oracle.apply_linear(u, offs, coef)
+    nz, ny, nx = (s - 2 for s in u.shape)
+    flat = u.reshape(-1)
+    rows, ref = [], []
+    for k in range(2, nz):
+        for j in range(2, ny):
+            for i in range(2, nx):
+                row = np.zeros(flat.size)
+                for (dx, dy, dz), c in zip(offs, coef):
+                    row[np.ravel_multi_index((k + dz, j + dy, i + dx), u.shape)] += c
+                rows.append(row)
+                ref.append(got[k, j, i])
+    assert np.max(np.abs(np.array(rows) @ flat - np.array(ref))) <= 1e-13
