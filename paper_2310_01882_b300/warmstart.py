@@ -33,6 +33,59 @@ from . import stencil as S
 
 CHANNELS = [16, 32, 64, 64]
 RTOL = 1e-8
+# The network trained on 2000 (f, u*) pairs of 128^3 (seeds 10000..11999),
+# 30 epochs: its parameters in wsnet_load's parameters-only format.
+TRAINED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "wsnet_128cubed_2000pairs.wsnet")
+
+
+def save_params_only(path, levels, channels, n, params):
+    """Write parameters in the parameters-only file format wsnet_load reads
+    (magic "WSNET01", int32 levels, int32 channels[levels], int32 n, int64
+    count, FP32 parameters; little endian); loading it starts the optimiser
+    afresh."""
+    import struct
+    params = np.ascontiguousarray(params, dtype="<f4")
+    with open(path + ".tmp", "wb") as fh:
+        fh.write(b"WSNET01\x00")
+        fh.write(struct.pack("<i", levels))
+        fh.write(struct.pack(f"<{levels}i", *channels))
+        fh.write(struct.pack("<iq", n, params.size))
+        fh.write(params.tobytes())
+    os.replace(path + ".tmp", path)
+
+
+def trained_net(n=128):
+    """The committed trained network (for 128^3 grids)."""
+    net = S.WsNet(len(CHANNELS), CHANNELS, n, seed=1)
+    S.wsnet_load(net, TRAINED)
+    return net
+
+
+def warm_starts(net, ctx, fs, h, norms, tmp, check_sweeps=50):
+    """Warm starts for the F64 source Fields fs: the network's output where,
+    after `check_sweeps` plain FP64 Jacobi sweeps from it and from zero, its
+    FP64 relative residual is the smaller, else None (the fallback: plain
+    Jacobi from zero).  The output's own residual is no guide: its error is
+    mostly high-frequency, which the first sweeps remove, so it starts above
+    the zero start's and ends far below.  tmp: an F64 Field of the same
+    extents (scratch).  Returns (starts, residuals after the check from the
+    warm start, from zero); the caller times it."""
+    n = fs[0].nx
+    starts, rw, rz = [], [], []
+    for f in fs:
+        u = S.Field(n, n, n)
+        S.wsnet_infer(net, f, u)
+        start = u.storage.clone()
+        rels = []
+        for v in (u, S.Field(n, n, n)):
+            S.stencil_jacobi_sweep(ctx, v, tmp, f, None, h, check_sweeps, 0, S.SWEEP_AUTO)
+            S.stencil_residual(ctx, v, f, h, norms)
+            nrm = norms.cpu().numpy()
+            rels.append(float(nrm[0] / nrm[1]))
+        rw.append(rels[0])
+        rz.append(rels[1])
+        starts.append(start if rels[0] < rels[1] else None)
+    return starts, rw, rz
 
 
 class Solver:
@@ -392,6 +445,8 @@ def main():
         train_s = time.perf_counter() - t0
         del fs, us
         np.save(os.path.join(args.out, "wsnet_params.npy"), net.get_params())
+        save_params_only(os.path.join(args.out, "wsnet_params.wsnet"), len(CHANNELS), CHANNELS, args.n,
+                         net.get_params())
     rows = evaluate(net, solver, [20000 + i for i in range(args.test)])
     summary = summarise(rows)
     log(json.dumps(summary))

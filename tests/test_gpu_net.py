@@ -57,10 +57,13 @@ def from_oracle_grads(g, channels):
 
 
 @pytest.mark.parametrize("levels,channels,n,tc", [(2, [16, 32], 16, 1), (3, [16, 32, 64], 16, 1),
-                                                   (3, [16, 32, 64], 32, 1), (3, [16, 32, 64], 32, 0)])
+                                                   (3, [16, 32, 64], 32, 1), (3, [16, 32, 64], 32, 0),
+                                                   (2, [16, 32], 128, 1)])
 def test_forward_backward_match_oracle(levels, channels, n, tc):
     """tc = 1: the tcgen05 convolutions run wherever they apply (rows of 16
-    to 128 voxels: levels 0 and 1 at n = 32); tc = 0: mma.sync everywhere."""
+    to 128 voxels: levels 0 and 1 at n = 32; at n = 128 level 0 runs the
+    row-halo kernel of the production 128^3 net, forward and input
+    gradient); tc = 0: mma.sync everywhere."""
     import torch
     net = S.WsNet(levels, channels, n, seed=3)
     S.wsnet_use_tcgen05(net, tc)
@@ -102,7 +105,7 @@ def test_forward_backward_match_oracle(levels, channels, n, tc):
     net.close()
 
 
-@pytest.mark.parametrize("n", [32, 64])
+@pytest.mark.parametrize("n", [32, 64, 128])
 def test_tcgen05_matches_mma_sync(n):
     """The two convolution paths agree on the same net and data (both are
     bf16 products with FP32 sums; only the summation order differs)."""
@@ -218,3 +221,54 @@ def test_checkpoint_resumes_training_exactly(tmp_path):
     assert not np.array_equal(c.get_params(), ref.get_params())
     for net in (ref, a, b, c):
         net.close()
+
+
+def _read_checkpoint(path):
+    """wsnet_save's file: parameters, the Adam step count and both moments."""
+    import struct
+    with open(path, "rb") as fh:
+        raw = fh.read()
+    assert raw[:8] == b"WSNET02\x00"
+    L = struct.unpack_from("<i", raw, 8)[0]
+    off = 12 + 4 * L + 4
+    cnt = struct.unpack_from("<q", raw, off)[0]
+    off += 8
+    p = np.frombuffer(raw, dtype="<f4", count=cnt, offset=off).astype(np.float64)
+    off += 4 * cnt
+    step = struct.unpack_from("<q", raw, off)[0]
+    off += 8
+    m = np.frombuffer(raw, dtype="<f4", count=cnt, offset=off).astype(np.float64)
+    v = np.frombuffer(raw, dtype="<f4", count=cnt, offset=off + 4 * cnt).astype(np.float64)
+    return p, step, m, v
+
+
+def test_adam_update_matches_oracle(tmp_path):
+    """Each of three training steps applies the oracle's Adam update
+    (oracle.net.adam_step: bias corrections, eps outside the square root)
+    to the step's gradient, with the kernel's binary32 hyperparameters
+    (0.999 as binary32 makes 1 - b2 differ from 0.001 by 1.3e-5): with the
+    state saved before and after the step, the gradient is
+    g = (m_t - b1 m_(t-1)) / (1 - b1), and the oracle's (p, v) from
+    (p, m, v)_(t-1) and g equal the kernel's to binary32 rounding."""
+    n = 16
+    lr = 1e-3
+    net = S.WsNet(2, [16, 32], n, seed=41)
+    fs = [S.Field.from_numpy(inputs.grf(n, seed=80 + i)) for i in range(4)]
+    us = [S.Field.from_numpy(0.01 * inputs.grf(n, seed=90 + i)) for i in range(4)]
+    path = str(tmp_path / "s.bin")
+    S.wsnet_save(net, path)
+    prev = _read_checkpoint(path)
+    assert prev[1] == 0 and not prev[2].any() and not prev[3].any()
+    for t in range(1, 4):
+        S.wsnet_train_step(net, fs[t - 1:t + 1], us[t - 1:t + 1], lr)
+        S.wsnet_save(net, path)
+        p, step, m, v = _read_checkpoint(path)
+        assert step == t
+        b1, b2, eps = (float(np.float32(x)) for x in (0.9, 0.999, 1e-8))
+        g = (m - b1 * prev[2]) / (1.0 - b1)
+        p_ref, m_ref, v_ref = onet.adam_step(prev[0], g, prev[2], prev[3], t, float(np.float32(lr)), b1, b2, eps)
+        assert np.max(np.abs(v - v_ref)) <= 1e-6 * np.max(np.abs(v_ref)), t
+        assert np.all(np.abs(p - p_ref) <= 2e-7 * np.abs(p_ref) + 1e-5 * lr), (t, np.max(np.abs(p - p_ref)))
+        assert np.max(np.abs(prev[0] - p)) > 0.5 * lr        # the step moved the parameters
+        prev = (p, step, m, v)
+    net.close()
