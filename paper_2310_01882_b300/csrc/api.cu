@@ -285,8 +285,9 @@ int stencil_apply_linear(stencil_ctx* ctx, const stencil_grid* in, const stencil
   if (npoints < 1 || npoints > kMaxLinearTerms || !offsets || !coeffs)
     return set_error(STENCIL_ERR_ARG, "apply_linear: need 1..%d terms", kMaxLinearTerms);
   for (int p = 0; p < 3 * npoints; ++p)
-    if (offsets[p] < -1 || offsets[p] > 1)
-      return set_error(STENCIL_ERR_ARG, "apply_linear: offsets must lie in the one-cell halo (-1..1)");
+    if (offsets[p] < -kMaxApplyRadius || offsets[p] > kMaxApplyRadius)
+      return set_error(STENCIL_ERR_ARG, "apply_linear: offsets must lie in -%d..%d", kMaxApplyRadius,
+                       kMaxApplyRadius);
   DeviceGuard dg(ctx->device);
   if (dg.rc) return dg.rc;
   return launch_apply_linear(ctx, gi, go, offsets, coeffs, npoints, static_cast<cudaStream_t>(stream));
@@ -364,6 +365,23 @@ int stencil_redblack_config_count(int32_t dtype, int32_t flags, int32_t with_wor
   *count = (sweeps_per_pass >= 1 && 2 * sweeps_per_pass <= kMaxPass)
                ? sweep_variants_rb(policy, 2 * sweeps_per_pass, &v)
                : 0;
+  return STENCIL_OK;
+}
+
+int stencil_residual_config_count(int32_t* count) {
+  if (!count) return set_error(STENCIL_ERR_ARG, "residual_config_count: null count");
+  const SweepVariant* v;
+  *count = sweep_variants_resid(&v);
+  return STENCIL_OK;
+}
+
+int stencil_residual_config_select(stencil_ctx* ctx, int32_t index) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "residual_config_select: null ctx");
+  const SweepVariant* v;
+  const int n = sweep_variants_resid(&v);
+  if (index < 0 || index >= n)
+    return set_error(STENCIL_ERR_ARG, "residual_config_select: index %d out of range (%d configurations)", index, n);
+  ctx->resid_choice = index;
   return STENCIL_OK;
 }
 

@@ -105,6 +105,7 @@ struct SrcBatch {
     const SweepGeom& g = d.g[DT];
     v.t = decode_item(g, item - p->base[i]);
     v.nx = g.nx; v.ny = g.ny; v.nz = g.nz; v.sy = g.sy; v.sz = g.sz;
+    v.osy = g.sy; v.osz = g.sz;
     v.tm_u = &d.tm_e[DT][p->parity];
     v.tm_f = &d.tm_r[DT];
     v.out = static_cast<typename Pol::T*>(d.e[p->parity ^ 1]);

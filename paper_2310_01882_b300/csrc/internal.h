@@ -23,6 +23,7 @@ struct stencil_ctx {
   int best_pass[stencil::kNumPolicies];
   // red-black configuration index per policy and colour stages per pass
   int rb_choice[stencil::kNumPolicies][stencil::kMaxPass + 1];
+  int resid_choice;  // fixed-point residual configuration index
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)
@@ -44,9 +45,13 @@ constexpr size_t kScratchRange = 176;     // 3 x uint64 bits: max|u| halo, max|f
 constexpr size_t kScratchFxMag = 208;     // 4 x uint32: fixed-point magnitude keys (ring of 3)
 constexpr size_t kScratchFxScale = 224;   // 4 x int32: fixed-point scales (ring of 3)
 constexpr size_t kScratchFxGScale = 240;  // 4 x int32: scale of the stored source (ring of 3)
+constexpr size_t kScratchApplyRange = 80; // uint64 bits of max|in| (linear apply, fixed point)
 constexpr size_t kScratchPartials = 256;  // residual partial sums
 constexpr int kMaxPartials = 2048;        // blocks of the residual kernel
-constexpr size_t kScratchBytes = kScratchPartials + sizeof(double) * 2 * kMaxPartials;
+// fixed-point residual: CTA count, then 4 words per CTA (up to 2047 CTAs)
+constexpr size_t kScratchResidFx = kScratchPartials + sizeof(double) * 2 * kMaxPartials;
+constexpr int kMaxResidFxCtas = 2047;
+constexpr size_t kScratchBytes = kScratchResidFx + 32 * (kMaxResidFxCtas + 1);
 
 // Internal dtype code: biased 64-bit fixed-point iterate (never in the ABI).
 constexpr int kDtypeU64 = 100;
@@ -88,12 +93,23 @@ int sweep_variants_f32(int T, const SweepVariant** out);
 int sweep_variants_bf16(int T, const SweepVariant** out);
 // Red-black Gauss-Seidel configurations (T stages = T/2 sweeps per pass).
 int sweep_variants_rb(int policy, int T, const SweepVariant** out);
+// Fixed-point residual configurations (one pass of the sweep kernel).
+int sweep_variants_resid(const SweepVariant** out);
+
+#ifdef __CUDACC__
+// max|u| over the halo, max|f| and max|u| over the interior, as bit patterns
+// into maxbits[0..2] (jacobi.cu); maxbits must be zeroed first.
+__global__ void range_kernel(const double* __restrict__ u, const double* __restrict__ f, int64_t nx, int64_t ny,
+                             int64_t nz, int64_t usy, int64_t usz, int64_t fsy, int64_t fsz,
+                             unsigned long long* maxbits);
+#endif
 
 // Kernel launchers (jacobi.cu, residual.cu, advect.cu).
 int launch_jacobi(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,
                   double h, int64_t nsweeps, int spp, int flags, cudaStream_t st);
 int launch_average2d(stencil_ctx* ctx, const Grid& u, const Grid& ut, int64_t nsweeps, cudaStream_t st);
-constexpr int kMaxLinearTerms = 27;
+constexpr int kMaxLinearTerms = 64;
+constexpr int kMaxApplyRadius = 3;
 int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const int32_t* offsets,
                         const double* coeffs, int npoints, cudaStream_t st);
 int launch_redblack(stencil_ctx* ctx, const Grid& u, const Grid& ut, const Grid& f, const Grid* work,

@@ -32,6 +32,8 @@ struct SweepArgs {
   int64_t fsy, fsz;                       //   ... and its strides (host side: its tensor map)
   unsigned long long* gdst;               // resident fixed point: the stored source (work grid) ...
   int64_t gsy, gsz;                       //   ... and its strides
+  int write_r;                            // residual: store r
+  unsigned long long* rpart;              // residual: [CTA count, then 4 words per CTA] partial sums
 };
 
 __device__ __forceinline__ double bits_as_double(unsigned long long b) {
@@ -135,6 +137,7 @@ struct PolF64 {
   static constexpr bool kFixed = false;
   static constexpr bool kTrack = false;
   static constexpr bool kResident = false;
+  static constexpr bool kResidual = false;
   using Track = NoTrack<double>;
   struct K { double hh; };
   __device__ static __forceinline__ K make(const SweepArgs& a) { return K{a.hh}; }
@@ -159,6 +162,7 @@ struct PolF32 {
   static constexpr bool kFixed = false;
   static constexpr bool kTrack = false;
   static constexpr bool kResident = false;
+  static constexpr bool kResidual = false;
   using Track = NoTrack<float>;
   struct K { float hh; };
   __device__ static __forceinline__ K make(const SweepArgs& a) { return K{static_cast<float>(a.hh)}; }
@@ -184,6 +188,7 @@ struct PolBF16 {
   static constexpr bool kFixed = false;
   static constexpr bool kTrack = false;
   static constexpr bool kResident = false;
+  static constexpr bool kResidual = false;
   using Track = NoTrack<__nv_bfloat16>;
   struct K { float hh; };
   __device__ static __forceinline__ K make(const SweepArgs& a) { return K{static_cast<float>(a.hh)}; }
@@ -211,6 +216,7 @@ struct PolFixed {
   static constexpr bool kFixed = true;
   static constexpr bool kTrack = true;
   static constexpr bool kResident = false;
+  static constexpr bool kResidual = false;
   using K = FixedParams;
   struct Track {
     uint32_t m = 0;
@@ -254,6 +260,7 @@ struct PolResident {
   static constexpr bool kFixed = true;
   static constexpr bool kTrack = true;
   static constexpr bool kResident = true;
+  static constexpr bool kResidual = false;
   using K = FixedParams;
   struct Track {
     uint32_t mx = 0u, mn = 0xffffffffu;
@@ -290,6 +297,99 @@ struct PolResident {
   __device__ static __forceinline__ T out(C v, const K&) { return v; }
   __device__ static __forceinline__ C update(C xm, C xp, C ym, C yp, C zm, C zp, T g, const K&) {
     return fx_div6(xm + xp + ym + yp + zm + zp + g + 3ull);
+  }
+};
+
+// The residual r = f - (6u - sum of the six neighbours) / h^2 and its
+// squared norm (Section 4.1's operator; the residual decides convergence),
+// in 64-bit fixed point.  One scale S for the call: u -> U = K + round(u 2^S)
+// and h*h*f -> G = round(h*h*f 2^S) with 12 max|u| + h*h max|f| below
+// 2^(62 - S), so D = 6U - (sum of the six neighbours' U) = 6q - sum q is
+// exact (the bias K cancels) and R = G - D = round(h^2 r 2^S) up to the
+// conversions (at most 6.5 units of 2^-S: about 2^-55 of 12 max|u|, finer
+// than a binary64 evaluation of the same expression).  The squared norm of
+// R is summed exactly in 192-bit integers (so it is the same whatever the
+// order), that of f in binary64; r, when asked for, is R 2^-S / h^2.
+struct PolResid {
+  using T = double;
+  using C = uint64_t;
+  static constexpr int kElem = 8;
+  static constexpr bool kFixed = true;
+  static constexpr bool kTrack = false;
+  static constexpr bool kResident = false;
+  static constexpr bool kResidual = true;
+  struct K {
+    int S, Cu, Cg;
+    uint64_t H;
+    int bad;     // 1: input not finite, 2: beyond range
+    int write;   // store r
+    double rs;   // 2^-S / h^2
+  };
+  // exact sums: s = s2 2^128 + s1 2^64 + s0 of R^2, and ff of f^2
+  struct Track {
+    uint64_t s0 = 0, s1 = 0, s2 = 0;
+    double ff = 0.0;
+    __device__ __forceinline__ void add_sq(int64_t R) {
+      const uint64_t a = static_cast<uint64_t>(R < 0 ? -R : R);
+      const uint64_t lo = a * a, hi = __umul64hi(a, a);
+      s0 += lo;
+      const uint64_t c0 = s0 < lo;
+      const uint64_t t = s1 + hi;
+      const uint64_t c1 = t < hi;
+      s1 = t + c0;
+      s2 += c1 + (s1 < c0);
+    }
+    __device__ __forceinline__ void add(uint64_t R, double f) {
+      add_sq(static_cast<int64_t>(R));
+      ff = fma(f, f, ff);
+    }
+    // this + o (exactly for the integer part)
+    __device__ __forceinline__ void merge(uint64_t o0, uint64_t o1, uint64_t o2, double off) {
+      s0 += o0;
+      const uint64_t c0 = s0 < o0;
+      const uint64_t t = s1 + o1;
+      const uint64_t c1 = t < o1;
+      s1 = t + c0;
+      s2 += o2 + c1 + (s1 < c0);
+      ff += off;
+    }
+  };
+  __device__ static __forceinline__ K make(const SweepArgs& a) {
+    K k;
+    k.bad = 0;
+    k.write = a.write_r;
+    const double mh = bits_as_double(a.maxbits[0]), mf = bits_as_double(a.maxbits[1]),
+                 mu = bits_as_double(a.maxbits[2]);
+    int S = 0;
+    if (!(mh <= 1.0e300) || !(mf <= 1.0e300) || !(mu <= 1.0e300)) {
+      k.bad = (mh - mh == 0.0 && mf - mf == 0.0 && mu - mu == 0.0) ? 2 : 1;
+    } else {
+      // B = 12 max|u| + h^2 max|f|; S = 62 - ceil(log2 B)
+      const double B = 12.0 * fmax(mh, mu) + a.hh * mf;
+      int e = 0;
+      if (B > 0.0) frexp(B, &e);
+      S = 62 - e;
+      if (S > 1022) S = 1022;
+      if (S < -900) k.bad = 2;
+    }
+    FixedParams p;
+    fx_conv(p, S, a.hh);
+    k.S = S; k.Cu = p.Cu; k.Cg = p.Cg; k.H = p.H;
+    k.rs = ldexp(1.0, -S) / a.hh;
+    return k;
+  }
+  __device__ static __forceinline__ C in(T v, const K& k) { return fx_in(v, k.Cu); }
+  __device__ static __forceinline__ C in_halo(T v, const K& k) { return in(v, k); }
+  // R = G - (6 U_c - sum of the six neighbours' U), as a two's-complement word
+  __device__ static __forceinline__ C residual(C c, C xm, C xp, C ym, C yp, C zm, C zp, T f, const K& k) {
+    const uint64_t six = (c << 2) + (c << 1);
+    const uint64_t D = six - (xm + xp + ym + yp + zm + zp);
+    return static_cast<uint64_t>(fx_source(f, k.Cg, k.H)) - D;
+  }
+  __device__ static __forceinline__ C update(C, C, C, C, C, C, T, const K&) { return 0; }
+  __device__ static __forceinline__ T out(C v, const K& k) {
+    return k.bad ? __longlong_as_double(0x7ff8000000000000ll)
+                 : __ll2double_rn(static_cast<long long>(v)) * k.rs;
   }
 };
 

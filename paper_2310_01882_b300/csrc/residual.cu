@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "sweep_kernel.cuh"
 
 namespace stencil {
 
@@ -114,10 +115,72 @@ int launch_residual_with(double* partials, const Grid& u, const Grid& f, double 
   return check_cuda(cudaGetLastError(), "residual finish kernel");
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-point residual (PolResid, policies.cuh): the caller's u and f staged
+// by TMA through one pass of the sweep kernel, R = round(h^2 r 2^S) per
+// point, its squared norm summed exactly per CTA (192-bit integers), f's in
+// binary64; this one-thread kernel adds the CTA sums in CTA order.
+// ---------------------------------------------------------------------------
+__global__ void resid_fx_finish_kernel(const unsigned long long* __restrict__ rpart, SweepArgs a,
+                                       double* __restrict__ norms) {
+  const PolResid::K k = PolResid::make(a);
+  if (k.bad) {
+    atomicOr(a.status, k.bad == 1 ? kStatusNonFinite : kStatusRange);
+    norms[0] = norms[1] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const int n = static_cast<int>(rpart[0]);
+  PolResid::Track t;
+  for (int b = 0; b < n; ++b) {
+    const unsigned long long* p = rpart + 4 + 4 * b;
+    t.merge(p[0], p[1], p[2], __longlong_as_double(static_cast<long long>(p[3])));
+  }
+  // s = s2 2^128 + s1 2^64 + s0 (a few roundings), ||r|| = sqrt(s) 2^-S / h^2
+  const double s = fma(static_cast<double>(t.s2), 0x1p128, fma(static_cast<double>(t.s1), 0x1p64,
+                                                               static_cast<double>(t.s0)));
+  norms[0] = ldexp(sqrt(s), -k.S) / a.hh;
+  norms[1] = sqrt(t.ff);
+}
+
+namespace {
+
+bool tma_aligned(const Grid& g) {
+  return (reinterpret_cast<uintptr_t>(g.data) & 15) == 0 && ((g.sy * g.elem) & 15) == 0 &&
+         ((g.sz * g.elem) & 15) == 0 && g.nz + 2 < (1ll << 31) && g.sz * g.elem < (1ll << 40);
+}
+
+}  // namespace
+
 int launch_residual(stencil_ctx* ctx, const Grid& u, const Grid& f, double h, const Grid* r,
                     double* norms_dev, cudaStream_t st) {
-  return launch_residual_with(reinterpret_cast<double*>(ctx->scratch + kScratchPartials), u, f, h,
-                              r, norms_dev, st);
+  // Grids a TMA descriptor cannot address (unaligned rows) take the
+  // binary64 kernel, which evaluates the definition in its written order.
+  if (!tma_aligned(u) || !tma_aligned(f))
+    return launch_residual_with(reinterpret_cast<double*>(ctx->scratch + kScratchPartials), u, f, h,
+                                r, norms_dev, st);
+  unsigned long long* maxbits = reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchRange);
+  int rc = check_cuda(cudaMemsetAsync(maxbits, 0, 24, st), "residual range init");
+  if (rc) return rc;
+  const int64_t rows = (u.ny + 2) * (u.nz + 2);
+  const int blocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
+  range_kernel<<<blocks, dim3(32, 8), 0, st>>>(static_cast<const double*>(u.data),
+                                               static_cast<const double*>(f.data), u.nx, u.ny, u.nz, u.sy, u.sz,
+                                               f.sy, f.sz, maxbits);
+  rc = check_cuda(cudaGetLastError(), "residual range kernel");
+  if (rc) return rc;
+  SweepArgs a{};
+  a.hh = h * h;
+  a.maxbits = maxbits;
+  a.status = reinterpret_cast<uint32_t*>(ctx->scratch + kScratchStatus);
+  a.write_r = r != nullptr;
+  a.rpart = reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchResidFx);
+  const SweepVariant* vs;
+  const int nv = sweep_variants_resid(&vs);
+  const int c = (ctx->resid_choice >= 0 && ctx->resid_choice < nv) ? ctx->resid_choice : 0;
+  rc = vs[c].fn(ctx, u, r ? *r : u, f, a, st);  // without r nothing is written
+  if (rc) return rc;
+  resid_fx_finish_kernel<<<1, 1, 0, st>>>(a.rpart, a, norms_dev);
+  return check_cuda(cudaGetLastError(), "residual finish kernel");
 }
 
 // ---------------------------------------------------------------------------

@@ -35,4 +35,17 @@ int sweep_variants_f64(int policy, int T, const SweepVariant** out) {
   return 0;
 }
 
+// The fixed-point residual (PolResid) through the same kernel: one pass, the
+// first configuration the default.
+int sweep_variants_resid(const SweepVariant** out) {
+  static const SweepVariant r1[] = {
+      variant<PolResid, TbCfg<PolResid, 1, 4, 16, 5, 1>>(),
+      variant<PolResid, TbCfg<PolResid, 1, 2, 16, 5, 1>>(),
+      variant<PolResid, TbCfg<PolResid, 1, 4, 8, 5, 2>>(),
+      variant<PolResid, TbCfg<PolResid, 1, 8, 4, 4, 3>>(),
+  };
+  *out = r1;
+  return sizeof(r1) / sizeof(r1[0]);
+}
+
 }  // namespace stencil

@@ -105,6 +105,7 @@ template <class Pol>
 struct ItemView {
   Item t;
   int64_t nx, ny, nz, sy, sz;
+  int64_t osy, osz;  // strides of the output grid
   const CUtensorMap* tm_u;
   const CUtensorMap* tm_f;
   typename Pol::T* out;
@@ -119,6 +120,7 @@ struct SingleParams {
   CUtensorMap tm_f;
   CUtensorMap tm_f64;  // resident fixed point: the binary64 source (read by fpath passes)
   typename Pol::T* out;
+  int64_t osy, osz;    // strides of the output grid
   SweepGeom g;
   SweepArgs a;
 };
@@ -146,6 +148,41 @@ struct SrcGrid {
   __device__ __forceinline__ void fx_end(uint32_t key) const {
     if constexpr (Pol::kTrack) fx_track_commit(p->a, key);
   }
+  // Residual: this CTA's sums of R^2 (exact) and f^2, over its consumer
+  // warps in warp order, into partial slot blockIdx.x (block 0 also stores
+  // the CTA count).  Every consumer warp calls it.
+  __device__ __forceinline__ void resid_end(typename Pol::Track& trk, int warp, int nwarps) const {
+    if constexpr (Pol::kResidual) {
+      __shared__ unsigned long long wsum[4 * 32];
+      __syncwarp();
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a0 = __shfl_xor_sync(0xffffffffu, trk.s0, o);
+        const unsigned long long a1 = __shfl_xor_sync(0xffffffffu, trk.s1, o);
+        const unsigned long long a2 = __shfl_xor_sync(0xffffffffu, trk.s2, o);
+        const double af = __shfl_xor_sync(0xffffffffu, trk.ff, o);
+        trk.merge(a0, a1, a2, af);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        wsum[4 * warp] = trk.s0;
+        wsum[4 * warp + 1] = trk.s1;
+        wsum[4 * warp + 2] = trk.s2;
+        wsum[4 * warp + 3] = static_cast<unsigned long long>(__double_as_longlong(trk.ff));
+      }
+      named_barrier(1, 32 * nwarps);
+      if (threadIdx.x == 0) {
+        typename Pol::Track t;
+        for (int w = 0; w < nwarps; ++w)
+          t.merge(wsum[4 * w], wsum[4 * w + 1], wsum[4 * w + 2],
+                  __longlong_as_double(static_cast<long long>(wsum[4 * w + 3])));
+        unsigned long long* out = p->a.rpart + 4 + 4 * static_cast<int64_t>(blockIdx.x);
+        out[0] = t.s0;
+        out[1] = t.s1;
+        out[2] = t.s2;
+        out[3] = static_cast<unsigned long long>(__double_as_longlong(t.ff));
+        if (blockIdx.x == 0) p->a.rpart[0] = gridDim.x;
+      }
+    }
+  }
   // Resident fixed point, an fpath pass: store the source of cell (x, y, z).
   __device__ __forceinline__ void store_source(int64_t x, int64_t y, int64_t z, unsigned long long g) const {
     const SweepArgs& a = p->a;
@@ -154,6 +191,7 @@ struct SrcGrid {
   __device__ __forceinline__ bool view(int64_t item, ItemView<Pol>& v) const {
     v.t = decode_item(p->g, item);
     v.nx = p->g.nx; v.ny = p->g.ny; v.nz = p->g.nz; v.sy = p->g.sy; v.sz = p->g.sz;
+    v.osy = p->osy; v.osz = p->osz;
     v.tm_u = &p->tm_u;
     v.tm_f = f64src ? &p->tm_f64 : &p->tm_f;
     v.out = p->out;
@@ -269,19 +307,29 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
         if constexpr (RS) {
           if (k.fpath) fv = Pol::source_at(fv, k);
         }
-        v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2],
-                        st.W[t - 1][OLD][rr + 1], st.W[t - 1][NEW][rr + 1], fv, k);
+        if constexpr (Pol::kResidual) {
+          v = Pol::residual(c, xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2], st.W[t - 1][OLD][rr + 1],
+                            st.W[t - 1][NEW][rr + 1], fv, k);
+        } else {
+          v = Pol::update(xm, xp, st.W[t - 1][MID][rr], st.W[t - 1][MID][rr + 2],
+                          st.W[t - 1][OLD][rr + 1], st.W[t - 1][NEW][rr + 1], fv, k);
+        }
       }
       if (t < TT) {
         st.W[t][NEW][rr] = v;
       } else if (in && lane >= Cfg::XL && lane < 32 - Cfg::XL) {
-        T o = Pol::out(v, k);
-        if constexpr (RS) {
-          if (k.dshift) o = Pol::rescale(o, k);
-          if (k.fpath) src.store_source(x, y0 + rr, q, fv);
+        if constexpr (Pol::kResidual) {
+          trk.add(v, fv);
+          if (k.write) orow0[static_cast<int64_t>(q) * sz + rr * sy] = Pol::out(v, k);
+        } else {
+          T o = Pol::out(v, k);
+          if constexpr (RS) {
+            if (k.dshift) o = Pol::rescale(o, k);
+            if (k.fpath) src.store_source(x, y0 + rr, q, fv);
+          }
+          orow0[static_cast<int64_t>(q) * sz + rr * sy] = o;
+          trk.add(o);
         }
-        orow0[static_cast<int64_t>(q) * sz + rr * sy] = o;
-        trk.add(o);
       }
     }
   }
@@ -315,7 +363,7 @@ __device__ __forceinline__ bool tb_consume(const Src& src, const unsigned char* 
       const int64_t y = t.yo + row0 + w;
       ymask |= (y >= 1 && y <= v.ny) ? (1u << (w + TT)) : 0u;
     }
-    typename Pol::T* orow0 = v.out + x + (t.yo + row0) * v.sy;
+    typename Pol::T* orow0 = v.out + x + (t.yo + row0) * v.osy;
     const int steps = (t.ze - t.zs + 1) + 2 * TT;
     const uint32_t seq0 = it;
     int j = 0;
@@ -338,7 +386,7 @@ __device__ __forceinline__ bool tb_consume(const Src& src, const unsigned char* 
     const int slot = wait(j);                                                                      \
     if (slot < 0) return false;                                                                    \
     tb_step<Pol, Cfg, Src, ROT, RS>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane,   \
-                                    off, xin, ymask, edge_halo, any_edge_halo, orow0, v.sy, v.sz,  \
+                                    off, xin, ymask, edge_halo, any_edge_halo, orow0, v.osy, v.osz,\
                                     static_cast<int>(v.nz), src, x, t.yo + row0, trk);             \
     if (j >= TT) release(seq0 + j - TT);                                                           \
     if (++j >= steps) break;                                                                       \
@@ -398,7 +446,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
   } else {
     ok = tb_consume<Pol, Cfg, Src, false>(src, ring, bar_full, bar_empty, &abort_flag, warp, lane, trk);
   }
-  if (ok) src.fx_end(trk.key());
+  if constexpr (Pol::kResidual) {
+    src.resid_end(trk, warp, WY);  // every consumer warp takes part (a failed wait is in the status)
+  } else {
+    if (ok) src.fx_end(trk.key());
+  }
 }
 
 }  // namespace stencil

@@ -77,8 +77,11 @@ int run_tb(stencil_ctx* ctx, const Grid& in, const Grid& out, const Grid& f, con
   const int zc = pick_zc(txy, in.nz, per_sm * ctx->num_sms, Cfg::T);
   prm.g = make_geom<Cfg>(in, zc);
   prm.out = static_cast<typename Pol::T*>(out.data);
+  prm.osy = out.sy;
+  prm.osz = out.sz;
   prm.a = a;
   grid = static_cast<int>(std::min<int64_t>(prm.g.items, static_cast<int64_t>(per_sm) * ctx->num_sms));
+  if constexpr (Pol::kResidual) grid = std::min(grid, kMaxResidFxCtas);  // one partial-sum slot per CTA
   kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(prm);
   return check_cuda(cudaGetLastError(), "jacobi_tb launch");
 }

@@ -182,7 +182,7 @@ __device__ __forceinline__ bool rb_consume(const Src& src, const unsigned char* 
       const int64_t y = t.yo + row0 + w;
       ymask |= (y >= 1 && y <= v.ny) ? (1u << (w + TT)) : 0u;
     }
-    typename Pol::T* orow0 = v.out + x + (t.yo + row0) * v.sy;
+    typename Pol::T* orow0 = v.out + x + (t.yo + row0) * v.osy;
     const int pb = static_cast<int>((t.xo - TT + t.yo + row0) & 1);
     const int steps = (t.ze - t.zs + 1) + 2 * TT;
     const uint32_t seq0 = it;
@@ -206,7 +206,7 @@ __device__ __forceinline__ bool rb_consume(const Src& src, const unsigned char* 
     const int slot = wait(j);                                                                        \
     if (slot < 0) return false;                                                                      \
     rb_step<Pol, Cfg, Src, ROT, RS>(st, v.k, ring, slot, seq0 + j, j, t.zs - TT + j, row0, lane, off,  \
-                                    xin0, xin1, ymask, pb, orow0, v.sy, v.sz, static_cast<int>(v.nz),  \
+                                    xin0, xin1, ymask, pb, orow0, v.osy, v.osz, static_cast<int>(v.nz),\
                                     src, x, t.yo + row0, trk);                                         \
     if (j >= TT) release(seq0 + j - TT);                                                             \
     if (++j >= steps) break;                                                                         \

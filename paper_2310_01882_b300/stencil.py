@@ -84,6 +84,8 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "stencil_redblack_config_select": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32], ctypes.c_int),
+    "stencil_residual_config_count": ([ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "stencil_residual_config_select": ([_P, ctypes.c_int32], ctypes.c_int),
     "wsnet_create": ([ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "wsnet_destroy": ([_P], ctypes.c_int),
@@ -224,8 +226,9 @@ def stencil_jacobi_sweep(ctx, u, u_tmp, f, work, h, nsweeps, sweeps_per_pass=0, 
 
 
 def stencil_apply_linear(ctx, inp, out, offsets, coeffs, stream=None):
-    """out = sum_p coeffs[p] * inp(. + offsets[p]) on the interior (offsets:
-    (npoints, 3) ints in -1..1; F64 Fields)."""
+    """out = sum_p coeffs[p] * inp(. + offsets[p]) on the interior points whose
+    reads lie in the field (offsets: (npoints, 3) ints in -3..3; F64 Fields;
+    see include/stencil.h)."""
     off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64).reshape(-1))
     gi, go = inp.grid(), out.grid()
@@ -285,6 +288,16 @@ def stencil_redblack_config_count(dtype, flags, with_work, sweeps_per_pass):
 def stencil_redblack_config_select(ctx, dtype, flags, with_work, sweeps_per_pass, index):
     return _check(lib().stencil_redblack_config_select(ctx.handle, int(dtype), int(flags), int(bool(with_work)),
                                                        int(sweeps_per_pass), int(index)))
+
+
+def stencil_residual_config_count():
+    c = ctypes.c_int32()
+    _check(lib().stencil_residual_config_count(ctypes.byref(c)))
+    return c.value
+
+
+def stencil_residual_config_select(ctx, index):
+    return _check(lib().stencil_residual_config_select(ctx.handle, int(index)))
 
 
 def stencil_residual(ctx, u, f, h, norms_dev, r=None, stream=None):

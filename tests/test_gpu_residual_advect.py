@@ -24,17 +24,80 @@ def gpu_residual(u, f, h, want_r=True):
     return n[0], n[1], (rf.to_numpy() if want_r else None)
 
 
+def r_tol(u, f, h):
+    """Bound on |r_gpu - r_oracle| per point.  Both are within a few
+    rounding units of the exact f - A u: the library's fixed-point
+    evaluation within 6.5 units of 2^-S <= 2^-61 (12 max|u| + h^2 max|f|),
+    divided by h^2 (plus the final rounding); the oracle's binary64
+    evaluation in the written order within about 16 eps (12 max|u| / h^2 +
+    max|f|).  1e-14 of that scale covers both."""
+    return 1e-14 * (12.0 * np.max(np.abs(u)) / (h * h) + np.max(np.abs(f[1:-1, 1:-1, 1:-1])))
+
+
+def check_residual(u, f, h):
+    nr, nf, r = oracle.residual(u, f, h, want_r=True, nthreads=0)
+    gr, gf, rg = gpu_residual(u, f, h)
+    tol = r_tol(u, f, h)
+    d = np.max(np.abs(rg[1:-1, 1:-1, 1:-1] - r[1:-1, 1:-1, 1:-1]))
+    assert d <= tol, (d, tol)
+    npts = r[1:-1, 1:-1, 1:-1].size
+    assert abs(gr - nr) <= np.sqrt(npts) * tol + 1e-12 * nr, (gr, nr)
+    assert abs(gf - nf) <= 1e-13 * nf
+    gr2, _, _ = gpu_residual(u, f, h, want_r=False)
+    assert gr2 == gr          # the same norm with or without r written
+    return r, rg
+
+
 @pytest.mark.parametrize("shape", SHAPES)
-def test_residual_bitwise_per_point(shape):
+def test_residual_per_point(shape):
     nx, ny, nz = shape
     rng = np.random.default_rng(sum(shape))
     u = rng.random((nz + 2, ny + 2, nx + 2))
     f = rng.standard_normal((nz + 2, ny + 2, nx + 2))
+    check_residual(u, f, 1.0 / (max(shape) + 1))
+
+
+@pytest.mark.parametrize("shape", [(64, 64, 64), (67, 35, 19)])
+def test_residual_near_convergence(shape):
+    """u within 1e-9 of the discrete solution: r is a small difference of
+    large terms, and both evaluations agree to their rounding bound."""
+    nx, ny, nz = shape
+    f = inputs.grf(nx, seed=5, ny=ny, nz=nz)
     h = 1.0 / (max(shape) + 1)
+    ud = exact.solve(f, h)
+    rng = np.random.default_rng(6)
+    ud[1:-1, 1:-1, 1:-1] += 1e-9 * np.max(np.abs(ud)) * rng.standard_normal((nz, ny, nx))
+    check_residual(ud, f, h)
+
+
+def test_residual_unaligned_grid_is_bitwise():
+    """A grid whose rows a TMA descriptor cannot address (odd row length in
+    elements) takes the binary64 kernel: r bitwise the oracle's."""
+    import torch
+    nx, ny, nz = 13, 7, 5
+    rng = np.random.default_rng(9)
+    u = rng.random((nz + 2, ny + 2, nx + 2))
+    f = rng.standard_normal(u.shape)
+    h = 1.0 / 14
+    sy = nx + 2                      # 15 doubles: rows not 16-byte aligned
+    sz = sy * (ny + 2)
+
+    def raw(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        return t, S.stencil_grid(t.data_ptr(), nx, ny, nz, sy, sz, S.F64, 0)
+
+    tu, gu = raw(u)
+    tf, gf = raw(f)
+    tr, gr = raw(np.zeros_like(u))
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    import ctypes
+    rc = S.lib().stencil_residual(ctx().handle, ctypes.byref(gu), ctypes.byref(gf), h, ctypes.byref(gr),
+                                  ctypes.c_void_p(norms.data_ptr()), None)
+    assert rc == 0
+    torch.cuda.synchronize()
     nr, nf, r = oracle.residual(u, f, h, want_r=True)
-    gr, gf, rg = gpu_residual(u, f, h)
-    assert np.array_equal(rg[1:-1, 1:-1, 1:-1], r[1:-1, 1:-1, 1:-1])
-    assert abs(gr - nr) <= 1e-13 * nr and abs(gf - nf) <= 1e-13 * nf
+    assert np.array_equal(tr.cpu().numpy()[1:-1, 1:-1, 1:-1], r[1:-1, 1:-1, 1:-1])
+    assert abs(norms[0].item() - nr) <= 1e-13 * nr
 
 
 def test_residual_deterministic_and_exact_solution():
