@@ -169,14 +169,26 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
  * stencil.apply reads its input at constant offsets and yields one value
  * per point of the output's bounds; here the body is a linear combination):
  *   out(x, y, z) = sum_{p < npoints} coeffs[p] * in(x + dx_p, y + dy_p, z + dz_p)
- * on the interior; each product is rounded, then added in the listed order
- * (binary64, no fused multiply-add), so the result is bitwise that order's.
- *   in, out   F64 grids of equal extents, distinct (out of place); out's
- *             halo is not written.
- *   offsets   HOST array of 3 * npoints int32 (dx, dy, dz), each in -1..1
- *             (the one-cell halo); coeffs: HOST array of npoints doubles;
- *             1 <= npoints <= 27.  Both are copied into the launch.
- * Asynchronous on `stream`; STENCIL_ERR_ARG / _DTYPE on bad arguments.
+ * on the output's bounds: the interior points whose reads all lie in the
+ * field, halo included -- with r = max |offset|, indices r .. n + 1 - r
+ * per axis (the whole interior when every offset is within one cell).
+ * Nothing else of out is written.
+ *   Coefficients that are all integer multiples of one power of two,
+ *   coeffs[p] = k_p 2^E with |k_p| <= 2^20 (integer-weight stencils such as
+ *   Laplacians, or averages with weight 1/4): computed in 64-bit fixed
+ *   point, the input converted at one scale 2^-S per call (S from max|in|
+ *   and sum |k_p|), sum k_p q_p exact and rounded to binary64 once, so the
+ *   result is within 2^-61 sum|coeffs| max|in| of the exact sum (exactly it
+ *   for inputs on the 2^-S grid, e.g. integer-valued ones).  Any other
+ *   coefficients: each product rounded, then added in the listed order
+ *   (binary64, no fused multiply-add): bitwise that order's result.
+ *   in, out   F64 grids of equal extents, distinct (out of place).
+ *   offsets   HOST array of 3 * npoints int32 (dx, dy, dz), each in -3..3;
+ *             coeffs: HOST array of npoints doubles; 1 <= npoints <= 64.
+ *             Both are copied into the launch.
+ * Asynchronous on `stream`; STENCIL_ERR_ARG / _DTYPE on bad arguments; a
+ * non-finite input to the fixed-point form gives NaN and the ctx status
+ * reports STENCIL_ERR_NONFINITE.
  */
 STENCIL_API int stencil_apply_linear(stencil_ctx* ctx, const stencil_grid* in, const stencil_grid* out,
                                      const int32_t* offsets, const double* coeffs, int32_t npoints,
@@ -267,10 +279,30 @@ STENCIL_API int stencil_redblack_config_select(stencil_ctx* ctx, int32_t dtype,
                                                int32_t index);
 
 /*
+ * The same for stencil_residual's fixed-point evaluation: the number of
+ * compiled tile configurations, and the one ctx uses (index 0 unless
+ * selected).  Errors: STENCIL_ERR_ARG (null count or ctx, index out of
+ * range).
+ */
+STENCIL_API int stencil_residual_config_count(int32_t* count);
+STENCIL_API int stencil_residual_config_select(stencil_ctx* ctx, int32_t index);
+
+/*
  * stencil_residual -- the residual of A u = f for the 7-point operator
  *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2,
  *     r = f - A u on the interior,
- * always in binary64 (it decides convergence of the iterative solve).
+ * to binary64 accuracy or better (it decides convergence of the iterative
+ * solve).  Grids whose data and row strides are 16-byte aligned (what a TMA
+ * descriptor needs) are evaluated in 64-bit fixed point: u and h^2 f at one
+ * scale 2^-S per call with 12 max|u| + h^2 max|f| < 2^(62-S), so 6u minus
+ * the six neighbours is exact and each r is within 6.5 2^-S / h^2 of the
+ * exact f - A u (finer than a binary64 evaluation of the same expression,
+ * whose rounding is up to about 16 eps (12 max|u| / h^2 + max|f|)); r is
+ * rounded to binary64 once it is formed.  ||r||^2 is summed exactly (192-bit
+ * integers), so the norm does not depend on the summation order.  Other
+ * grids take a binary64 evaluation in the written order (bitwise the plain
+ * definition).  Non-finite input: norms and r are NaN and the ctx status
+ * reports STENCIL_ERR_NONFINITE.
  *   u, f      F64 grids of equal extents (u's halo is the boundary).
  *   r         NULL, or an F64 grid of the same extents, distinct from u and
  *             f (STENCIL_ERR_ARG if it is either): its interior receives r
@@ -448,9 +480,10 @@ STENCIL_API int wsnet_loss_grad(wsnet* net, const float* x, const float* t,
  *   Limit:   ny * nz <= 524288 (one partial sum per 64 rows, 8192 sums);
  *            larger grids are rejected with STENCIL_ERR_ARG before any
  *            launch (use stencil_residual with a context for them).
- *   r values are bitwise those of stencil_residual; the norms use a
- *   different (fixed) partition of the sum, so they agree to rounding and
- *   are reproducible run to run.
+ *   r is evaluated in binary64 in the written order (bitwise the plain
+ *   definition), so it agrees with stencil_residual's to both evaluations'
+ *   rounding; the norms use a fixed partition of the sum and are
+ *   reproducible run to run.
  *   The first call in each CUDA context on a device looks up the array's
  *   device address (with that device current; again after the context is
  *   replaced, e.g. by cudaDeviceReset); make that first call before any

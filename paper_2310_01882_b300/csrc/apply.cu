@@ -1,0 +1,278 @@
+// apply.cu -- the general linear stencil apply (Section 2.2: a stencil.apply
+// reads its input at constant offsets and yields one value per point of the
+// output's bounds; here the body is a linear combination):
+//   out(x) = sum_p c_p in(x + d_p),   |d_p| <= 3 per axis,
+// over the interior points whose reads all lie in the field (halo
+// included): with r = max |d|, indices r .. n + 1 - r per axis (the whole
+// interior when the offsets stay in the one-cell halo).
+//
+// Two evaluations:
+//  * coefficients that are integer multiples of one power of two, c_p =
+//    k_p 2^E with |k_p| <= 2^20 (integer-weight stencils: Laplacians,
+//    averages, finite differences with their denominators folded out):
+//    64-bit fixed point.  The input is converted at one scale 2^-S per call
+//    (S from max|in| and sum |k_p|, so no sum can overflow), sum k_p q_p is
+//    exact and rounded to binary64 once, times 2^E.  A z-marching kernel:
+//    each CTA owns a 32 x 8 column of outputs and keeps the 2R + 1 input
+//    planes the offsets reach, with their x/y margins, in shared memory as
+//    fixed-point integers; every loaded plane is written to two slots of a
+//    doubled ring, so the planes z - R .. z + R always sit in consecutive
+//    slots and each term's shared-memory offset is one constant, whatever
+//    the offsets are.  Each input value is read from HBM and converted once.
+//  * any other coefficients: binary64, each product rounded then added in
+//    the listed order (no fused multiply-add): bitwise the definition; one
+//    thread per point, neighbours through L1 (bound by the FP64 pipe).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "fixed.cuh"
+#include "internal.h"
+
+namespace stencil {
+
+namespace {
+
+constexpr int kApBX = 32, kApBY = 8;
+
+struct LinearTerms {
+  int64_t off[kMaxLinearTerms];  // element offsets dx + dy sy + dz sz
+  double c[kMaxLinearTerms];
+  int n, r;
+};
+
+__global__ void __launch_bounds__(256)
+    apply_linear_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
+                        int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ LinearTerms t) {
+  const int64_t i = t.r + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t j = t.r + blockIdx.y * int64_t(blockDim.y) + threadIdx.y;
+  if (i > nx + 1 - t.r || j > ny + 1 - t.r) return;
+  for (int64_t k = t.r + blockIdx.z; k <= nz + 1 - t.r; k += gridDim.z) {
+    const int64_t c = i + j * sy + k * sz;
+    double acc = 0.0;
+    for (int p = 0; p < t.n; ++p) acc = __dadd_rn(acc, __dmul_rn(t.c[p], in[c + t.off[p]]));
+    out[i + j * osy + k * osz] = acc;
+  }
+}
+
+// Terms of the fixed-point form: the shared-memory offset of each term
+// (from the window's first slot), its integer weight, the power of two E.
+struct FxTerms {
+  int soff[kMaxLinearTerms];
+  int k[kMaxLinearTerms];
+  int n, r, E;
+  double sumk;  // sum |k_p|
+};
+
+// max|in| over the field (halo included), as bits into *maxbits (zeroed first).
+__global__ void apply_range_kernel(const double* __restrict__ in, int64_t nx, int64_t ny, int64_t nz, int64_t sy,
+                                   int64_t sz, unsigned long long* maxbits) {
+  const int64_t rows = (ny + 2) * (nz + 2);
+  unsigned long long m = 0;
+  for (int64_t row = blockIdx.x * int64_t(blockDim.y) + threadIdx.y; row < rows;
+       row += int64_t(gridDim.x) * blockDim.y) {
+    const int64_t k = row / (ny + 2), j = row - k * (ny + 2);
+    for (int64_t i = threadIdx.x; i < nx + 2; i += blockDim.x) {
+      const unsigned long long b =
+          static_cast<unsigned long long>(__double_as_longlong(in[i + j * sy + k * sz])) & 0x7fffffffffffffffull;
+      m = b > m ? b : m;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, m, o);
+    m = a > m ? a : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, m);
+}
+
+// round(x 2^S) as a signed integer, halves away from zero, for |x| 2^S < 2^62
+// (Cu = 1085 - S; zeros and subnormals give 0).
+__device__ __forceinline__ int64_t fx_quant_signed(double x, int Cu) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  const uint64_t m63 = (b << 11) | 0x8000000000000000ull;
+  const uint64_t t = shr64(m63, static_cast<unsigned>(Cu - e));  // floor(2 |x| 2^S)
+  return static_cast<int64_t>((t ^ fx_sign_mask(b)) + 1) >> 1;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kApBX * kApBY)
+    apply_fx_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
+                    int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ FxTerms t,
+                    const unsigned long long* __restrict__ maxbits, uint32_t* status, int zchunk) {
+  constexpr int WX = kApBX + 2 * R, WY = kApBY + 2 * R, PL = WX * WY, NP = 2 * R + 1;
+  extern __shared__ long long ap_win[];  // 2 NP slots of PL values
+  // scale: sum |k_p| max|in| 2^S <= 2^61, so every partial sum stays below 2^62
+  const double mx = __longlong_as_double(static_cast<long long>(maxbits[0]));
+  int bad = 0;
+  int S = 0;
+  if (!(mx <= 1.0e300)) {
+    bad = 1;
+  } else {
+    int e = 0;
+    if (mx > 0.0) frexp(mx * t.sumk, &e);
+    S = 61 - e;
+    if (S > 1022) S = 1022;
+    if (S < -900) bad = 2;
+  }
+  if (bad) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+      atomicOr(status, bad == 1 ? kStatusNonFinite : kStatusRange);
+  }
+  const int Cu = 1085 - S;
+  const int sh = t.E - S;  // out = sum 2^sh
+  const bool exp_ok = sh >= -1022 && sh <= 960;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kApBX + tx;
+  const int64_t ox = t.r + static_cast<int64_t>(blockIdx.x) * kApBX;  // first output column of the tile
+  const int64_t oy = t.r + static_cast<int64_t>(blockIdx.y) * kApBY;
+  const int64_t zs = t.r + static_cast<int64_t>(blockIdx.z) * zchunk;
+  const int64_t ze = std::min<int64_t>(zs + zchunk - 1, nz + 1 - t.r);
+  const int64_t i = ox + tx, j = oy + ty;
+  const bool owner = i <= nx + 1 - t.r && j <= ny + 1 - t.r;
+  for (int64_t p = zs - R; p <= ze + R; ++p) {
+    // plane p into ring slots s and s + NP (so planes z - R .. z + R are
+    // consecutive from slot (z - R) mod NP)
+    const int s = static_cast<int>(((p % NP) + NP) % NP);
+    long long* w0 = ap_win + s * PL;
+    long long* w1 = ap_win + (s + NP) * PL;
+    for (int c = tid; c < PL; c += kApBX * kApBY) {
+      const int cy = c / WX, cx = c - cy * WX;
+      const int64_t gi = ox - R + cx, gj = oy - R + cy;
+      long long q = 0;
+      if (p >= 0 && p <= nz + 1 && gi >= 0 && gi <= nx + 1 && gj >= 0 && gj <= ny + 1)
+        q = fx_quant_signed(in[gi + gj * sy + p * sz], Cu);
+      w0[c] = q;
+      w1[c] = q;
+    }
+    __syncthreads();
+    const int64_t z = p - R;
+    if (z >= zs && owner) {
+      const int base = static_cast<int>(((z - R) % NP + NP) % NP) * PL + ty * WX + tx;
+      long long acc = 0;
+      for (int q = 0; q < t.n; ++q) acc += static_cast<long long>(t.k[q]) * ap_win[base + t.soff[q]];
+      double v;
+      if (bad) {
+        v = __longlong_as_double(0x7ff8000000000000ll);
+      } else if (acc == 0) {
+        v = 0.0;
+      } else {
+        const double d = __ll2double_rn(acc);
+        v = exp_ok ? __longlong_as_double(__double_as_longlong(d) + (static_cast<long long>(sh) << 52))
+                   : ldexp(d, sh);
+      }
+      out[i + j * osy + z * osz] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// c = k 2^e with k an odd integer (c != 0): the exact decomposition.
+void odd_power(double c, long long* k, int* e) {
+  int ex = 0;
+  const double m = std::frexp(std::fabs(c), &ex);          // |c| = m 2^ex, m in [0.5, 1)
+  long long M = static_cast<long long>(std::ldexp(m, 53));  // exact: 53-bit integer
+  int tz = 0;
+  while ((M & 1) == 0) {
+    M >>= 1;
+    ++tz;
+  }
+  *k = c < 0 ? -M : M;
+  *e = ex - 53 + tz;
+}
+
+}  // namespace
+
+int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const int32_t* offsets,
+                        const double* coeffs, int npoints, cudaStream_t st) {
+  int r = 1;
+  for (int p = 0; p < 3 * npoints; ++p) r = std::max(r, std::abs(offsets[p]));
+  // nothing to write when the bounds are empty
+  if (in.nx + 2 - 2 * r < 1 || in.ny + 2 - 2 * r < 1 || in.nz + 2 - 2 * r < 1) return STENCIL_OK;
+  // integer multiples of one power of two?
+  bool fx = true;
+  int E = 1 << 20;
+  std::vector<long long> k0(npoints, 0);
+  std::vector<int> e0(npoints, 0);
+  for (int p = 0; p < npoints && fx; ++p) {
+    if (!std::isfinite(coeffs[p])) fx = false;
+    else if (coeffs[p] != 0.0) {
+      odd_power(coeffs[p], &k0[p], &e0[p]);
+      if (k0[p] > (1ll << 20) || k0[p] < -(1ll << 20)) fx = false;
+      E = std::min(E, e0[p]);
+    }
+  }
+  if (fx && E != (1 << 20)) {
+    FxTerms t{};
+    double sumk = 0.0;
+    int n = 0;
+    const int R = r;  // the window radius is the offsets' radius
+    const int WX = kApBX + 2 * R, WY = kApBY + 2 * R, PL = WX * WY;
+    for (int p = 0; p < npoints; ++p) {
+      if (coeffs[p] == 0.0) continue;
+      const int shift = e0[p] - E;
+      if (shift > 20 || std::llabs(k0[p]) > ((1ll << 20) >> shift)) {  // |k_p| 2^shift > 2^20
+        fx = false;
+        break;
+      }
+      t.k[n] = static_cast<int>(k0[p] << shift);
+      sumk += std::fabs(static_cast<double>(t.k[n]));
+      const int dx = offsets[3 * p], dy = offsets[3 * p + 1], dz = offsets[3 * p + 2];
+      t.soff[n] = (R + dz) * PL + (R + dy) * WX + (R + dx);
+      ++n;
+    }
+    if (fx) {
+      t.n = n;
+      t.r = r;
+      t.E = E;
+      t.sumk = sumk > 0.0 ? sumk : 1.0;
+      unsigned long long* mb = reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchApplyRange);
+      int rc = check_cuda(cudaMemsetAsync(mb, 0, 8, st), "apply range init");
+      if (rc) return rc;
+      const int64_t rows = (in.ny + 2) * (in.nz + 2);
+      const int rblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
+      apply_range_kernel<<<rblocks, dim3(32, 8), 0, st>>>(static_cast<const double*>(in.data), in.nx, in.ny, in.nz,
+                                                           in.sy, in.sz, mb);
+      rc = check_cuda(cudaGetLastError(), "apply range kernel");
+      if (rc) return rc;
+      const int64_t ox = in.nx + 2 - 2 * r, oy = in.ny + 2 - 2 * r, oz = in.nz + 2 - 2 * r;  // output extents
+      const int64_t tiles = ((ox + kApBX - 1) / kApBX) * ((oy + kApBY - 1) / kApBY);
+      // z chunks: about 8 CTAs per SM in total, each chunk at least 8 planes
+      int64_t zc = std::max<int64_t>(8, (oz * tiles + 8 * ctx->num_sms - 1) / (8 * ctx->num_sms));
+      zc = std::min<int64_t>(zc, oz);
+      const dim3 grid(static_cast<unsigned>((ox + kApBX - 1) / kApBX), static_cast<unsigned>((oy + kApBY - 1) / kApBY),
+                      static_cast<unsigned>((oz + zc - 1) / zc));
+      if (grid.y > 65535 || grid.z > 65535) return set_error(STENCIL_ERR_ARG, "apply_linear: grid too large");
+      const int smem = 2 * (2 * R + 1) * PL * static_cast<int>(sizeof(long long));
+      auto kern = R == 1 ? apply_fx_kernel<1> : (R == 2 ? apply_fx_kernel<2> : apply_fx_kernel<3>);
+      rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                      "apply smem attribute");
+      if (rc) return rc;
+      kern<<<grid, dim3(kApBX, kApBY), smem, st>>>(
+          static_cast<const double*>(in.data), static_cast<double*>(out.data), in.nx, in.ny, in.nz, in.sy, in.sz,
+          out.sy, out.sz, t, mb, reinterpret_cast<uint32_t*>(ctx->scratch + kScratchStatus), static_cast<int>(zc));
+      return check_cuda(cudaGetLastError(), "apply_linear fixed-point kernel");
+    }
+  }
+  LinearTerms t;
+  t.n = npoints;
+  t.r = r;
+  for (int p = 0; p < npoints; ++p) {
+    t.off[p] = offsets[3 * p] + offsets[3 * p + 1] * in.sy + offsets[3 * p + 2] * in.sz;
+    t.c[p] = coeffs[p];
+  }
+  for (int p = npoints; p < kMaxLinearTerms; ++p) {
+    t.off[p] = 0;
+    t.c[p] = 0.0;
+  }
+  const int64_t ox = in.nx + 2 - 2 * r, oy = in.ny + 2 - 2 * r, oz = in.nz + 2 - 2 * r;
+  const dim3 block(32, 8);
+  const dim3 grid(static_cast<unsigned>((ox + 31) / 32), static_cast<unsigned>((oy + 7) / 8),
+                  static_cast<unsigned>(std::min<int64_t>(oz, 65535)));
+  if (grid.y > 65535) return set_error(STENCIL_ERR_ARG, "apply_linear: ny too large");
+  apply_linear_kernel<<<grid, block, 0, st>>>(static_cast<const double*>(in.data), static_cast<double*>(out.data),
+                                              in.nx, in.ny, in.nz, in.sy, in.sz, out.sy, out.sz, t);
+  return check_cuda(cudaGetLastError(), "apply_linear kernel");
+}
+
+}  // namespace stencil

@@ -356,55 +356,6 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-namespace {
-
-// A general linear stencil apply: out = sum_p c_p in(. + d_p) over the
-// interior, each product rounded then added in the listed order (binary64,
-// no fused multiply-add), the terms passed by value.
-struct LinearTerms {
-  int64_t off[kMaxLinearTerms];  // element offsets dx + dy sy + dz sz
-  double c[kMaxLinearTerms];
-  int n;
-};
-
-__global__ void __launch_bounds__(256)
-    apply_linear_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
-                        int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ LinearTerms t) {
-  const int64_t i = 1 + blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  const int64_t j = 1 + blockIdx.y * int64_t(blockDim.y) + threadIdx.y;
-  if (i > nx || j > ny) return;
-  for (int64_t k = 1 + blockIdx.z; k <= nz; k += gridDim.z) {
-    const int64_t c = i + j * sy + k * sz;
-    double acc = 0.0;
-    for (int p = 0; p < t.n; ++p) acc = __dadd_rn(acc, __dmul_rn(t.c[p], in[c + t.off[p]]));
-    out[i + j * osy + k * osz] = acc;
-  }
-}
-
-}  // namespace
-
-int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const int32_t* offsets,
-                        const double* coeffs, int npoints, cudaStream_t st) {
-  (void)ctx;
-  LinearTerms t;
-  t.n = npoints;
-  for (int p = 0; p < npoints; ++p) {
-    t.off[p] = offsets[3 * p] + offsets[3 * p + 1] * in.sy + offsets[3 * p + 2] * in.sz;
-    t.c[p] = coeffs[p];
-  }
-  for (int p = npoints; p < kMaxLinearTerms; ++p) {
-    t.off[p] = 0;
-    t.c[p] = 0.0;
-  }
-  const dim3 block(32, 8);
-  const dim3 grid(static_cast<unsigned>((in.nx + 31) / 32), static_cast<unsigned>((in.ny + 7) / 8),
-                  static_cast<unsigned>(std::min<int64_t>(in.nz, 65535)));
-  if (grid.y > 65535) return set_error(STENCIL_ERR_ARG, "apply_linear: ny too large");
-  apply_linear_kernel<<<grid, block, 0, st>>>(static_cast<const double*>(in.data), static_cast<double*>(out.data),
-                                              in.nx, in.ny, in.nz, in.sy, in.sz, out.sy, out.sz, t);
-  return check_cuda(cudaGetLastError(), "apply_linear kernel");
-}
-
 int launch_average2d(stencil_ctx* ctx, const Grid& u, const Grid& ut, int64_t nsweeps, cudaStream_t st) {
   (void)ctx;
   if (nsweeps == 0) return STENCIL_OK;

@@ -1,6 +1,9 @@
-"""GPU parity of stencil_apply_linear (a general linear stencil.apply):
-bitwise equal to the oracle for random offset sets and coefficients, the
-out halo untouched."""
+"""GPU parity of stencil_apply_linear (a general linear stencil.apply, offsets
+up to three cells): with general coefficients (binary64 in the written
+order) bitwise equal to the oracle, the rest of out untouched; with
+integer-weight coefficients (the fixed-point path) exact -- bitwise equal to
+the oracle on integer-valued inputs, where both are exact -- and within the
+oracle's own rounding bound otherwise."""
 import numpy as np
 import pytest
 
@@ -32,11 +35,92 @@ def test_bitwise(shape, npoints):
     assert np.array_equal(got, ref)
 
 
+def run(u, offs, coef, out0):
+    import torch
+    a, b = S.Field.from_numpy(u), S.Field.from_numpy(out0)
+    S.stencil_apply_linear(ctx(), a, b, offs, coef)
+    torch.cuda.synchronize()
+    S.stencil_ctx_status(ctx())
+    return b.to_numpy()
+
+
+def star(radius, weights):
+    """Offsets and coefficients of a star stencil: weights[d] at distance d
+    along each axis (weights[0] at the centre once)."""
+    offs, coef = [(0, 0, 0)], [weights[0]]
+    for axis in range(3):
+        for d in range(1, radius + 1):
+            for sgn in (-1, 1):
+                o = [0, 0, 0]
+                o[axis] = sgn * d
+                offs.append(tuple(o))
+                coef.append(weights[d])
+    return offs, coef
+
+
+@pytest.mark.parametrize("shape", [(9, 8, 7), (67, 35, 19), (130, 17, 9)])
+@pytest.mark.parametrize("radius", [2, 3])
+def test_wide_offsets_bitwise(shape, radius):
+    """General coefficients, offsets up to `radius`: bitwise the oracle; out
+    is written only on the points whose reads lie in the field."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + radius)
+    u = rng.standard_normal((nz + 2, ny + 2, nx + 2))
+    offs = [tuple(int(v) for v in rng.integers(-radius, radius + 1, 3)) for _ in range(12)]
+    offs.append((radius, -radius, radius))
+    coef = rng.standard_normal(len(offs))
+    out0 = rng.standard_normal(u.shape)
+    assert np.array_equal(run(u, offs, coef, out0), oracle.apply_linear(u, offs, coef, out=out0))
+
+
+INT_STENCILS = {
+    "laplacian7": star(1, [-6.0, 1.0]),
+    "laplacian13_4th": star(2, [-90.0, 16.0, -1.0]),       # 12 h^2 times the fourth-order Laplacian
+    "star19_r3": star(3, [-25.0, 3.0, -2.0, 1.0]),
+    "average4": ([(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0)], [0.25] * 4),
+    "box27": ([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)],
+              [float(v) for v in np.random.default_rng(0).integers(-9, 10, 27)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(INT_STENCILS))
+@pytest.mark.parametrize("shape", [(9, 8, 7), (67, 35, 19), (130, 17, 40)])
+def test_integer_weights_exact_on_integer_inputs(name, shape):
+    """Integer-valued inputs and integer (or dyadic) weights: every partial
+    sum is exact in both evaluations, so the fixed-point path must equal the
+    oracle bit for bit -- every offset, index and bound is checked."""
+    nx, ny, nz = shape
+    offs, coef = INT_STENCILS[name]
+    rng = np.random.default_rng(sum(shape) + len(offs))
+    u = rng.integers(-1000, 1001, (nz + 2, ny + 2, nx + 2)).astype(np.float64)
+    out0 = rng.standard_normal(u.shape)
+    assert np.array_equal(run(u, offs, coef, out0), oracle.apply_linear(u, offs, coef, out=out0))
+
+
+@pytest.mark.parametrize("name", sorted(INT_STENCILS))
+def test_integer_weights_on_smooth_and_random_fields(name):
+    """General binary64 inputs: the fixed-point sum is exact up to the
+    input's conversion (2^-61 of sum |c| max|u|), the oracle's within
+    npoints eps sum |c| max|u|; they agree to that bound (a smooth field,
+    whose Laplacian cancels most digits, and a random one)."""
+    offs, coef = INT_STENCILS[name]
+    nx, ny, nz = 64, 48, 40
+    k, j, i = np.meshgrid(np.arange(nz + 2), np.arange(ny + 2), np.arange(nx + 2), indexing="ij")
+    smooth = np.sin(0.07 * i) * np.cos(0.05 * j) * np.sin(0.03 * k + 0.2) * 3.0
+    rnd = np.random.default_rng(5).standard_normal(smooth.shape)
+    for u in (smooth, rnd):
+        out0 = np.zeros_like(u)
+        got = run(u, offs, coef, out0)
+        ref = oracle.apply_linear(u, offs, coef, out=out0)
+        bound = 2 * len(offs) * np.finfo(float).eps * np.sum(np.abs(coef)) * np.max(np.abs(u))
+        assert np.max(np.abs(got - ref)) <= bound, name
+
+
 def test_arguments():
     a = S.Field(8, 8, 8)
     with pytest.raises(S.StencilError):
         S.stencil_apply_linear(ctx(), a, a, [(0, 0, 0)], [1.0])          # in place
     with pytest.raises(S.StencilError):
-        S.stencil_apply_linear(ctx(), a, a.like(), [(2, 0, 0)], [1.0])   # beyond the halo
+        S.stencil_apply_linear(ctx(), a, a.like(), [(4, 0, 0)], [1.0])   # beyond three cells
     with pytest.raises(S.StencilError):
-        S.stencil_apply_linear(ctx(), a, a.like(), [(0, 0, 0)] * 28, [1.0] * 28)
+        S.stencil_apply_linear(ctx(), a, a.like(), [(0, 0, 0)] * 65, [1.0] * 65)
