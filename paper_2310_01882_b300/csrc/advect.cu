@@ -30,6 +30,7 @@
 // 3.72 ms at 512 x 512 x 256: 21 binary64 operations per cell keep the
 // FP64 pipe busy for about 3 ms on their own.)
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "internal.h"
@@ -223,13 +224,30 @@ __device__ __forceinline__ long long flux(long long a, long long b, long long c,
   return prod(a, b, c) - prod(d, e, f);
 }
 
+// The high half of c d for a horizontal factor c.  POW2: c = 2^m exactly
+// (tcx, tcy powers of two, as 1/4 is), so the high half of c d is d shifted
+// right by 64 - m, floor -- bit for bit what the multiply gives.
+template <bool POW2>
+__device__ __forceinline__ long long hfactor(long long c, int sh, long long d) {
+  if constexpr (POW2) return d >> sh;
+  else return __mul64hi(c, d);
+}
+
 // cx dx + cy dy + c1 p3 - c2 p4, each factor product's high half, as binary64.
-__device__ __forceinline__ double combine(long long cx, long long dx, long long cy, long long dy, long long c1,
-                                          long long p3, long long c2, long long p4, int Q) {
-  const long long s = __mul64hi(cx, dx) + __mul64hi(cy, dy) + __mul64hi(c1, p3) - __mul64hi(c2, p4);
+template <bool POW2>
+__device__ __forceinline__ double combine(long long cx, int shx, long long dx, long long cy, int shy, long long dy,
+                                          long long c1, long long p3, long long c2, long long p4, int Q) {
+  const long long s =
+      hfactor<POW2>(cx, shx, dx) + hfactor<POW2>(cy, shy, dy) + __mul64hi(c1, p3) - __mul64hi(c2, p4);
   return fx64_to_double(s, Q);
 }
 
+// 64 - log2(c) for c a positive power of two (the shift of hfactor), else -1.
+__device__ __forceinline__ int pow2_shift(long long c) {
+  return (c > 0 && (c & (c - 1)) == 0) ? 64 - (63 - __clzll(c)) : -1;
+}
+
+template <bool POW2>
 __global__ void __launch_bounds__(256, 4)
     advect_kernel(const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ w,
                   double* __restrict__ su, double* __restrict__ sv, double* __restrict__ sw,
@@ -237,6 +255,7 @@ __global__ void __launch_bounds__(256, 4)
                   int64_t nx, int64_t ny, int64_t nz, int64_t sy, int64_t sz, int64_t osy, int64_t osz,
                   const unsigned long long* __restrict__ range) {
   extern __shared__ long long adv_tile[];
+  __shared__ long long zfac[2 * kAdvZT];  // tzc1, tzc2 of the tile's planes at scale T
   const AdvScales sc = adv_scales(range);
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kAdvBX;  // halo index of the tile's first cell
   const int64_t j0 = static_cast<int64_t>(blockIdx.y) * kAdvBY;
@@ -270,14 +289,22 @@ __global__ void __launch_bounds__(256, 4)
     V[t] = qv;
     W[t] = qw;
   }
+  {
+    const int t = threadIdx.y * kAdvBX + threadIdx.x;
+    if (t < 2 * kAdvZT) {
+      const int64_t k = k0 + 1 + (t >> 1);
+      zfac[t] = k <= nz ? fx_quant((t & 1) ? tzc2[k - 1] : tzc1[k - 1], sc.T) : 0;
+    }
+  }
   __syncthreads();
   if (i > nx || j > ny) return;
   const long long cx = fx_quant(tcx, sc.T), cy = fx_quant(tcy, sc.T);
+  const int shx = pow2_shift(cx), shy = pow2_shift(cy);
   constexpr int DX = 1, DY = kTX, DZ = kTX * kTY;
   for (int kk = 0; kk < kAdvZT; ++kk) {
     const int64_t k = k0 + 1 + kk;
     if (k > nz) break;
-    const long long c1 = fx_quant(tzc1[k - 1], sc.T), c2 = fx_quant(tzc2[k - 1], sc.T);
+    const long long c1 = zfac[2 * kk], c2 = zfac[2 * kk + 1];
     const int t = (kk + 1) * DZ + (threadIdx.y + 1) * DY + (threadIdx.x + 1);
     const long long u0 = U[t], v0 = V[t], w0 = W[t];
     const int64_t o = i + j * osy + k * osz;
@@ -288,7 +315,7 @@ __global__ void __launch_bounds__(256, 4)
       const long long dy = flux(U[t - DY], V[t - DY], V[t - DY + DX], U[t + DY], v0, V[t + DX]);
       const long long p3 = prod(U[t - DZ], W[t - DZ], W[t - DZ + DX]);
       const long long p4 = prod(U[t + DZ], w0, W[t + DX]);
-      su[o] = combine(cx, dx, cy, dy, c1, p3, c2, p4, sc.Q);
+      su[o] = combine<POW2>(cx, shx, dx, cy, shy, dy, c1, p3, c2, p4, sc.Q);
     }
     // sv at (i, j+1/2, k)
     {
@@ -297,7 +324,7 @@ __global__ void __launch_bounds__(256, 4)
       const long long dy = flux(vm, v0, vm, vp, v0, vp);
       const long long p3 = prod(V[t - DZ], W[t - DZ], W[t - DZ + DY]);
       const long long p4 = prod(V[t + DZ], w0, W[t + DY]);
-      sv[o] = combine(cx, dx, cy, dy, c1, p3, c2, p4, sc.Q);
+      sv[o] = combine<POW2>(cx, shx, dx, cy, shy, dy, c1, p3, c2, p4, sc.Q);
     }
     // sw at (i, j, k+1/2)
     {
@@ -306,7 +333,7 @@ __global__ void __launch_bounds__(256, 4)
       const long long dy = flux(W[t - DY], V[t - DY], V[t - DY + DZ], W[t + DY], v0, V[t + DZ]);
       const long long p3 = prod(wm, w0, wm);
       const long long p4 = prod(wp, w0, wp);
-      sw[o] = combine(cx, dx, cy, dy, c1, p3, c2, p4, sc.Q);
+      sw[o] = combine<POW2>(cx, shx, dx, cy, shy, dy, c1, p3, c2, p4, sc.Q);
     }
   }
 }
@@ -333,13 +360,22 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
       u.nx, u.ny, u.nz, u.sy, u.sz, tzc1, tzc2, tcx, tcy, range);
   rc = check_cuda(cudaGetLastError(), "advect range kernel");
   if (rc) return rc;
-  rc = check_cuda(cudaFuncSetAttribute(advect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdvSmem),
+  // tcx and tcy positive powers of two (within the fixed-point range): their
+  // factor products are shifts (the quantised factor is then exactly
+  // 2^(m + T), see hfactor)
+  auto pow2 = [](double c) {
+    int e = 0;
+    return c > 0.0 && std::frexp(c, &e) == 0.5 && e > -900 && e < 900;
+  };
+  const bool p2 = pow2(tcx) && pow2(tcy);
+  auto kern = p2 ? advect_kernel<true> : advect_kernel<false>;
+  rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdvSmem),
                   "advect smem attribute");
   if (rc) return rc;
   const dim3 block(kAdvBX, kAdvBY);
   const dim3 grid(static_cast<unsigned>((u.nx + kAdvBX - 1) / kAdvBX), static_cast<unsigned>(gy),
                   static_cast<unsigned>(gz));
-  advect_kernel<<<grid, block, kAdvSmem, st>>>(
+  kern<<<grid, block, kAdvSmem, st>>>(
       static_cast<const double*>(u.data), static_cast<const double*>(v.data),
       static_cast<const double*>(w.data), static_cast<double*>(su.data), static_cast<double*>(sv.data),
       static_cast<double*>(sw.data), tzc1, tzc2, tcx, tcy, u.nx, u.ny, u.nz, u.sy, u.sz, su.sy, su.sz, range);
