@@ -349,6 +349,13 @@ def run_ours(args, rank, world, local_rank):
         ctx.close()
         return
 
+    if args.only == "apply":
+        r = apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak)
+        if rank == 0:
+            print(json.dumps({"metric": "linear apply (profiling run)", **r}))
+        ctx.close()
+        return
+
     if args.only == "residual":
         u, ut, f = fields(S.F64)
         norms = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -501,21 +508,8 @@ def run_ours(args, rank, world, local_rank):
     del a2, a2t
     torch.cuda.empty_cache()
 
-    # ---- general linear apply: the 7-point operator as 7 (offset, coefficient)
-    # terms on 512^3, binary64 in the order written -------------------------------
-    li = S.Field.from_numpy(u0, S.F64, device=dev)
-    lo = li.like()
-    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
-    coefs = [-6.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0]
-    lms = timed_steps(lambda: S.stencil_apply_linear(ctx, li, lo, offs, coefs), 5, 2)
-    components["apply_linear_7pt_512cubed_f64"] = {
-        "ms": round(lms, 3), "gpts": round(N ** 3 / (lms * 1e-3) / 1e9, 2),
-        "hbm_gbs": round(16 * N ** 3 / (lms * 1e-3) / 1e9, 1),
-        "frac_of_measured_hbm": round(16 * N ** 3 / (lms * 1e-3) / 1e9 / hbm_peak, 4),
-        "note": "one rounded multiply and one rounded add per term in the order given (bitwise the "
-                "definition): 14 FP64 instructions per point, FP64-pipe bound"}
-    del li, lo
-    torch.cuda.empty_cache()
+    # ---- general linear apply -------------------------------------------------
+    components.update(apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak))
 
     # ---- z-slab decomposition: 4 virtual ranks on this GPU, a halo exchange
     # every `depth` sweeps, against the whole grid swept in calls of as many
@@ -737,6 +731,48 @@ def batch_throughput(max_sweeps=4000, sweeps_per_cycle=400, sizes=None):
     return out
 
 
+def star_stencil(radius, weights):
+    """Offsets and coefficients of a star stencil: weights[d] at distance d
+    along each axis (weights[0] once, at the centre)."""
+    offs, coef = [(0, 0, 0)], [weights[0]]
+    for axis in range(3):
+        for d in range(1, radius + 1):
+            for sgn in (-1, 1):
+                o = [0, 0, 0]
+                o[axis] = sgn * d
+                offs.append(tuple(o))
+                coef.append(weights[d])
+    return offs, coef
+
+
+def apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak):
+    """stencil_apply_linear on the 512^3 field: the 7-point and the
+    fourth-order 13-point Laplacians with integer weights (the exact
+    fixed-point path) and the 7-point average with weights 1/6 (binary64 in
+    the order written).  16 algorithmic bytes per output point."""
+    li = S.Field.from_numpy(u0, S.F64, device=dev)
+    lo = li.like()
+    cases = {
+        "apply_linear_7pt_int_512cubed_f64": star_stencil(1, [-6.0, 1.0]) + ("fixed point (integer weights)",),
+        "apply_linear_13pt_r2_int_512cubed_f64": star_stencil(2, [-90.0, 16.0, -1.0])
+        + ("fixed point (integer weights), radius 2",),
+        "apply_linear_7pt_sixth_512cubed_f64": star_stencil(1, [0.0, 1.0 / 6.0]) + (
+            "binary64 in the order written (weights 1/6, not integer multiples of a power of two): "
+            "FP64-pipe bound",),
+    }
+    out = {}
+    for name, (offs, coefs, note) in cases.items():
+        r = max(abs(v) for o in offs for v in o)
+        pts = (N + 2 - 2 * r) ** 3
+        lms = timed_steps(lambda: S.stencil_apply_linear(ctx, li, lo, offs, coefs), 5, 2)
+        S.stencil_ctx_status(ctx)
+        gb = 16 * pts / (lms * 1e-3) / 1e9
+        out[name] = {"ms": round(lms, 3), "gpts": round(pts / (lms * 1e-3) / 1e9, 2), "terms": len(offs),
+                     "hbm_gbs": round(gb, 1), "frac_of_measured_hbm": round(gb / hbm_peak, 4), "note": note}
+    del li, lo
+    return out
+
+
 def tune_residual(S, ctx, u, f, h, norms, timed_steps):
     """Time every compiled configuration of the fixed-point residual on these
     grids (with the caller's CUDA-event timer) and keep the fastest in ctx;
@@ -819,7 +855,7 @@ def main():
                     help="pin the headline's FP64 one-sweep configuration (index; profiling runs)")
     ap.add_argument("--grid", type=int, default=None, help="grid extent (profiling runs; default 512)")
     ap.add_argument("--sweeps", type=int, default=None, help="sweeps per step (profiling runs; default 1000)")
-    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet", "batch", "redblack", "residual"],
+    ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet", "batch", "redblack", "residual", "apply"],
                     help="run one dtype's step only (profiling runs)")
     ap.add_argument("--spp", type=int, default=0, help="sweeps per pass for --only runs (0 = library default)")
     ap.add_argument("--resid-config", type=int, default=None,

@@ -96,13 +96,89 @@ __device__ __forceinline__ int64_t fx_quant_signed(double x, int Cu) {
   return static_cast<int64_t>((t ^ fx_sign_mask(b)) + 1) >> 1;
 }
 
+// The z march of one CTA.  EXACT_EXP: every nonzero result's binary64
+// exponent can be shifted by E - S without leaving the normal range (the
+// scaling is then an integer add to the exponent field); otherwise ldexp.
+template <int R, bool EXACT_EXP>
+__device__ __forceinline__ void apply_fx_march(const double* __restrict__ in, double* __restrict__ out, int64_t nx,
+                                               int64_t ny, int64_t nz, int64_t sy, int64_t sz, int64_t osy,
+                                               int64_t osz, const FxTerms& t, int Cu, int sh, bool bad, int zchunk) {
+  constexpr int WX = kApBX + 2 * R, WY = kApBY + 2 * R, PL = WX * WY, NP = 2 * R + 1;
+  constexpr int NT = kApBX * kApBY, NL = (PL + NT - 1) / NT;
+  extern __shared__ long long ap_win[];  // 2 NP slots of PL values
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kApBX + tx;
+  const int64_t ox = t.r + static_cast<int64_t>(blockIdx.x) * kApBX;  // first output column of the tile
+  const int64_t oy = t.r + static_cast<int64_t>(blockIdx.y) * kApBY;
+  const int64_t zs = t.r + static_cast<int64_t>(blockIdx.z) * zchunk;
+  const int64_t ze = min(zs + zchunk - 1, nz + 1 - t.r);
+  const int64_t i = ox + tx, j = oy + ty;
+  const bool owner = i <= nx + 1 - t.r && j <= ny + 1 - t.r;
+  // the window cells this thread loads: their offset within a plane, and
+  // whether they lie in the field (in x and y)
+  int64_t goff[NL];
+  bool gin[NL];
+#pragma unroll
+  for (int m = 0; m < NL; ++m) {
+    const int c = tid + m * NT;
+    const int cy = c / WX, cx = c - cy * WX;
+    const int64_t gi = ox - R + cx, gj = oy - R + cy;
+    gin[m] = c < PL && gi >= 0 && gi <= nx + 1 && gj >= 0 && gj <= ny + 1;
+    goff[m] = gin[m] ? gi + gj * sy : 0;
+  }
+  int slot = static_cast<int>((((zs - R) % NP) + NP) % NP);  // ring slot of plane p
+  const double* src = in + (zs - R) * sz;
+  double* dst = out + i + j * osy + (zs - 2 * R) * osz;    // output plane p - R
+  // software pipeline: the raw values of plane p are loaded while plane
+  // p - 1 is computed, and converted into the ring at the top of step p
+  double raw[NL];
+  auto load = [&](int64_t p, const double* srcp) {
+    const bool pin = p >= 0 && p <= nz + 1;
+#pragma unroll
+    for (int m = 0; m < NL; ++m) raw[m] = (pin && gin[m]) ? srcp[goff[m]] : 0.0;
+  };
+  load(zs - R, src);
+  for (int64_t p = zs - R; p <= ze + R; ++p, src += sz, dst += osz) {
+    // plane p into ring slots `slot` and `slot + NP`, so that the planes
+    // z - R .. z + R are consecutive from the slot of z - R
+#pragma unroll
+    for (int m = 0; m < NL; ++m) {
+      const int c = tid + m * NT;
+      if (c < PL) {
+        const long long q = fx_quant_signed(raw[m], Cu);
+        ap_win[slot * PL + c] = q;
+        ap_win[(slot + NP) * PL + c] = q;
+      }
+    }
+    if (p < ze + R) load(p + 1, src + sz);
+    __syncthreads();
+    if (p - R >= zs && owner) {
+      int b = slot - 2 * R;  // slot of plane (p - R) - R
+      if (b < 0) b += NP;
+      const long long* w = ap_win + b * PL + ty * WX + tx;
+      long long acc = 0;
+      for (int q = 0; q < t.n; ++q) acc += static_cast<long long>(t.k[q]) * w[t.soff[q]];
+      double v;
+      if (bad) {
+        v = __longlong_as_double(0x7ff8000000000000ll);
+      } else if (acc == 0) {
+        v = 0.0;
+      } else if constexpr (EXACT_EXP) {
+        v = __longlong_as_double(__double_as_longlong(__ll2double_rn(acc)) + (static_cast<long long>(sh) << 52));
+      } else {
+        v = ldexp(__ll2double_rn(acc), sh);
+      }
+      *dst = v;
+    }
+    __syncthreads();
+    slot = slot + 1 == NP ? 0 : slot + 1;
+  }
+}
+
 template <int R>
 __global__ void __launch_bounds__(kApBX * kApBY)
     apply_fx_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
                     int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ FxTerms t,
                     const unsigned long long* __restrict__ maxbits, uint32_t* status, int zchunk) {
-  constexpr int WX = kApBX + 2 * R, WY = kApBY + 2 * R, PL = WX * WY, NP = 2 * R + 1;
-  extern __shared__ long long ap_win[];  // 2 NP slots of PL values
   // scale: sum |k_p| max|in| 2^S <= 2^61, so every partial sum stays below 2^62
   const double mx = __longlong_as_double(static_cast<long long>(maxbits[0]));
   int bad = 0;
@@ -116,55 +192,15 @@ __global__ void __launch_bounds__(kApBX * kApBY)
     if (S > 1022) S = 1022;
     if (S < -900) bad = 2;
   }
-  if (bad) {
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
-      atomicOr(status, bad == 1 ? kStatusNonFinite : kStatusRange);
-  }
-  const int Cu = 1085 - S;
+  if (bad && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    atomicOr(status, bad == 1 ? kStatusNonFinite : kStatusRange);
   const int sh = t.E - S;  // out = sum 2^sh
-  const bool exp_ok = sh >= -1022 && sh <= 960;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kApBX + tx;
-  const int64_t ox = t.r + static_cast<int64_t>(blockIdx.x) * kApBX;  // first output column of the tile
-  const int64_t oy = t.r + static_cast<int64_t>(blockIdx.y) * kApBY;
-  const int64_t zs = t.r + static_cast<int64_t>(blockIdx.z) * zchunk;
-  const int64_t ze = std::min<int64_t>(zs + zchunk - 1, nz + 1 - t.r);
-  const int64_t i = ox + tx, j = oy + ty;
-  const bool owner = i <= nx + 1 - t.r && j <= ny + 1 - t.r;
-  for (int64_t p = zs - R; p <= ze + R; ++p) {
-    // plane p into ring slots s and s + NP (so planes z - R .. z + R are
-    // consecutive from slot (z - R) mod NP)
-    const int s = static_cast<int>(((p % NP) + NP) % NP);
-    long long* w0 = ap_win + s * PL;
-    long long* w1 = ap_win + (s + NP) * PL;
-    for (int c = tid; c < PL; c += kApBX * kApBY) {
-      const int cy = c / WX, cx = c - cy * WX;
-      const int64_t gi = ox - R + cx, gj = oy - R + cy;
-      long long q = 0;
-      if (p >= 0 && p <= nz + 1 && gi >= 0 && gi <= nx + 1 && gj >= 0 && gj <= ny + 1)
-        q = fx_quant_signed(in[gi + gj * sy + p * sz], Cu);
-      w0[c] = q;
-      w1[c] = q;
-    }
-    __syncthreads();
-    const int64_t z = p - R;
-    if (z >= zs && owner) {
-      const int base = static_cast<int>(((z - R) % NP + NP) % NP) * PL + ty * WX + tx;
-      long long acc = 0;
-      for (int q = 0; q < t.n; ++q) acc += static_cast<long long>(t.k[q]) * ap_win[base + t.soff[q]];
-      double v;
-      if (bad) {
-        v = __longlong_as_double(0x7ff8000000000000ll);
-      } else if (acc == 0) {
-        v = 0.0;
-      } else {
-        const double d = __ll2double_rn(acc);
-        v = exp_ok ? __longlong_as_double(__double_as_longlong(d) + (static_cast<long long>(sh) << 52))
-                   : ldexp(d, sh);
-      }
-      out[i + j * osy + z * osz] = v;
-    }
-    __syncthreads();
-  }
+  // |sum| in [1, 2^62): its exponent is 0..61, shifted stays normal when
+  // -1022 <= sh and sh + 61 <= 1023
+  if (sh >= -1022 && sh <= 962)
+    apply_fx_march<R, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
+  else
+    apply_fx_march<R, false>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
 }
 
 // c = k 2^e with k an odd integer (c != 0): the exact decomposition.

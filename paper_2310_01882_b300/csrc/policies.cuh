@@ -332,12 +332,10 @@ struct PolResid {
     __device__ __forceinline__ void add_sq(int64_t R) {
       const uint64_t a = static_cast<uint64_t>(R < 0 ? -R : R);
       const uint64_t lo = a * a, hi = __umul64hi(a, a);
-      s0 += lo;
-      const uint64_t c0 = s0 < lo;
-      const uint64_t t = s1 + hi;
-      const uint64_t c1 = t < hi;
-      s1 = t + c0;
-      s2 += c1 + (s1 < c0);
+      // (s2, s1, s0) += (0, hi, lo) as one carry chain
+      asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, 0;"
+          : "+l"(s0), "+l"(s1), "+l"(s2)
+          : "l"(lo), "l"(hi));
     }
     __device__ __forceinline__ void add(uint64_t R, double f) {
       add_sq(static_cast<int64_t>(R));
