@@ -51,16 +51,16 @@ ALGO_BYTES = {"f64": 24, "f32": 12, "bf16": 6}   # read u, read f, write u' per 
 #   python bench.py --grid 320 --sweeps 8 --only f64 --steps 1 --warmup 1 --no-cpu --f64-config i
 _SCALE_320 = (512 / 320) ** 3
 MEASURED_TRAFFIC = {
-    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (587434752 + 231388160) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (569373696 + 232077568) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (569324288 + 232129280) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (568562944 + 231546624) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (573722880 + 234918144) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=5>": (550198528 + 235312384) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=6>": (550281728 + 234866944) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=16,S=5>": (575207936 + 233568000) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=2,WY=8,S=5>": (546770944 + 234200064) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=1,WY=16,S=5>": (563922432 + 237409024) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=16,S=5>": (574407680 + 233541120) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=6>": (550171904 + 234793984) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=5>": (550025984 + 235125504) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=8,S=5>": (547156736 + 234843136) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (567644160 + 231931648) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (587555584 + 232088832) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (571086336 + 232422400) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (574176768 + 234781440) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=1,WY=16,S=5>": (565510400 + 238744320) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (564643840 + 230349312) * _SCALE_320,
 }
 
 

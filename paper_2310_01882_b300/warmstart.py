@@ -415,7 +415,8 @@ def main():
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--streams", type=int, default=8)
-    ap.add_argument("--load", default=None, help="evaluate saved parameters (.npy) instead of training")
+    ap.add_argument("--load", default=None,
+                    help="evaluate saved parameters (.npy, or a wsnet file such as the committed TRAINED) instead of training")
     ap.add_argument("--together", type=int, default=0,
                     help="also time solving this many held-out fields as one job")
     ap.add_argument("--kinds", default="fp64,f32,bf16",
@@ -431,7 +432,10 @@ def main():
     gen_s = train_s = 0.0
     hist = []
     if args.load:
-        net.set_params(np.load(args.load))
+        if args.load.endswith(".npy"):
+            net.set_params(np.load(args.load))
+        else:  # a wsnet_save / save_params_only file (e.g. TRAINED)
+            S.wsnet_load(net, args.load)
         args.train = args.epochs = 0
     else:
         t0 = time.perf_counter()
