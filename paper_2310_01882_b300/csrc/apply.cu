@@ -96,10 +96,27 @@ __device__ __forceinline__ int64_t fx_quant_signed(double x, int Cu) {
   return static_cast<int64_t>((t ^ fx_sign_mask(b)) + 1) >> 1;
 }
 
+// Compiled offset sets: the common shapes, offsets known at compile time so
+// that every term's shared-memory offset is an immediate and its weight a
+// constant-bank operand.  SHAPE 1: the star of radius R (the centre, then
+// +-1..R along x, y, z); SHAPE 2: the 27-point box (R = 1).  SHAPE 0: any
+// offsets (read from the launch parameters term by term).
+template <int SHAPE, int R>
+struct ApShape {
+  static constexpr int N = SHAPE == 2 ? 27 : 1 + 6 * R;
+  // offset of term q along x, y, z
+  __host__ __device__ static constexpr int d(int q, int axis) {
+    if (SHAPE == 2) return axis == 0 ? q % 3 - 1 : (axis == 1 ? (q / 3) % 3 - 1 : q / 9 - 1);
+    if (q == 0) return 0;
+    const int idx = q - 1, ax = idx / (2 * R), rem = idx % (2 * R);
+    return ax != axis ? 0 : ((rem & 1) ? 1 : -1) * (rem / 2 + 1);
+  }
+};
+
 // The z march of one CTA.  EXACT_EXP: every nonzero result's binary64
 // exponent can be shifted by E - S without leaving the normal range (the
 // scaling is then an integer add to the exponent field); otherwise ldexp.
-template <int R, bool EXACT_EXP>
+template <int R, int SHAPE, bool EXACT_EXP>
 __device__ __forceinline__ void apply_fx_march(const double* __restrict__ in, double* __restrict__ out, int64_t nx,
                                                int64_t ny, int64_t nz, int64_t sy, int64_t sz, int64_t osy,
                                                int64_t osz, const FxTerms& t, int Cu, int sh, bool bad, int zchunk) {
@@ -156,7 +173,15 @@ __device__ __forceinline__ void apply_fx_march(const double* __restrict__ in, do
       if (b < 0) b += NP;
       const long long* w = ap_win + b * PL + ty * WX + tx;
       long long acc = 0;
-      for (int q = 0; q < t.n; ++q) acc += static_cast<long long>(t.k[q]) * w[t.soff[q]];
+      if constexpr (SHAPE == 0) {
+        for (int q = 0; q < t.n; ++q) acc += static_cast<long long>(t.k[q]) * w[t.soff[q]];
+      } else {
+        using Sh = ApShape<SHAPE, R>;
+#pragma unroll
+        for (int q = 0; q < Sh::N; ++q)
+          acc += static_cast<long long>(t.k[q]) *
+                 w[(R + Sh::d(q, 2)) * PL + (R + Sh::d(q, 1)) * WX + (R + Sh::d(q, 0))];
+      }
       double v;
       if (bad) {
         v = __longlong_as_double(0x7ff8000000000000ll);
@@ -174,7 +199,7 @@ __device__ __forceinline__ void apply_fx_march(const double* __restrict__ in, do
   }
 }
 
-template <int R>
+template <int R, int SHAPE>
 __global__ void __launch_bounds__(kApBX * kApBY)
     apply_fx_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
                     int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ FxTerms t,
@@ -198,9 +223,9 @@ __global__ void __launch_bounds__(kApBX * kApBY)
   // |sum| in [1, 2^62): its exponent is 0..61, shifted stays normal when
   // -1022 <= sh and sh + 61 <= 1023
   if (sh >= -1022 && sh <= 962)
-    apply_fx_march<R, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
+    apply_fx_march<R, SHAPE, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
   else
-    apply_fx_march<R, false>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
+    apply_fx_march<R, SHAPE, false>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
 }
 
 // c = k 2^e with k an odd integer (c != 0): the exact decomposition.
@@ -244,6 +269,21 @@ int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const
     int n = 0;
     const int R = r;  // the window radius is the offsets' radius
     const int WX = kApBX + 2 * R, WY = kApBY + 2 * R, PL = WX * WY;
+    // a compiled shape that holds every offset: the star of radius r (all
+    // offsets on the axes) or, at r = 1, the 27-point box
+    bool on_axes = true;
+    for (int p = 0; p < npoints; ++p) {
+      const int nz_axes = (offsets[3 * p] != 0) + (offsets[3 * p + 1] != 0) + (offsets[3 * p + 2] != 0);
+      if (nz_axes > 1) on_axes = false;
+    }
+    const int shape = on_axes ? 1 : (r == 1 ? 2 : 0);
+    const int nshape = shape == 2 ? 27 : 1 + 6 * r;
+    auto shape_term = [&](int dx, int dy, int dz) {  // index of an offset in the compiled shape
+      if (shape == 2) return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+      if (dx == 0 && dy == 0 && dz == 0) return 0;
+      const int ax = dx ? 0 : (dy ? 1 : 2), d = dx + dy + dz;
+      return 1 + ax * 2 * r + 2 * (std::abs(d) - 1) + (d > 0);
+    };
     for (int p = 0; p < npoints; ++p) {
       if (coeffs[p] == 0.0) continue;
       const int shift = e0[p] - E;
@@ -251,14 +291,21 @@ int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const
         fx = false;
         break;
       }
-      t.k[n] = static_cast<int>(k0[p] << shift);
-      sumk += std::fabs(static_cast<double>(t.k[n]));
+      const int kp = static_cast<int>(k0[p] << shift);
+      sumk += std::fabs(static_cast<double>(kp));
       const int dx = offsets[3 * p], dy = offsets[3 * p + 1], dz = offsets[3 * p + 2];
-      t.soff[n] = (R + dz) * PL + (R + dy) * WX + (R + dx);
-      ++n;
+      if (shape) {  // the weights in the shape's order (repeated offsets add up: the sum is exact)
+        t.k[shape_term(dx, dy, dz)] += kp;
+      } else {
+        t.k[n] = kp;
+        t.soff[n] = (R + dz) * PL + (R + dy) * WX + (R + dx);
+        ++n;
+      }
     }
+    for (int q = 0; shape && q < nshape; ++q)
+      if (std::llabs(static_cast<long long>(t.k[q])) > (1ll << 20)) fx = false;  // summed repeats
     if (fx) {
-      t.n = n;
+      t.n = shape ? nshape : n;
       t.r = r;
       t.E = E;
       t.sumk = sumk > 0.0 ? sumk : 1.0;
@@ -280,7 +327,9 @@ int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const
                       static_cast<unsigned>((oz + zc - 1) / zc));
       if (grid.y > 65535 || grid.z > 65535) return set_error(STENCIL_ERR_ARG, "apply_linear: grid too large");
       const int smem = 2 * (2 * R + 1) * PL * static_cast<int>(sizeof(long long));
-      auto kern = R == 1 ? apply_fx_kernel<1> : (R == 2 ? apply_fx_kernel<2> : apply_fx_kernel<3>);
+      auto kern = shape == 2 ? apply_fx_kernel<1, 2>
+                  : shape == 1 ? (R == 1 ? apply_fx_kernel<1, 1> : (R == 2 ? apply_fx_kernel<2, 1> : apply_fx_kernel<3, 1>))
+                               : (R == 1 ? apply_fx_kernel<1, 0> : (R == 2 ? apply_fx_kernel<2, 0> : apply_fx_kernel<3, 0>));
       rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
                       "apply smem attribute");
       if (rc) return rc;

@@ -80,6 +80,10 @@ INT_STENCILS = {
     "average4": ([(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0)], [0.25] * 4),
     "box27": ([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)],
               [float(v) for v in np.random.default_rng(0).integers(-9, 10, 27)]),
+    # off-axis offsets of radius 2, a repeated offset, a zero weight: the
+    # fixed-point kernel that reads its terms at run time
+    "random_r2": ([(1, -2, 0), (0, 0, 0), (-1, 1, 2), (2, 2, -1), (1, -2, 0), (0, -2, 1)],
+                  [3.0, -8.0, 0.5, -1.25, 2.0, 0.0]),
 }
 
 
