@@ -469,8 +469,7 @@ STENCIL_API int wsnet_loss_grad(wsnet* net, const float* x, const float* t,
  * stencil_residual, for callers that cannot allocate device memory: code
  * running where allocation is forbidden or unavailable (a host application
  * that owns all device memory through its own allocator, a no-allocation
- * real-time loop, a stream that is being captured), and that therefore
- * cannot create a stencil_ctx either.  This call allocates nothing and takes
+ * real-time loop), and that therefore cannot create a stencil_ctx either.  This call allocates nothing and takes
  * no context: its partial sums live in a fixed array built into the
  * library (128 KiB per device that loads the library, held until the
  * process exits).  The paper has no counterpart; it is a deployment
