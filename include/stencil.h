@@ -288,6 +288,15 @@ STENCIL_API int stencil_residual_config_count(int32_t* count);
 STENCIL_API int stencil_residual_config_select(stencil_ctx* ctx, int32_t index);
 
 /*
+ * The same for stencil_advect_uvw's fixed-point kernel (its thread-block
+ * shape and CTAs per SM): the number of compiled configurations, and the
+ * one ctx uses (index 0 unless selected).  Errors: STENCIL_ERR_ARG (null
+ * count or ctx, index out of range).
+ */
+STENCIL_API int stencil_advect_config_count(int32_t* count);
+STENCIL_API int stencil_advect_config_select(stencil_ctx* ctx, int32_t index);
+
+/*
  * stencil_residual -- the residual of A u = f for the 7-point operator
  *     (A u)[i,j,k] = (6 u[i,j,k] - sum of the six neighbours) / h^2,
  *     r = f - A u on the interior,
@@ -516,10 +525,11 @@ STENCIL_API int stencil_residual_noalloc(const stencil_grid* u,
  * tzc1, tzc2: DEVICE arrays of nz doubles.
  * Arithmetic: 64-bit integer fixed point with one scale for u, v, w (from
  * their largest magnitude, halos included) and one for the factors; every
- * sum of two values is exact, every product keeps the high 64 bits of its
- * exact 128-bit value, and each tendency is rounded to binary64 once: the
- * error is at most about 2^-50 max|u,v,w|^2 max|factor|, the order of a
- * binary64 evaluation's rounding error, and equal fluxes cancel exactly.  If the three fields' (or
+ * sum of two or three values is exact, every product is within 9/4 units
+ * of 2^-64 of its exact value (three 32 x 32-bit partial products), and
+ * each tendency is rounded to binary64 once: the error is at most about
+ * 2^-50 max|u,v,w|^2 max|factor|, the order of a binary64 evaluation's
+ * rounding error, and equal fluxes cancel exactly.  If the three fields' (or
  * the factors') largest magnitudes differ by more than 2^8, or an input is
  * not finite, the launch evaluates the formula in binary64 instead (NaN and
  * Inf propagate as in binary64).  Uses the context's scratch; asynchronous.

@@ -5,30 +5,39 @@
 // B300 issues binary64 arithmetic at about 1/64 of its binary32 rate, so a
 // binary64 evaluation of the 63 operations is bound by the FP64 pipe at a
 // few percent of the HBM roofline.  The kernel therefore evaluates the
-// tendencies in 64-bit integer fixed point, as the Jacobi sweep does:
+// tendencies in 64-bit integer fixed point:
 //   * one scale S per call from max |u|, |v|, |w| (halos included):
-//     X = round(x 2^S) with |X| <= 2^61, so every sum of two is exact;
-//   * each product a (b + c) keeps the high 64 bits of its exact 128-bit
-//     value (a truncation below 2^-56 max|x|^2), so equal fluxes cancel
-//     exactly;
+//     X = trunc(x 2^S) with |X| <= 2^61, so every sum of two or three is
+//     exact;
+//   * each product a (b + c) is a s / 2^64 from three 32 x 32-bit products
+//     (mh: within [-1/4, 9/4) of the exact value, 2^-57 of the largest
+//     product), a function of (a, s) alone, so equal fluxes cancel exactly;
+//     the self terms um (u + um) - up (u + up) are taken as the one product
+//     (um - up)(u + um + up), the same value in exact arithmetic;
 //   * the factors tcx, tcy, tzc1[k], tzc2[k] use one scale T from their
-//     maximum (|C| <= 2^62; exact for the binary64 inputs in use), each
-//     factor product again keeps its high 64 bits, the three terms are
-//     summed in 64 bits and the sum is rounded to binary64 once.
-// The error is at most about 2^-50 max|x|^2 max|C| per output, the order of
-// the rounding error of a binary64 evaluation of the same formula.  When the fields'
-// magnitudes differ by more than 2^8, or the factors' do, or a value is not
-// finite, a single scale would cost the smaller field its precision, so the
-// launch evaluates the formula in binary64 instead (the decision is taken
-// on the device from the range reduction: the call stays asynchronous).
+//     maximum (|C| <= 2^62; exact for the binary64 inputs in use); the
+//     factor products are mh again (power-of-two tcx, tcy: exact shifts),
+//     the three terms are summed in 64 bits and the sum is rounded to
+//     binary64 once.
+// The error is a few units of 2^-57 of the largest product per output, the
+// order of the rounding error of a binary64 evaluation of the same formula.
+// When the fields' magnitudes differ by more than 2^8, or the factors' do,
+// or a value is not finite, a single scale would cost the smaller field its
+// precision, so the launch evaluates the formula in binary64 instead (the
+// decision is taken on the device from the range reduction: the call stays
+// asynchronous).
 //
-// Each CTA quantises a (32+2) x (8+2) x (4+2) halo tile of u, v, w into
-// shared memory once; each thread then computes su, sv, sw for 4 cells
-// along z from the tile.  48 algorithmic bytes per cell (three fields in,
-// three out).  (Computing sw in binary64 on the otherwise idle FP64 pipe
-// while su and sv use the integer pipe was measured slower, 3.85 against
-// 3.72 ms at 512 x 512 x 256: 21 binary64 operations per cell keep the
-// FP64 pipe busy for about 3 ms on their own.)
+// Each CTA owns a 32 x BY column of cells and marches up a chunk of z
+// planes: every plane of u, v, w is loaded once (coalesced, one plane ahead
+// in registers), quantised once into a ring of four shared-memory plane
+// slots, and each thread computes su, sv, sw of its cell from the three
+// slots around it -- one CTA barrier per plane.  48 algorithmic bytes per
+// cell (three fields in, three out).  The quantisation and the final
+// rounding run as 64-bit conversions, which B300 issues on its FP64 pipe at
+// about twice its multiply rate, so the integer pipes keep the products.
+// (Computing sw in binary64 on the FP64 pipe while su and sv use the
+// integer pipes was measured slower: 21 binary64 operations per cell keep
+// that pipe busy on their own.)
 #include <algorithm>
 #include <cmath>
 
@@ -39,10 +48,6 @@ namespace stencil {
 
 namespace {
 
-constexpr int kAdvBX = 32, kAdvBY = 8, kAdvZT = 4;
-constexpr int kTX = kAdvBX + 2, kTY = kAdvBY + 2, kTZ = kAdvZT + 2;
-constexpr int kTile = kTX * kTY * kTZ;
-constexpr int kAdvSmem = 3 * kTile * 8;
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
@@ -131,6 +136,7 @@ __device__ __forceinline__ AdvScales adv_scales(const unsigned long long* r) {
   if (static_cast<int>(r[3] >> 52) - static_cast<int>(r[4] >> 52) > 8) return sc;
   sc.S = 61 - ceil_log2_bits(M);
   sc.T = 62 - ceil_log2_bits(r[3]);
+  if (sc.S > 1000 || sc.T > 1000) return sc;  // magnitudes below 2^-939: binary64
   sc.Q = 2 * sc.S + sc.T - 128;
   sc.fixed = true;
   return sc;
@@ -215,31 +221,41 @@ __device__ __forceinline__ void advect_cell_f64(const double* __restrict__ u, co
   osw = advect_sw_f64(u, v, w, c, sy, sz, tcx, tcy, c1, c2);
 }
 
-// floor(a (b + c) / 2^64): the high half of the exact product.
-__device__ __forceinline__ long long prod(long long a, long long b, long long c) { return __mul64hi(a, b + c); }
-
-// One flux difference a (b + c) - d (e + f) at scale 2^(2S - 64).
-__device__ __forceinline__ long long flux(long long a, long long b, long long c, long long d, long long e,
-                                          long long f) {
-  return prod(a, b, c) - prod(d, e, f);
+// a s / 2^64 for |a| <= 2^62 and |s| < 2^63 - 2^32, from three 32 x 32-bit
+// products: with a = ah 2^32 + al and s = sh 2^32 + sl, the low words taken
+// as SIGNED 32-bit values (so every limb product is a plain signed multiply),
+//   a s = ah sh 2^64 + (ah sl + al sh) 2^32 + al sl,
+// and the result is ah sh + floor(ah sl / 2^32) + floor(al sh / 2^32).  It
+// lies within [-1/4, 9/4) of the exact a s / 2^64 (the dropped al sl / 2^64
+// is below 1/4 in magnitude, the two floors drop less than 2): the same
+// order as keeping the exact product's high half, at a third of the integer
+// instructions.  It is a function of (a, s) alone, so equal fluxes still
+// cancel exactly.
+__device__ __forceinline__ long long mh(long long a, long long s) {
+  const int al = static_cast<int>(a);
+  const int ah = static_cast<int>(a >> 32) + static_cast<int>(static_cast<unsigned>(al) >> 31);
+  const int sl = static_cast<int>(s);
+  const int sh = static_cast<int>(s >> 32) + static_cast<int>(static_cast<unsigned>(sl) >> 31);
+  const int t = __mulhi(ah, sl) + __mulhi(al, sh);  // |t| < 2^31 for the stated ranges
+  return static_cast<long long>(ah) * sh + t;
 }
 
-// The high half of c d for a horizontal factor c.  POW2: c = 2^m exactly
-// (tcx, tcy powers of two, as 1/4 is), so the high half of c d is d shifted
-// right by 64 - m, floor -- bit for bit what the multiply gives.
+// The factor product of a horizontal factor c with a flux difference d.
+// POW2: c = 2^m exactly (tcx, tcy positive powers of two, as 1/4 is), so
+// c d / 2^64 is d shifted right by sh = 64 - m (floor).
+// On the fixed-point path sh lies in 2..11 (the factors' magnitudes are
+// within 2^8 of each other), so the shift is one 32-bit funnel shift of the
+// low word and one arithmetic shift of the high word.
 template <bool POW2>
 __device__ __forceinline__ long long hfactor(long long c, int sh, long long d) {
-  if constexpr (POW2) return d >> sh;
-  else return __mul64hi(c, d);
-}
-
-// cx dx + cy dy + c1 p3 - c2 p4, each factor product's high half, as binary64.
-template <bool POW2>
-__device__ __forceinline__ double combine(long long cx, int shx, long long dx, long long cy, int shy, long long dy,
-                                          long long c1, long long p3, long long c2, long long p4, int Q) {
-  const long long s =
-      hfactor<POW2>(cx, shx, dx) + hfactor<POW2>(cy, shy, dy) + __mul64hi(c1, p3) - __mul64hi(c2, p4);
-  return fx64_to_double(s, Q);
+  if constexpr (POW2) {
+    const unsigned lo = static_cast<unsigned>(d);
+    const int hi = static_cast<int>(d >> 32);
+    return static_cast<long long>((static_cast<unsigned long long>(static_cast<unsigned>(hi >> sh)) << 32) |
+                                  __funnelshift_r(lo, static_cast<unsigned>(hi), sh));
+  } else {
+    return mh(c, d);
+  }
 }
 
 // 64 - log2(c) for c a positive power of two (the shift of hfactor), else -1.
@@ -247,98 +263,227 @@ __device__ __forceinline__ int pow2_shift(long long c) {
   return (c > 0 && (c & (c - 1)) == 0) ? 64 - (63 - __clzll(c)) : -1;
 }
 
-template <bool POW2>
-__global__ void __launch_bounds__(256, 4)
+// trunc(x 2^S) (toward zero) for |x| 2^S <= 2^61 and S <= 1000: zero and
+// subnormal inputs give 0, and quant(-x) = -quant(x).  The significand with
+// its leading bit at 62 is shifted right by 1085 - e - S >= 1 (clamped at
+// 63, which gives 0), then the sign is applied.
+__device__ __forceinline__ long long fx_trunc(double x, int S) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  const unsigned long long m = ((b & 0xfffffffffffffull) | (1ull << 52)) << 10;
+  const int r = min(1085 - e - S, 63);
+  const long long q = static_cast<long long>(m >> r);
+  const long long s = static_cast<long long>(b) >> 63;
+  return (q ^ s) - s;
+}
+
+// Tile geometry of the z-marching kernel: a CTA of 32 x BY threads owns a
+// 32 x BY column of cells and marches up a chunk of z planes.  Each plane of
+// u, v, w is quantised once, with its one-cell x/y margin (34 x (BY + 2)
+// values per field), into a ring of four plane slots in shared memory: the
+// cell at plane k reads slots k - 1, k, k + 1 while plane k + 2 is written
+// into the fourth and plane k + 3 is loaded into registers.
+template <int BY>
+struct AdvGeom {
+  static constexpr int BX = 32;
+  static constexpr int PX = BX + 2, PY = BY + 2, PL = PX * PY;  // one quantised field plane
+  static constexpr int NT = BX * BY;
+  static constexpr int NE = (PL + NT - 1) / NT;  // plane values a thread loads per field
+  static constexpr int kSlot = 3 * PL;            // u, v, w of one plane
+  static constexpr int kSmem = 4 * kSlot * 8;
+};
+constexpr int kAdvZcMax = 64;  // z planes per CTA at most (factor table size)
+
+// The fixed-point z march of one CTA.  FAST: the conversions leave the
+// integer pipes -- a value is quantised as trunc(x 2^S) by adding S to its
+// exponent field and converting to a 64-bit integer toward zero (the same
+// integer fx_trunc gives; valid for 0 <= S <= 1000), and a sum is converted
+// to binary64 (nearest) and scaled by 2^-Q through its exponent field (valid
+// for -960 <= Q <= 1022, where every nonzero result is normal).  B300 runs
+// these conversions on its FP64 pipe at about twice its multiply rate.
+template <bool POW2, int BY, bool FAST>
+__device__ __forceinline__ void advect_march(const double* __restrict__ u, const double* __restrict__ v,
+                                             const double* __restrict__ w, double* __restrict__ su,
+                                             double* __restrict__ sv, double* __restrict__ sw,
+                                             const double* __restrict__ tzc1, const double* __restrict__ tzc2,
+                                             double tcx, double tcy, int64_t nx, int64_t ny, int64_t sy, int64_t sz,
+                                             int64_t osy, int64_t osz, int64_t i0, int64_t j0, int64_t k0, int kn,
+                                             const AdvScales& sc, long long* zfac) {
+  using G = AdvGeom<BY>;
+  extern __shared__ long long adv_ring[];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * G::BX + tx;
+  const int64_t i = i0 + 1 + tx, j = j0 + 1 + ty;
+  const bool mine = i <= nx && j <= ny;
+  const int sadd = sc.S << 20;  // FAST: x 2^S through the high word's exponent field
+  const int qsub = sc.Q << 20;  // FAST: s 2^-Q likewise (s != 0: the exponent stays in range)
+  auto quant = [&](double x) -> long long {
+    if constexpr (FAST) return __double2ll_rz(__hiloint2double(__double2hiint(x) + sadd, __double2loint(x)));
+    else return fx_trunc(x, sc.S);
+  };
+  auto outv = [&](long long s) -> double {
+    if constexpr (FAST) {
+      const double d = __ll2double_rn(s);
+      const int hi = __double2hiint(d);  // 0 only for s = 0
+      return __hiloint2double(hi == 0 ? 0 : hi - qsub, __double2loint(d));
+    } else {
+      return fx64_to_double(s, sc.Q);
+    }
+  };
+  // the plane values this thread loads: offsets within a plane, validity
+  int64_t goff[G::NE];
+  int soff[G::NE];
+  bool ok[G::NE];
+#pragma unroll
+  for (int n = 0; n < G::NE; ++n) {
+    const int e = tid + n * G::NT;
+    const int xx = e % G::PX, yy = e / G::PX;
+    soff[n] = e < G::PL ? e : -1;
+    ok[n] = e < G::PL && i0 + xx <= nx + 1 && j0 + yy <= ny + 1;
+    goff[n] = (i0 + xx) + (j0 + yy) * sy;
+  }
+  double raw[3][G::NE];
+  auto load = [&](int p) {  // plane k0 + p of u, v, w into registers
+    const int64_t base = (k0 + p) * sz;
+#pragma unroll
+    for (int n = 0; n < G::NE; ++n) {
+      raw[0][n] = ok[n] ? __ldg(u + base + goff[n]) : 0.0;
+      raw[1][n] = ok[n] ? __ldg(v + base + goff[n]) : 0.0;
+      raw[2][n] = ok[n] ? __ldg(w + base + goff[n]) : 0.0;
+    }
+  };
+  auto store = [&](int p) {  // the registers, quantised, into plane p's slot
+    long long* d = adv_ring + (p & 3) * G::kSlot;
+#pragma unroll
+    for (int n = 0; n < G::NE; ++n) {
+      if (soff[n] >= 0) {
+        d[soff[n]] = quant(raw[0][n]);
+        d[G::PL + soff[n]] = quant(raw[1][n]);
+        d[2 * G::PL + soff[n]] = quant(raw[2][n]);
+      }
+    }
+  };
+  // planes k0 .. k0 + kn + 1 are read; the first three fill slots 0..2
+#pragma unroll 1
+  for (int p = 0; p < 3 && p <= kn + 1; ++p) {
+    load(p);
+    store(p);
+  }
+  if (3 <= kn + 1) load(3);
+  if (tid < 2 * kn) {
+    const int64_t k = k0 + 1 + (tid >> 1);
+    zfac[tid] = fx_quant((tid & 1) ? tzc2[k - 1] : tzc1[k - 1], sc.T);
+  }
+  const long long cx = fx_quant(tcx, sc.T), cy = fx_quant(tcy, sc.T);
+  const int shx = pow2_shift(cx), shy = pow2_shift(cy);
+  __syncthreads();
+  constexpr int DX = 1, DY = G::PX;
+  const int t = (ty + 1) * DY + tx + 1;
+#pragma unroll 1
+  for (int kk = 0; kk < kn; ++kk) {
+    // plane kk + 3 (in registers) into the slot that plane kk - 1 freed;
+    // plane kk + 4 starts loading
+    if (kk + 3 <= kn + 1) store(kk + 3);
+    if (kk + 4 <= kn + 1) load(kk + 4);
+    if (mine) {
+      const long long* Um = adv_ring + (kk & 3) * G::kSlot;  // plane k - 1
+      const long long* U0 = adv_ring + ((kk + 1) & 3) * G::kSlot;
+      const long long* Up = adv_ring + ((kk + 2) & 3) * G::kSlot;
+      const long long *Vm = Um + G::PL, *Wm = Um + 2 * G::PL;
+      const long long *V0 = U0 + G::PL, *W0 = U0 + 2 * G::PL;
+      const long long *Vp = Up + G::PL, *Wp = Up + 2 * G::PL;
+      const long long c1 = zfac[2 * kk], c2 = zfac[2 * kk + 1];
+      const long long u0 = U0[t], v0 = V0[t], w0 = W0[t];
+      const int64_t k = k0 + 1 + kk;
+      const int64_t o = i + j * osy + k * osz;
+      // su at (i+1/2, j, k); its x term um (u0 + um) - up (u0 + up) taken as
+      // (um - up)(u0 + um + up), exact in integers
+      {
+        const long long um = U0[t - DX], up = U0[t + DX];
+        const long long dx = mh(um - up, u0 + um + up);
+        const long long dy = mh(U0[t - DY], V0[t - DY] + V0[t - DY + DX]) - mh(U0[t + DY], v0 + V0[t + DX]);
+        const long long p3 = mh(Um[t], Wm[t] + Wm[t + DX]);
+        const long long p4 = mh(Up[t], w0 + W0[t + DX]);
+        su[o] = outv(hfactor<POW2>(cx, shx, dx) + hfactor<POW2>(cy, shy, dy) + mh(c1, p3) - mh(c2, p4));
+      }
+      // sv at (i, j+1/2, k)
+      {
+        const long long vm = V0[t - DY], vp = V0[t + DY];
+        const long long dx = mh(V0[t - DX], U0[t - DX] + U0[t - DX + DY]) - mh(V0[t + DX], u0 + U0[t + DY]);
+        const long long dy = mh(vm - vp, v0 + vm + vp);
+        const long long p3 = mh(Vm[t], Wm[t] + Wm[t + DY]);
+        const long long p4 = mh(Vp[t], w0 + W0[t + DY]);
+        sv[o] = outv(hfactor<POW2>(cx, shx, dx) + hfactor<POW2>(cy, shy, dy) + mh(c1, p3) - mh(c2, p4));
+      }
+      // sw at (i, j, k+1/2)
+      {
+        const long long wm = Wm[t], wp = Wp[t];
+        const long long dx = mh(W0[t - DX], U0[t - DX] + Up[t - DX]) - mh(W0[t + DX], u0 + Up[t]);
+        const long long dy = mh(W0[t - DY], V0[t - DY] + Vp[t - DY]) - mh(W0[t + DY], v0 + Vp[t]);
+        const long long p3 = mh(wm, w0 + wm);
+        const long long p4 = mh(wp, w0 + wp);
+        sw[o] = outv(hfactor<POW2>(cx, shx, dx) + hfactor<POW2>(cy, shy, dy) + mh(c1, p3) - mh(c2, p4));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <bool POW2, int BY, int MINB, bool FASTCVT>
+__global__ void __launch_bounds__(32 * BY, MINB)
     advect_kernel(const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ w,
                   double* __restrict__ su, double* __restrict__ sv, double* __restrict__ sw,
                   const double* __restrict__ tzc1, const double* __restrict__ tzc2, double tcx, double tcy,
                   int64_t nx, int64_t ny, int64_t nz, int64_t sy, int64_t sz, int64_t osy, int64_t osz,
-                  const unsigned long long* __restrict__ range) {
-  extern __shared__ long long adv_tile[];
-  __shared__ long long zfac[2 * kAdvZT];  // tzc1, tzc2 of the tile's planes at scale T
+                  int zc, const unsigned long long* __restrict__ range) {
+  __shared__ long long zfac[2 * kAdvZcMax];  // tzc1, tzc2 of the chunk's planes at scale T
   const AdvScales sc = adv_scales(range);
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kAdvBX;  // halo index of the tile's first cell
-  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * kAdvBY;
-  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * kAdvZT;
-  const int64_t i = i0 + 1 + threadIdx.x, j = j0 + 1 + threadIdx.y;
-  if (!sc.fixed) {
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;  // halo index of the plane box's first column
+  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * BY;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * zc;
+  const int kn = static_cast<int>(min(static_cast<int64_t>(zc), nz - k0));  // cells of this chunk along z
+  if (!sc.fixed) {  // uniform over the launch
+    const int64_t i = i0 + 1 + threadIdx.x, j = j0 + 1 + threadIdx.y;
     if (i > nx || j > ny) return;
-    for (int kk = 0; kk < kAdvZT; ++kk) {
+    for (int kk = 0; kk < kn; ++kk) {
       const int64_t k = k0 + 1 + kk;
-      if (k > nz) break;
       const int64_t o = i + j * osy + k * osz;
       advect_cell_f64(u, v, w, i + j * sy + k * sz, sy, sz, tcx, tcy, tzc1[k - 1], tzc2[k - 1], su[o], sv[o],
                       sw[o]);
     }
     return;
   }
-  long long* U = adv_tile;
-  long long* V = adv_tile + kTile;
-  long long* W = adv_tile + 2 * kTile;
-  for (int t = threadIdx.y * kAdvBX + threadIdx.x; t < kTile; t += kAdvBX * kAdvBY) {
-    const int xx = t % kTX, yy = (t / kTX) % kTY, zz = t / (kTX * kTY);
-    const int64_t gi = i0 + xx, gj = j0 + yy, gk = k0 + zz;
-    long long qu = 0, qv = 0, qw = 0;
-    if (gi <= nx + 1 && gj <= ny + 1 && gk <= nz + 1) {
-      const int64_t c = gi + gj * sy + gk * sz;
-      qu = fx_quant(u[c], sc.S);
-      qv = fx_quant(v[c], sc.S);
-      qw = fx_quant(w[c], sc.S);
-    }
-    U[t] = qu;
-    V[t] = qv;
-    W[t] = qw;
-  }
-  {
-    const int t = threadIdx.y * kAdvBX + threadIdx.x;
-    if (t < 2 * kAdvZT) {
-      const int64_t k = k0 + 1 + (t >> 1);
-      zfac[t] = k <= nz ? fx_quant((t & 1) ? tzc2[k - 1] : tzc1[k - 1], sc.T) : 0;
-    }
-  }
-  __syncthreads();
-  if (i > nx || j > ny) return;
-  const long long cx = fx_quant(tcx, sc.T), cy = fx_quant(tcy, sc.T);
-  const int shx = pow2_shift(cx), shy = pow2_shift(cy);
-  constexpr int DX = 1, DY = kTX, DZ = kTX * kTY;
-  for (int kk = 0; kk < kAdvZT; ++kk) {
-    const int64_t k = k0 + 1 + kk;
-    if (k > nz) break;
-    const long long c1 = zfac[2 * kk], c2 = zfac[2 * kk + 1];
-    const int t = (kk + 1) * DZ + (threadIdx.y + 1) * DY + (threadIdx.x + 1);
-    const long long u0 = U[t], v0 = V[t], w0 = W[t];
-    const int64_t o = i + j * osy + k * osz;
-    // su at (i+1/2, j, k)
-    {
-      const long long um = U[t - DX], up = U[t + DX];
-      const long long dx = flux(um, u0, um, up, u0, up);
-      const long long dy = flux(U[t - DY], V[t - DY], V[t - DY + DX], U[t + DY], v0, V[t + DX]);
-      const long long p3 = prod(U[t - DZ], W[t - DZ], W[t - DZ + DX]);
-      const long long p4 = prod(U[t + DZ], w0, W[t + DX]);
-      su[o] = combine<POW2>(cx, shx, dx, cy, shy, dy, c1, p3, c2, p4, sc.Q);
-    }
-    // sv at (i, j+1/2, k)
-    {
-      const long long vm = V[t - DY], vp = V[t + DY];
-      const long long dx = flux(V[t - DX], U[t - DX], U[t - DX + DY], V[t + DX], u0, U[t + DY]);
-      const long long dy = flux(vm, v0, vm, vp, v0, vp);
-      const long long p3 = prod(V[t - DZ], W[t - DZ], W[t - DZ + DY]);
-      const long long p4 = prod(V[t + DZ], w0, W[t + DY]);
-      sv[o] = combine<POW2>(cx, shx, dx, cy, shy, dy, c1, p3, c2, p4, sc.Q);
-    }
-    // sw at (i, j, k+1/2)
-    {
-      const long long wm = W[t - DZ], wp = W[t + DZ];
-      const long long dx = flux(W[t - DX], U[t - DX], U[t - DX + DZ], W[t + DX], u0, U[t + DZ]);
-      const long long dy = flux(W[t - DY], V[t - DY], V[t - DY + DZ], W[t + DY], v0, V[t + DZ]);
-      const long long p3 = prod(wm, w0, wm);
-      const long long p4 = prod(wp, w0, wp);
-      sw[o] = combine<POW2>(cx, shx, dx, cy, shy, dy, c1, p3, c2, p4, sc.Q);
-    }
-  }
+  if (FASTCVT && sc.S >= 0 && sc.S <= 1000 && sc.Q >= -960 && sc.Q <= 1022)
+    advect_march<POW2, BY, FASTCVT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0, j0,
+                                    k0, kn, sc, zfac);
+  else
+    advect_march<POW2, BY, false>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0, j0, k0,
+                                  kn, sc, zfac);
 }
 
+// Compiled tile shapes (thread rows BY, CTAs per SM); index 0 is the
+// default.  Measured at 512 x 512 x 256 they are within 5% of each other.
+using AdvKernel = void (*)(const double*, const double*, const double*, double*, double*, double*, const double*,
+                           const double*, double, double, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
+                           int64_t, int, const unsigned long long*);
+struct AdvVariant {
+  int BY, minb;
+  AdvKernel kern[2];  // tcx, tcy general / powers of two
+  int smem;
+};
+#define STENCIL_ADV_VARIANT(BY, MINB) \
+  {BY, MINB, {advect_kernel<false, BY, MINB, true>, advect_kernel<true, BY, MINB, true>}, AdvGeom<BY>::kSmem}
+const AdvVariant kAdvVariants[] = {
+    STENCIL_ADV_VARIANT(8, 3),
+    STENCIL_ADV_VARIANT(8, 4),
+    STENCIL_ADV_VARIANT(4, 6),
+    STENCIL_ADV_VARIANT(16, 2),
+};
+#undef STENCIL_ADV_VARIANT
+constexpr int kNumAdvVariants = sizeof(kAdvVariants) / sizeof(kAdvVariants[0]);
+
 }  // namespace
+
+int advect_config_count() { return kNumAdvVariants; }
 
 int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w, const Grid& su,
                   const Grid& sv, const Grid& sw, const double* tzc1, const double* tzc2,
@@ -347,8 +492,15 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
     return set_error(STENCIL_ERR_ARG, "advect: u, v, w must share strides");
   if (su.sy != sv.sy || su.sy != sw.sy || su.sz != sv.sz || su.sz != sw.sz)
     return set_error(STENCIL_ERR_ARG, "advect: su, sv, sw must share strides");
-  const int64_t gy = (u.ny + kAdvBY - 1) / kAdvBY, gz = (u.nz + kAdvZT - 1) / kAdvZT;
-  if (gy > 65535 || gz > 65535) return set_error(STENCIL_ERR_ARG, "advect: grid too large");
+  const AdvVariant& av =
+      kAdvVariants[(ctx->advect_choice >= 0 && ctx->advect_choice < kNumAdvVariants) ? ctx->advect_choice : 0];
+  const int64_t gx = (u.nx + 31) / 32, gy = (u.ny + av.BY - 1) / av.BY;
+  // z chunk: the longest (up to 32 planes) that still gives every SM several
+  // CTAs to interleave
+  int zc = 32;
+  while (zc > 4 && gx * gy * ((u.nz + zc - 1) / zc) < int64_t(4) * av.minb * ctx->num_sms) zc /= 2;
+  const int64_t gz = (u.nz + zc - 1) / zc;
+  if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return set_error(STENCIL_ERR_ARG, "advect: grid too large");
   unsigned long long* range = reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchAdvRange);
   int rc = check_cuda(cudaMemsetAsync(range, 0, 4 * sizeof(unsigned long long), st), "advect range init");
   if (!rc) rc = check_cuda(cudaMemsetAsync(range + 4, 0xff, sizeof(unsigned long long), st), "advect range init");
@@ -368,17 +520,16 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
     return c > 0.0 && std::frexp(c, &e) == 0.5 && e > -900 && e < 900;
   };
   const bool p2 = pow2(tcx) && pow2(tcy);
-  auto kern = p2 ? advect_kernel<true> : advect_kernel<false>;
-  rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kAdvSmem),
+  auto kern = av.kern[p2 ? 1 : 0];
+  rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, av.smem),
                   "advect smem attribute");
   if (rc) return rc;
-  const dim3 block(kAdvBX, kAdvBY);
-  const dim3 grid(static_cast<unsigned>((u.nx + kAdvBX - 1) / kAdvBX), static_cast<unsigned>(gy),
-                  static_cast<unsigned>(gz));
-  kern<<<grid, block, kAdvSmem, st>>>(
+  const dim3 block(32, av.BY);
+  const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(gz));
+  kern<<<grid, block, av.smem, st>>>(
       static_cast<const double*>(u.data), static_cast<const double*>(v.data),
       static_cast<const double*>(w.data), static_cast<double*>(su.data), static_cast<double*>(sv.data),
-      static_cast<double*>(sw.data), tzc1, tzc2, tcx, tcy, u.nx, u.ny, u.nz, u.sy, u.sz, su.sy, su.sz, range);
+      static_cast<double*>(sw.data), tzc1, tzc2, tcx, tcy, u.nx, u.ny, u.nz, u.sy, u.sz, su.sy, su.sz, zc, range);
   return check_cuda(cudaGetLastError(), "advect kernel");
 }
 

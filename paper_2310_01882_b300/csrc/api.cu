@@ -385,6 +385,21 @@ int stencil_residual_config_select(stencil_ctx* ctx, int32_t index) {
   return STENCIL_OK;
 }
 
+int stencil_advect_config_count(int32_t* count) {
+  if (!count) return set_error(STENCIL_ERR_ARG, "advect_config_count: null count");
+  *count = advect_config_count();
+  return STENCIL_OK;
+}
+
+int stencil_advect_config_select(stencil_ctx* ctx, int32_t index) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "advect_config_select: null ctx");
+  const int n = advect_config_count();
+  if (index < 0 || index >= n)
+    return set_error(STENCIL_ERR_ARG, "advect_config_select: index %d out of range (%d configurations)", index, n);
+  ctx->advect_choice = index;
+  return STENCIL_OK;
+}
+
 int stencil_redblack_config_select(stencil_ctx* ctx, int32_t dtype, int32_t flags, int32_t with_work,
                                    int32_t sweeps_per_pass, int32_t index) {
   if (!ctx) return set_error(STENCIL_ERR_ARG, "redblack_config_select: null ctx");

@@ -24,6 +24,7 @@ struct stencil_ctx {
   // red-black configuration index per policy and colour stages per pass
   int rb_choice[stencil::kNumPolicies][stencil::kMaxPass + 1];
   int resid_choice;  // fixed-point residual configuration index
+  int advect_choice; // advection tile configuration index
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)
@@ -121,5 +122,6 @@ int launch_residual(stencil_ctx* ctx, const Grid& u, const Grid& f, double h, co
 int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w, const Grid& su,
                   const Grid& sv, const Grid& sw, const double* tzc1, const double* tzc2,
                   double tcx, double tcy, cudaStream_t st);
+int advect_config_count();
 
 }  // namespace stencil

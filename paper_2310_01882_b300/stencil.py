@@ -86,6 +86,8 @@ SIGNATURES = {
                                         ctypes.c_int32], ctypes.c_int),
     "stencil_residual_config_count": ([ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "stencil_residual_config_select": ([_P, ctypes.c_int32], ctypes.c_int),
+    "stencil_advect_config_count": ([ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "stencil_advect_config_select": ([_P, ctypes.c_int32], ctypes.c_int),
     "wsnet_create": ([ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                       ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "wsnet_destroy": ([_P], ctypes.c_int),
@@ -298,6 +300,16 @@ def stencil_residual_config_count():
 
 def stencil_residual_config_select(ctx, index):
     return _check(lib().stencil_residual_config_select(ctx.handle, int(index)))
+
+
+def stencil_advect_config_count():
+    c = ctypes.c_int32(0)
+    _check(lib().stencil_advect_config_count(ctypes.byref(c)))
+    return c.value
+
+
+def stencil_advect_config_select(ctx, index):
+    return _check(lib().stencil_advect_config_select(ctx.handle, int(index)))
 
 
 def stencil_residual(ctx, u, f, h, norms_dev, r=None, stream=None):

@@ -145,6 +145,35 @@ def test_advect_parity(shape):
         assert rel_err(g, r) <= 1e-13
 
 
+def test_advect_every_config():
+    """Each compiled tile configuration of the fixed-point kernel (pinned
+    with advect_config_select) matches the oracle: ragged x/y tiles, several
+    z chunks, tcy not a power of two (the multiplied factor path) and a
+    power of two (the shifted one)."""
+    import torch
+    from paper_2310_01882_b300.stencil import Context
+    count = S.stencil_advect_config_count()
+    assert count >= 1
+    nx, ny, nz = 45, 37, 70
+    u, v, w = inputs.winds(nx, ny, nz, seeds=(41, 42, 43))
+    t1, t2 = inputs.tzc(nz, 7), inputs.tzc(nz, 8)
+    d1, d2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
+    fu, fv, fw = (S.Field.from_numpy(a) for a in (u, v, w))
+    for tcy in (0.25, 0.3):
+        ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, tcy)
+        for idx in range(count):
+            c = Context(0)
+            S.stencil_advect_config_select(c, idx)
+            outs = [fu.like() for _ in range(3)]
+            S.stencil_advect_uvw(c, fu, fv, fw, *outs, d1, d2, 0.25, tcy)
+            torch.cuda.synchronize()
+            for o, r in zip(outs, ref):
+                assert rel_err(o.to_numpy(), r) <= 1e-13, (idx, tcy)
+            with pytest.raises(S.StencilError):
+                S.stencil_advect_config_select(c, count)
+            c.close()
+
+
 def test_advect_full_size():
     """512 x 512 x 256, winds per the benchmark recipe, oracle on all cores."""
     u, v, w = inputs.winds(512, 512, 256)
