@@ -12,13 +12,15 @@
 //    averages, finite differences with their denominators folded out):
 //    64-bit fixed point.  The input is converted at one scale 2^-S per call
 //    (S from max|in| and sum |k_p|, so no sum can overflow), sum k_p q_p is
-//    exact and rounded to binary64 once, times 2^E.  A z-marching kernel:
-//    each CTA owns a 32 x 8 column of outputs and keeps the 2R + 1 input
-//    planes the offsets reach, with their x/y margins, in shared memory as
-//    fixed-point integers; every loaded plane is written to two slots of a
-//    doubled ring, so the planes z - R .. z + R always sit in consecutive
-//    slots and each term's shared-memory offset is one constant, whatever
-//    the offsets are.  Each input value is read from HBM and converted once.
+//    exact and rounded to binary64 once, times 2^E.  Stars (the centre and
+//    +-1..R along each axis: Laplacians of every order) run a z march that
+//    keeps each thread's own column in registers (apply_star_march); other
+//    offset sets a z march that keeps the 2R + 1 input planes the offsets
+//    reach, with their x/y margins, in shared memory as fixed-point
+//    integers; every loaded plane is written to two slots of a doubled
+//    ring, so the planes z - R .. z + R always sit in consecutive slots and
+//    each term's shared-memory offset is one constant, whatever the offsets
+//    are.  Either way each input value is read from HBM and converted once.
 //  * any other coefficients: binary64, each product rounded then added in
 //    the listed order (no fused multiply-add): bitwise the definition; one
 //    thread per point, neighbours through L1 (bound by the FP64 pipe).
@@ -199,6 +201,209 @@ __device__ __forceinline__ void apply_fx_march(const double* __restrict__ in, do
   }
 }
 
+// Asynchronous 8-byte global -> shared copies (zero-filled when !valid),
+// committed in groups; a thread waits only for its own copies.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The star of radius R (SHAPE 1), z march with the z terms in registers.
+// A CTA of 32 x 8 threads owns a 32 x 16 column of outputs (two rows per
+// thread, rows ty and ty + 8).  Input planes, with their x/y
+// margin of R cells, stream into a ring of kApStarDepth raw planes in shared
+// memory by asynchronous copies issued kApStarDepth - 1 planes ahead (each
+// thread copies, then converts, the same cells, so only its own copies need
+// waiting for).  Each plane is quantised once into a ring of R + 2 slots in
+// pre-split form q = H 2^31 + L (0 <= L < 2^31, H signed 32-bit, one 64-bit
+// word), and each thread keeps its own column's values of the 2R + 1 planes
+// its z terms read in a register window (rotated by an unrolled loop, no
+// moves).  Step p converts plane p, passes one CTA barrier, takes its own
+// value of plane p into the window and computes output plane p - R: its z
+// terms from the window, its x and y terms from that plane's slot.  The sum
+// is two exact 64-bit dot products, sum k_p L_p and sum k_p H_p (one
+// 32 x 32 -> 64-bit multiply-add per term each), recombined as
+// (sum k H) 2^31 + sum k L.  The quantised slot written at step p + 1 held
+// plane p - R - 1, last read before step p's barrier.  FASTQ: a thread's
+// first cell of a plane is quantised by adding S to its exponent field and
+// converting to the nearest integer on the FP64 pipe (valid for
+// 0 <= S <= 1000), its other cells by fx_quant_signed in integer
+// instructions (the two pipes share the work); both give round(x 2^S) up to
+// the rounding of an exact half.
+constexpr int kApStarDepth = 6;
+constexpr int kApStarRows = 2;  // output rows per thread: the tile is 32 x 16
+template <int R>
+struct ApStar {
+  static constexpr int ROWS = kApStarRows, TY = kApBY * ROWS;  // tile rows
+  static constexpr int WX = kApBX + 2 * R, WY = TY + 2 * R, PL = WX * WY, NS = R + 2, NW = 2 * R + 1;
+  static constexpr int NT = kApBX * kApBY, NL = (PL + NT - 1) / NT, D = kApStarDepth;
+  static constexpr int kSmem = (NS + D) * PL * 8;
+};
+
+// d = a b + c with a, b signed 32-bit and c, d 64-bit (one wide multiply-add).
+__device__ __forceinline__ long long madw(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long lds64(uint32_t a) {
+  unsigned long long v;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double lds64f(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts64(uint32_t a, unsigned long long v) {
+  asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+template <int R, bool FASTQ, bool EXACT_EXP>
+__device__ __forceinline__ void apply_star_march(const double* __restrict__ in, double* __restrict__ out,
+                                                 int64_t nx, int64_t ny, int64_t nz, int64_t sy, int64_t sz,
+                                                 int64_t osy, int64_t osz, const FxTerms& t, int S, int Cu, int sh,
+                                                 bool bad, int zchunk) {
+  using G = ApStar<R>;
+  constexpr int WX = G::WX, PL = G::PL, NS = G::NS, NW = G::NW, NT = G::NT, NL = G::NL, D = G::D;
+  constexpr uint32_t kPlaneBytes = PL * 8;
+  using Sh = ApShape<1, R>;
+  extern __shared__ long long ap_win[];  // NS slots of PL pre-split values, then D raw planes
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kApBX + tx;
+  const int64_t ox = R + static_cast<int64_t>(blockIdx.x) * kApBX;  // first output column of the tile
+  const int64_t oy = R + static_cast<int64_t>(blockIdx.y) * G::TY;
+  const int64_t zs = R + static_cast<int64_t>(blockIdx.z) * zchunk;
+  const int64_t ze = min(zs + zchunk - 1, nz + 1 - R);
+  constexpr int ROWS = G::ROWS;
+  const int64_t i = ox + tx;
+  bool owner[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) owner[r] = i <= nx + 1 - R && oy + ty + r * kApBY <= ny + 1 - R;
+  const int nplanes = static_cast<int>(ze - zs) + 1 + 2 * R;  // input planes zs - R .. ze + R
+  // this thread's cells of every plane: source pointers (advanced a plane at
+  // a time), validity, and shared-memory byte offsets
+  const double* src[NL];
+  bool gin[NL];
+#pragma unroll
+  for (int m = 0; m < NL; ++m) {
+    const int c = tid + m * NT;
+    const int cy = c / WX, cx = c - cy * WX;
+    const int64_t gi = ox - R + cx, gj = oy - R + cy;
+    gin[m] = c < PL && gi <= nx + 1 && gj <= ny + 1;  // gi, gj >= 0 always (ox, oy >= R)
+    src[m] = in + (gin[m] ? gi + gj * sy + (zs - R) * sz : 0);
+  }
+  const uint32_t qbase = smem_addr(ap_win);               // quantised ring, slot 0
+  const uint32_t rbase = qbase + NS * kPlaneBytes;         // raw ring, slot 0
+  const uint32_t mine8 = static_cast<uint32_t>(tid) * 8;  // byte offset of cell tid in a plane
+  const uint32_t own8 = static_cast<uint32_t>((ty + R) * WX + (tx + R)) * 8;  // row r: + r * 8 WX * 8
+  const int sadd = S << 20;
+  auto quant = [&](double x) -> long long {
+    if constexpr (FASTQ) return __double2ll_rn(__hiloint2double(__double2hiint(x) + sadd, __double2loint(x)));
+    else return fx_quant_signed(x, Cu);
+  };
+  // plane n (0-based from zs - R) into raw slot rslot (an empty group past the end)
+  auto issue = [&](int n, uint32_t rslot) {
+    if (n < nplanes) {
+#pragma unroll
+      for (int m = 0; m < NL; ++m) {
+        if (m + 1 < NL || tid + m * NT < PL)
+          cp_async8(rslot + mine8 + m * NT * 8, gin[m] ? src[m] : in, gin[m]);
+        src[m] += sz;
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < D - 1; ++d) issue(d, rbase + d * kPlaneBytes);
+  int WL[ROWS][NW], WH[ROWS][NW];  // own columns: plane n's pre-split value in window slot n mod NW
+  double* dst = out + i + (oy + ty) * osy + zs * osz;  // row r: + r * 8 osy
+  uint32_t qslot = qbase;                               // quantised slot of plane n
+  uint32_t rslot = rbase;                               // raw slot of plane n
+  uint32_t rnext = rbase + (D - 1) * kPlaneBytes;       // raw slot of plane n + D - 1
+  const uint32_t qend = qbase + NS * kPlaneBytes, rend = rbase + D * kPlaneBytes;
+  int n = 0;
+  for (;;) {
+#pragma unroll
+    for (int rot = 0; rot < NW; ++rot) {
+      if (n >= nplanes) return;
+      issue(n + D - 1, rnext);  // into plane n - 1's raw slot (converted by this thread)
+      cp_async_wait<D - 1>();   // plane n's copies (this thread's) have landed
+#pragma unroll
+      for (int m = 0; m < NL; ++m) {
+        if (m + 1 < NL || tid + m * NT < PL) {
+          // FASTQ: the first cell through the FP64 pipe's conversion, the
+          // others in integer instructions (balances the two pipes)
+          const double x = lds64f(rslot + mine8 + m * NT * 8);
+          const long long q = (FASTQ && m == 0) ? quant(x) : fx_quant_signed(x, Cu);
+          sts64(qslot + mine8 + m * NT * 8,
+                (static_cast<unsigned long long>(static_cast<unsigned>(static_cast<int>(q >> 31))) << 32) |
+                    static_cast<unsigned>(q & 0x7fffffff));
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const unsigned long long v = lds64(qslot + own8 + r * kApBY * WX * 8);
+        WL[r][rot] = static_cast<int>(v);
+        WH[r][rot] = static_cast<int>(v >> 32);
+      }
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+      if (n >= 2 * R && owner[r]) {
+        // output plane zs + n - 2R: its window slot is rot - R, its ring slot R back
+        const uint32_t ws = qslot >= qbase + R * kPlaneBytes ? qslot - R * kPlaneBytes
+                                                             : qslot + (NS - R) * kPlaneBytes;
+        // two accumulators per half (terms alternate), so the multiply-add
+        // chains are half as long
+        long long aL[2] = {0, 0}, aH[2] = {0, 0};
+#pragma unroll
+        for (int q = 0; q < Sh::N; ++q) {
+          const int dz = Sh::d(q, 2);
+          int l, h;
+          if (dz != 0 || q == 0) {
+            const int wi = ((rot - R + dz) % NW + NW) % NW;
+            l = WL[r][wi];
+            h = WH[r][wi];
+          } else {
+            const unsigned long long v =
+                lds64(ws + own8 + static_cast<uint32_t>((r * kApBY * WX + Sh::d(q, 1) * WX + Sh::d(q, 0)) * 8));
+            l = static_cast<int>(v);
+            h = static_cast<int>(v >> 32);
+          }
+          aL[q & 1] = madw(t.k[q], l, aL[q & 1]);
+          aH[q & 1] = madw(t.k[q], h, aH[q & 1]);
+        }
+        const long long acc = (aH[0] + aH[1]) * (1ll << 31) + (aL[0] + aL[1]);
+        double vout;
+        if (bad) {
+          vout = __longlong_as_double(0x7ff8000000000000ll);
+        } else if (acc == 0) {
+          vout = 0.0;
+        } else if constexpr (EXACT_EXP) {
+          vout = __longlong_as_double(__double_as_longlong(__ll2double_rn(acc)) + (static_cast<long long>(sh) << 52));
+        } else {
+          vout = ldexp(__ll2double_rn(acc), sh);
+        }
+        dst[r * kApBY * osy] = vout;
+      }
+      }
+      if (n >= 2 * R) dst += osz;
+      qslot += kPlaneBytes;
+      if (qslot == qend) qslot = qbase;
+      rnext = rslot;
+      rslot += kPlaneBytes;
+      if (rslot == rend) rslot = rbase;
+      ++n;
+    }
+  }
+}
+
 template <int R, int SHAPE>
 __global__ void __launch_bounds__(kApBX * kApBY)
     apply_fx_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
@@ -226,6 +431,45 @@ __global__ void __launch_bounds__(kApBX * kApBY)
     apply_fx_march<R, SHAPE, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
   else
     apply_fx_march<R, SHAPE, false>(in, out, nx, ny, nz, sy, sz, osy, osz, t, 1085 - S, sh, bad != 0, zchunk);
+}
+
+// Scale of a fixed-point apply (the same in every thread): sum |k_p|
+// max|in| 2^S <= 2^61, so every partial sum stays below 2^62.  bad: 1 for a
+// non-finite input, 2 for a magnitude the exponent range cannot scale.
+__device__ __forceinline__ int apply_scale(const unsigned long long* maxbits, double sumk, int* bad) {
+  const double mx = __longlong_as_double(static_cast<long long>(maxbits[0]));
+  int S = 0;
+  *bad = 0;
+  if (!(mx <= 1.0e300)) {
+    *bad = 1;
+  } else {
+    int e = 0;
+    if (mx > 0.0) frexp(mx * sumk, &e);
+    S = 61 - e;
+    if (S > 1022) S = 1022;
+    if (S < -900) *bad = 2;
+  }
+  return S;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kApBX * kApBY, 3)
+    apply_star_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
+                      int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ FxTerms t,
+                      const unsigned long long* __restrict__ maxbits, uint32_t* status, int zchunk) {
+  int bad = 0;
+  const int S = apply_scale(maxbits, t.sumk, &bad);
+  if (bad && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    atomicOr(status, bad == 1 ? kStatusNonFinite : kStatusRange);
+  const int sh = t.E - S;  // out = sum 2^sh; the sum's exponent is 0..61
+  const bool exact_exp = sh >= -1022 && sh <= 962;
+  const bool fastq = S >= 0 && S <= 1000;
+  if (fastq && exact_exp)
+    apply_star_march<R, true, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk);
+  else if (exact_exp)
+    apply_star_march<R, false, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk);
+  else
+    apply_star_march<R, false, false>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk);
 }
 
 // c = k 2^e with k an odd integer (c != 0): the exact decomposition.
@@ -320,6 +564,27 @@ int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const
       if (rc) return rc;
       const int64_t ox = in.nx + 2 - 2 * r, oy = in.ny + 2 - 2 * r, oz = in.nz + 2 - 2 * r;  // output extents
       const int64_t tiles = ((ox + kApBX - 1) / kApBX) * ((oy + kApBY - 1) / kApBY);
+      if (shape == 1) {
+        // stars: the register-window march; z chunks as long as still give
+        // every SM several CTAs (each chunk re-reads 2R planes)
+        const int64_t stiles = ((ox + kApBX - 1) / kApBX) * ((oy + kApBY * kApStarRows - 1) / (kApBY * kApStarRows));
+        int64_t zcs = 64;
+        while (zcs > 8 && stiles * ((oz + zcs - 1) / zcs) < int64_t(6) * ctx->num_sms) zcs /= 2;
+        zcs = std::min<int64_t>(zcs, oz);
+        const int64_t sty = kApBY * kApStarRows;
+        const dim3 sgrid(static_cast<unsigned>((ox + kApBX - 1) / kApBX), static_cast<unsigned>((oy + sty - 1) / sty),
+                         static_cast<unsigned>((oz + zcs - 1) / zcs));
+        if (sgrid.y > 65535 || sgrid.z > 65535) return set_error(STENCIL_ERR_ARG, "apply_linear: grid too large");
+        const int ssmem = R == 1 ? ApStar<1>::kSmem : (R == 2 ? ApStar<2>::kSmem : ApStar<3>::kSmem);
+        auto skern = R == 1 ? apply_star_kernel<1> : (R == 2 ? apply_star_kernel<2> : apply_star_kernel<3>);
+        rc = check_cuda(cudaFuncSetAttribute(skern, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem),
+                        "apply smem attribute");
+        if (rc) return rc;
+        skern<<<sgrid, dim3(kApBX, kApBY), ssmem, st>>>(
+            static_cast<const double*>(in.data), static_cast<double*>(out.data), in.nx, in.ny, in.nz, in.sy, in.sz,
+            out.sy, out.sz, t, mb, reinterpret_cast<uint32_t*>(ctx->scratch + kScratchStatus), static_cast<int>(zcs));
+        return check_cuda(cudaGetLastError(), "apply_linear star kernel");
+      }
       // z chunks: about 8 CTAs per SM in total, each chunk at least 8 planes
       int64_t zc = std::max<int64_t>(8, (oz * tiles + 8 * ctx->num_sms - 1) / (8 * ctx->num_sms));
       zc = std::min<int64_t>(zc, oz);
