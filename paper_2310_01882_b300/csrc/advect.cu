@@ -33,8 +33,8 @@
 // slots, and each thread computes su, sv, sw of its cell from the three
 // slots around it -- one CTA barrier per plane.  48 algorithmic bytes per
 // cell (three fields in, three out).  The quantisation and the final
-// rounding run as 64-bit conversions, which B300 issues on its FP64 pipe at
-// about twice its multiply rate, so the integer pipes keep the products.
+// rounding run as 64-bit conversions on B300's FP64 pipe (about two per
+// clock per SM), so the integer pipes keep the products.
 // (Computing sw in binary64 on the FP64 pipe while su and sv use the
 // integer pipes was measured slower: 21 binary64 operations per cell keep
 // that pipe busy on their own.)
@@ -300,7 +300,7 @@ constexpr int kAdvZcMax = 64;  // z planes per CTA at most (factor table size)
 // integer fx_trunc gives; valid for 0 <= S <= 1000), and a sum is converted
 // to binary64 (nearest) and scaled by 2^-Q through its exponent field (valid
 // for -960 <= Q <= 1022, where every nonzero result is normal).  B300 runs
-// these conversions on its FP64 pipe at about twice its multiply rate.
+// these conversions on its FP64 pipe, about two per clock per SM.
 template <bool POW2, int BY, bool FAST>
 __device__ __forceinline__ void advect_march(const double* __restrict__ u, const double* __restrict__ v,
                                              const double* __restrict__ w, double* __restrict__ su,
