@@ -394,7 +394,11 @@ def run_ours(args, rank, world, local_rank):
     if args.only in ("f32", "bf16"):
         dt = S.F32 if args.only == "f32" else S.BF16
         u, ut, f = fields(dt)
-        rep = "" if args.no_tune else S.stencil_autotune_sweep(ctx, u, ut, f, None, h)
+        if args.config is not None:  # pin one compiled configuration (profiling)
+            S.stencil_sweep_config_select(ctx, dt, 0, False, args.spp or 1, args.config)
+            rep = ""
+        else:
+            rep = "" if args.no_tune else S.stencil_autotune_sweep(ctx, u, ut, f, None, h)
         ms = timed_steps(lambda: S.stencil_jacobi_sweep(ctx, u, ut, f, None, h, SWEEPS, args.spp, 0), args.steps,
                          args.warmup)
         S.stencil_ctx_status(ctx)
@@ -881,6 +885,8 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "f64", "f32", "bf16", "advect", "wsnet", "batch", "redblack", "residual", "apply"],
                     help="run one dtype's step only (profiling runs)")
     ap.add_argument("--spp", type=int, default=0, help="sweeps per pass for --only runs (0 = library default)")
+    ap.add_argument("--config", type=int, default=None,
+                    help="--only f32/bf16: configuration index at --spp sweeps per pass (default: autotune)")
     ap.add_argument("--advect-config", type=int, default=None,
                     help="advection configuration index for --only advect (default: time all, keep the fastest)")
     ap.add_argument("--resid-config", type=int, default=None,
