@@ -27,11 +27,11 @@
 // decision is taken on the device from the range reduction: the call stays
 // asynchronous).
 //
-// Each CTA owns a 32 x BY column of cells and marches up a chunk of z
-// planes: every plane of u, v, w is loaded once (coalesced, one plane ahead
-// in registers), quantised once into a ring of four shared-memory plane
-// slots, and each thread computes su, sv, sw of its cell from the three
-// slots around it -- one CTA barrier per plane.  48 algorithmic bytes per
+// Each CTA owns a 32 x (RPT BY) column of cells and marches up a chunk of
+// z planes: every plane of u, v, w is loaded once (coalesced, one plane
+// ahead in registers), quantised once into a ring of four shared-memory
+// plane slots, and each thread computes su, sv, sw of its RPT cells from
+// the three slots around them -- one CTA barrier per plane.  48 algorithmic bytes per
 // cell (three fields in, three out).  The quantisation and the final
 // rounding run as 64-bit conversions on B300's FP64 pipe (about two per
 // clock per SM), so the integer pipes keep the products.
@@ -283,10 +283,11 @@ __device__ __forceinline__ long long fx_trunc(double x, int S) {
 // values per field), into a ring of four plane slots in shared memory: the
 // cell at plane k reads slots k - 1, k, k + 1 while plane k + 2 is written
 // into the fourth and plane k + 3 is loaded into registers.
-template <int BY>
+template <int BY, int RPT = 1>
 struct AdvGeom {
   static constexpr int BX = 32;
-  static constexpr int PX = BX + 2, PY = BY + 2, PL = PX * PY;  // one quantised field plane
+  // RPT rows per thread: thread row ty computes rows ty, ty + BY, ...
+  static constexpr int PX = BX + 2, PY = RPT * BY + 2, PL = PX * PY;  // one quantised field plane
   static constexpr int NT = BX * BY;
   static constexpr int NE = (PL + NT - 1) / NT;  // plane values a thread loads per field
   static constexpr int kSlot = 3 * PL;            // u, v, w of one plane
@@ -301,7 +302,7 @@ constexpr int kAdvZcMax = 64;  // z planes per CTA at most (factor table size)
 // to binary64 (nearest) and scaled by 2^-Q through its exponent field (valid
 // for -960 <= Q <= 1022, where every nonzero result is normal).  B300 runs
 // these conversions on its FP64 pipe, about two per clock per SM.
-template <bool POW2, int BY, bool FAST>
+template <bool POW2, int BY, bool FAST, int QF = 3, int RPT = 1>
 __device__ __forceinline__ void advect_march(const double* __restrict__ u, const double* __restrict__ v,
                                              const double* __restrict__ w, double* __restrict__ su,
                                              double* __restrict__ sv, double* __restrict__ sw,
@@ -309,17 +310,17 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
                                              double tcx, double tcy, int64_t nx, int64_t ny, int64_t sy, int64_t sz,
                                              int64_t osy, int64_t osz, int64_t i0, int64_t j0, int64_t k0, int kn,
                                              const AdvScales& sc, long long* zfac) {
-  using G = AdvGeom<BY>;
+  using G = AdvGeom<BY, RPT>;
   extern __shared__ long long adv_ring[];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * G::BX + tx;
   const int64_t i = i0 + 1 + tx, j = j0 + 1 + ty;
-  const bool mine = i <= nx && j <= ny;
   const int sadd = sc.S << 20;  // FAST: x 2^S through the high word's exponent field
   const int qsub = sc.Q << 20;  // FAST: s 2^-Q likewise (s != 0: the exponent stays in range)
   auto quant = [&](double x) -> long long {
     if constexpr (FAST) return __double2ll_rz(__hiloint2double(__double2hiint(x) + sadd, __double2loint(x)));
     else return fx_trunc(x, sc.S);
   };
+  auto quant_i = [&](double x) -> long long { return fx_trunc(x, sc.S); };
   auto outv = [&](long long s) -> double {
     if constexpr (FAST) {
       const double d = __ll2double_rn(s);
@@ -356,9 +357,11 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
 #pragma unroll
     for (int n = 0; n < G::NE; ++n) {
       if (soff[n] >= 0) {
-        d[soff[n]] = quant(raw[0][n]);
-        d[G::PL + soff[n]] = quant(raw[1][n]);
-        d[2 * G::PL + soff[n]] = quant(raw[2][n]);
+        // the first QF fields on the FP64 pipe's conversion, the rest in
+        // integer instructions (the same integers either way)
+        d[soff[n]] = QF >= 1 ? quant(raw[0][n]) : quant_i(raw[0][n]);
+        d[G::PL + soff[n]] = QF >= 2 ? quant(raw[1][n]) : quant_i(raw[1][n]);
+        d[2 * G::PL + soff[n]] = QF >= 3 ? quant(raw[2][n]) : quant_i(raw[2][n]);
       }
     }
   };
@@ -377,14 +380,16 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
   const int shx = pow2_shift(cx), shy = pow2_shift(cy);
   __syncthreads();
   constexpr int DX = 1, DY = G::PX;
-  const int t = (ty + 1) * DY + tx + 1;
 #pragma unroll 1
   for (int kk = 0; kk < kn; ++kk) {
     // plane kk + 3 (in registers) into the slot that plane kk - 1 freed;
     // plane kk + 4 starts loading
     if (kk + 3 <= kn + 1) store(kk + 3);
     if (kk + 4 <= kn + 1) load(kk + 4);
-    if (mine) {
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+    const int t = (ty + rr * BY + 1) * DY + tx + 1;
+    if (i <= nx && j + rr * BY <= ny) {
       const long long* Um = adv_ring + (kk & 3) * G::kSlot;  // plane k - 1
       const long long* U0 = adv_ring + ((kk + 1) & 3) * G::kSlot;
       const long long* Up = adv_ring + ((kk + 2) & 3) * G::kSlot;
@@ -394,7 +399,7 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
       const long long c1 = zfac[2 * kk], c2 = zfac[2 * kk + 1];
       const long long u0 = U0[t], v0 = V0[t], w0 = W0[t];
       const int64_t k = k0 + 1 + kk;
-      const int64_t o = i + j * osy + k * osz;
+      const int64_t o = i + (j + rr * BY) * osy + k * osz;
       // su at (i+1/2, j, k); its x term um (u0 + um) - up (u0 + up) taken as
       // (um - up)(u0 + um + up), exact in integers
       {
@@ -424,11 +429,12 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
         sw[o] = outv(hfactor<POW2>(cx, shx, dx) + hfactor<POW2>(cy, shy, dy) + mh(c1, p3) - mh(c2, p4));
       }
     }
+    }
     __syncthreads();
   }
 }
 
-template <bool POW2, int BY, int MINB, bool FASTCVT>
+template <bool POW2, int BY, int MINB, bool FASTCVT, int QF = 3, int RPT = 1>
 __global__ void __launch_bounds__(32 * BY, MINB)
     advect_kernel(const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ w,
                   double* __restrict__ su, double* __restrict__ sv, double* __restrict__ sw,
@@ -438,45 +444,50 @@ __global__ void __launch_bounds__(32 * BY, MINB)
   __shared__ long long zfac[2 * kAdvZcMax];  // tzc1, tzc2 of the chunk's planes at scale T
   const AdvScales sc = adv_scales(range);
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;  // halo index of the plane box's first column
-  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * BY;
+  const int64_t j0 = static_cast<int64_t>(blockIdx.y) * BY * RPT;
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * zc;
   const int kn = static_cast<int>(min(static_cast<int64_t>(zc), nz - k0));  // cells of this chunk along z
   if (!sc.fixed) {  // uniform over the launch
-    const int64_t i = i0 + 1 + threadIdx.x, j = j0 + 1 + threadIdx.y;
-    if (i > nx || j > ny) return;
-    for (int kk = 0; kk < kn; ++kk) {
-      const int64_t k = k0 + 1 + kk;
-      const int64_t o = i + j * osy + k * osz;
-      advect_cell_f64(u, v, w, i + j * sy + k * sz, sy, sz, tcx, tcy, tzc1[k - 1], tzc2[k - 1], su[o], sv[o],
-                      sw[o]);
+    const int64_t i = i0 + 1 + threadIdx.x;
+    for (int rr = 0; rr < RPT; ++rr) {
+      const int64_t j = j0 + 1 + threadIdx.y + rr * BY;
+      if (i > nx || j > ny) continue;
+      for (int kk = 0; kk < kn; ++kk) {
+        const int64_t k = k0 + 1 + kk;
+        const int64_t o = i + j * osy + k * osz;
+        advect_cell_f64(u, v, w, i + j * sy + k * sz, sy, sz, tcx, tcy, tzc1[k - 1], tzc2[k - 1], su[o], sv[o],
+                        sw[o]);
+      }
     }
     return;
   }
   if (FASTCVT && sc.S >= 0 && sc.S <= 1000 && sc.Q >= -960 && sc.Q <= 1022)
-    advect_march<POW2, BY, FASTCVT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0, j0,
-                                    k0, kn, sc, zfac);
+    advect_march<POW2, BY, FASTCVT, QF, RPT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz,
+                                             i0, j0, k0, kn, sc, zfac);
   else
-    advect_march<POW2, BY, false>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0, j0, k0,
-                                  kn, sc, zfac);
+    advect_march<POW2, BY, false, 3, RPT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0,
+                                          j0, k0, kn, sc, zfac);
 }
 
-// Compiled tile shapes (thread rows BY, CTAs per SM); index 0 is the
-// default.  Measured at 512 x 512 x 256 they are within 5% of each other.
+// Compiled tile shapes (thread rows BY, CTAs per SM, fields quantised on
+// the FP64 pipe QF, rows per thread RPT); index 0 is the default, the
+// fastest at 512 x 512 x 256 (two rows per thread and one field quantised in
+// integer instructions gained 5% over one row and three fields; four rows
+// per thread lost 30%).
 using AdvKernel = void (*)(const double*, const double*, const double*, double*, double*, double*, const double*,
                            const double*, double, double, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
                            int64_t, int, const unsigned long long*);
 struct AdvVariant {
-  int BY, minb;
+  int BY, minb, rpt;  // thread rows, CTAs per SM, rows per thread
   AdvKernel kern[2];  // tcx, tcy general / powers of two
   int smem;
 };
-#define STENCIL_ADV_VARIANT(BY, MINB) \
-  {BY, MINB, {advect_kernel<false, BY, MINB, true>, advect_kernel<true, BY, MINB, true>}, AdvGeom<BY>::kSmem}
+#define STENCIL_ADV_VARIANT(BY, MINB, QF, RPT)                                            \
+  {BY, MINB, RPT, {advect_kernel<false, BY, MINB, true, QF, RPT>, advect_kernel<true, BY, MINB, true, QF, RPT>}, \
+   AdvGeom<BY, RPT>::kSmem}
 const AdvVariant kAdvVariants[] = {
-    STENCIL_ADV_VARIANT(8, 3),
-    STENCIL_ADV_VARIANT(8, 4),
-    STENCIL_ADV_VARIANT(4, 6),
-    STENCIL_ADV_VARIANT(16, 2),
+    STENCIL_ADV_VARIANT(8, 3, 2, 2), STENCIL_ADV_VARIANT(8, 3, 1, 2), STENCIL_ADV_VARIANT(8, 3, 3, 2),
+    STENCIL_ADV_VARIANT(4, 6, 2, 2), STENCIL_ADV_VARIANT(8, 3, 2, 1),
 };
 #undef STENCIL_ADV_VARIANT
 constexpr int kNumAdvVariants = sizeof(kAdvVariants) / sizeof(kAdvVariants[0]);
@@ -494,7 +505,7 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
     return set_error(STENCIL_ERR_ARG, "advect: su, sv, sw must share strides");
   const AdvVariant& av =
       kAdvVariants[(ctx->advect_choice >= 0 && ctx->advect_choice < kNumAdvVariants) ? ctx->advect_choice : 0];
-  const int64_t gx = (u.nx + 31) / 32, gy = (u.ny + av.BY - 1) / av.BY;
+  const int64_t gx = (u.nx + 31) / 32, gy = (u.ny + av.BY * av.rpt - 1) / (av.BY * av.rpt);
   // z chunk: the longest (up to 32 planes) that still gives every SM several
   // CTAs to interleave
   int zc = 32;
