@@ -303,7 +303,8 @@ STENCIL_API int stencil_advect_config_select(stencil_ctx* ctx, int32_t index);
  * to binary64 accuracy or better (it decides convergence of the iterative
  * solve).  Grids whose data and row strides are 16-byte aligned (what a TMA
  * descriptor needs) are evaluated in 64-bit fixed point: u and h^2 f at one
- * scale 2^-S per call with 12 max|u| + h^2 max|f| < 2^(62-S), so 6u minus
+ * scale 2^-S per call with 12 max|u| + h^2 max|f| < 2^(62-S) (the maxima of
+ * the values read, rounded up to their high words), so 6u minus
  * the six neighbours is exact and each r is within 6.5 2^-S / h^2 of the
  * exact f - A u (finer than a binary64 evaluation of the same expression,
  * whose rounding is up to about 16 eps (12 max|u| / h^2 + max|f|)); r is
@@ -311,7 +312,12 @@ STENCIL_API int stencil_advect_config_select(stencil_ctx* ctx, int32_t index);
  * integers), so the norm does not depend on the summation order.  Other
  * grids take a binary64 evaluation in the written order (bitwise the plain
  * definition).  Non-finite input: norms and r are NaN and the ctx status
- * reports STENCIL_ERR_NONFINITE.
+ * reports STENCIL_ERR_NONFINITE.  The first call on a ctx reads u and f
+ * twice (a range pass fixes S); later calls take the previous call's
+ * magnitudes as the scale, check on the device that the values read give
+ * the same scale, and repeat the pass at the right scale when they do not,
+ * so the result depends on the input alone and a call whose magnitudes keep
+ * the scale reads u and f once.
  *   u, f      F64 grids of equal extents (u's halo is the boundary).
  *   r         NULL, or an F64 grid of the same extents, distinct from u and
  *             f (STENCIL_ERR_ARG if it is either): its interior receives r

@@ -25,6 +25,7 @@ struct stencil_ctx {
   int rb_choice[stencil::kNumPolicies][stencil::kMaxPass + 1];
   int resid_choice;  // fixed-point residual configuration index
   int advect_choice; // advection tile configuration index
+  int resid_guess;   // a residual ran on this ctx: its magnitudes are the next call's scale guess
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)
@@ -47,6 +48,14 @@ constexpr size_t kScratchFxMag = 208;     // 4 x uint32: fixed-point magnitude k
 constexpr size_t kScratchFxScale = 224;   // 4 x int32: fixed-point scales (ring of 3)
 constexpr size_t kScratchFxGScale = 240;  // 4 x int32: scale of the stored source (ring of 3)
 constexpr size_t kScratchApplyRange = 80; // uint64 bits of max|in| (linear apply, fixed point)
+// fixed-point residual: magnitudes (3 x uint64 bits, the layout of
+// kScratchRange) of the previous call (the next call's scale guess), of what
+// this call's pass read, and of the scale the final pass used; then the
+// flag that makes the second pass run (uint32)
+constexpr size_t kScratchResidGuess = 88;
+constexpr size_t kScratchResidMeas = 112;
+constexpr size_t kScratchResidFinal = 136;
+constexpr size_t kScratchResidRedo = 160;
 constexpr size_t kScratchPartials = 256;  // residual partial sums
 constexpr int kMaxPartials = 2048;        // blocks of the residual kernel
 // fixed-point residual: CTA count, then 4 words per CTA (up to 2047 CTAs)

@@ -34,6 +34,8 @@ struct SweepArgs {
   int64_t gsy, gsz;                       //   ... and its strides
   int write_r;                            // residual: store r
   unsigned long long* rpart;              // residual: [CTA count, then 4 words per CTA] partial sums
+  const uint32_t* run_flag;               // residual: if set, the pass runs only when *run_flag != 0
+  unsigned long long* seen;               // residual: [3] bounds (bits) of max|u|, max|f|, max|u| read
 };
 
 __device__ __forceinline__ double bits_as_double(unsigned long long b) {
@@ -325,10 +327,15 @@ struct PolResid {
     int write;   // store r
     double rs;   // 2^-S / h^2
   };
-  // exact sums: s = s2 2^128 + s1 2^64 + s0 of R^2, and ff of f^2
+  // exact sums: s = s2 2^128 + s1 2^64 + s0 of R^2, and ff of f^2; the
+  // largest high words of |u| and |f| the lane converted
   struct Track {
     uint64_t s0 = 0, s1 = 0, s2 = 0;
     double ff = 0.0;
+    uint32_t mu = 0, mf = 0;
+    __device__ __forceinline__ void see_u(double u) {
+      mu = max(mu, static_cast<uint32_t>(__double2hiint(u)) & 0x7fffffffu);
+    }
     __device__ __forceinline__ void add_sq(int64_t R) {
       const uint64_t a = static_cast<uint64_t>(R < 0 ? -R : R);
       const uint64_t lo = a * a, hi = __umul64hi(a, a);
@@ -340,6 +347,7 @@ struct PolResid {
     __device__ __forceinline__ void add(uint64_t R, double f) {
       add_sq(static_cast<int64_t>(R));
       ff = fma(f, f, ff);
+      mf = max(mf, static_cast<uint32_t>(__double2hiint(f)) & 0x7fffffffu);
     }
     // this + o (exactly for the integer part)
     __device__ __forceinline__ void merge(uint64_t o0, uint64_t o1, uint64_t o2, double off) {
@@ -352,12 +360,15 @@ struct PolResid {
       ff += off;
     }
   };
+  // The scale follows from the magnitudes' high words (each rounded up to
+  // the largest double with that high word), so a bound measured from high
+  // words alone gives the same scale as the exact maxima.
   __device__ static __forceinline__ K make(const SweepArgs& a) {
     K k;
     k.bad = 0;
     k.write = a.write_r;
-    const double mh = bits_as_double(a.maxbits[0]), mf = bits_as_double(a.maxbits[1]),
-                 mu = bits_as_double(a.maxbits[2]);
+    const double mh = bits_as_double(a.maxbits[0] | 0xffffffffull), mf = bits_as_double(a.maxbits[1] | 0xffffffffull),
+                 mu = bits_as_double(a.maxbits[2] | 0xffffffffull);
     int S = 0;
     if (!(mh <= 1.0e300) || !(mf <= 1.0e300) || !(mu <= 1.0e300)) {
       k.bad = (mh - mh == 0.0 && mf - mf == 0.0 && mu - mu == 0.0) ? 2 : 1;

@@ -162,6 +162,14 @@ struct SrcGrid {
         const double af = __shfl_xor_sync(0xffffffffu, trk.ff, o);
         trk.merge(a0, a1, a2, af);
       }
+      if (p->a.seen) {  // bounds of the magnitudes this warp read (the next call's scale guess)
+        const uint32_t mu = __reduce_max_sync(0xffffffffu, trk.mu);
+        const uint32_t mf = __reduce_max_sync(0xffffffffu, trk.mf);
+        if ((threadIdx.x & 31) == 0) {
+          atomicMax(p->a.seen, (static_cast<unsigned long long>(mu) << 32) | 0xffffffffull);
+          atomicMax(p->a.seen + 1, (static_cast<unsigned long long>(mf) << 32) | 0xffffffffull);
+        }
+      }
       if ((threadIdx.x & 31) == 0) {
         wsum[4 * warp] = trk.s0;
         wsum[4 * warp + 1] = trk.s1;
@@ -260,8 +268,11 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
     const T* U = reinterpret_cast<const T*>(ring + slot * Cfg::STAGE);
     const bool zin_p = (p >= 1 && p <= nz);
 #pragma unroll
-    for (int q = 0; q < Cfg::NROW; ++q)
-      st.W[0][NEW][q] = Pol::in(U[(row0 + q) * Cfg::BOXW + off + Cfg::COL0 + lane], k);
+    for (int q = 0; q < Cfg::NROW; ++q) {
+      const T uv = U[(row0 + q) * Cfg::BOXW + off + Cfg::COL0 + lane];
+      st.W[0][NEW][q] = Pol::in(uv, k);
+      if constexpr (Pol::kResidual) trk.see_u(uv);
+    }
     // Cells outside the interior (Dirichlet halo, or beyond the grid) may be
     // stored in a different form (PolResident keeps them binary64); only
     // warps that touch one take this branch.
@@ -294,6 +305,9 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
         const T* Um = reinterpret_cast<const T*>(ring + ((seq - 1) % S) * Cfg::STAGE);
         const T e = Um[(row0 + rr + 1) * Cfg::BOXW + off + (lane == 0 ? 0 : 33)];
         C ec = Pol::in(e, k);
+        if constexpr (Pol::kResidual) {
+          if (lane == 0 || lane == 31) trk.see_u(e);
+        }
         if (any_edge_halo && edge_halo) ec = Pol::in_halo(e, k);
         if (lane == 0) xm = ec;
         if (lane == 31) xp = ec;
@@ -409,6 +423,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
   constexpr int S = Cfg::S, WY = Cfg::WY;
   extern __shared__ unsigned char smem_raw[];
   __shared__ int abort_flag;
+  if constexpr (Pol::kResidual) {  // a conditional pass (uniform: every thread reads the same word)
+    if (params.a.run_flag && *params.a.run_flag == 0u) return;
+  }
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const uint32_t bar_full = smem_addr(base);

@@ -111,6 +111,47 @@ def test_residual_deterministic_and_exact_solution():
     assert a[0] <= 1e-12 * a[1]
 
 
+def test_residual_scale_follows_each_input():
+    """The fixed-point residual's scale comes from the magnitudes of what its
+    pass reads.  A context reuses the previous call's magnitudes as the
+    guess and repeats the pass when the guess gives another scale.  On one
+    context, fields of very different magnitudes in turn (1e-120, 1e+120,
+    1, 1 again, 1e-120 again) each match the oracle, and every call returns
+    bit for bit what a fresh context's first call returns for the same
+    input, so the result does not depend on what ran before."""
+    import torch
+    from paper_2310_01882_b300.stencil import Context
+    nx, ny, nz = 45, 30, 21
+    rng = np.random.default_rng(77)
+    base_u = rng.random((nz + 2, ny + 2, nx + 2))
+    base_f = rng.standard_normal((nz + 2, ny + 2, nx + 2))
+    h = 1.0 / 46
+    shared = Context(0)
+
+    def run(c, u, f):
+        uf, ff = S.Field.from_numpy(u), S.Field.from_numpy(f)
+        rf = S.Field(nx, ny, nz)
+        norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+        S.stencil_residual(c, uf, ff, h, norms, r=rf)
+        torch.cuda.synchronize()
+        S.stencil_ctx_status(c)
+        return norms.cpu().numpy(), rf.to_numpy()
+
+    for scale in (1e-120, 1e120, 1.0, 1.0, 1e-120):
+        u, f = scale * base_u, scale * base_f
+        nr, nf, r = oracle.residual(u, f, h, want_r=True, nthreads=0)
+        got_n, got_r = run(shared, u, f)
+        tol = r_tol(u, f, h)
+        assert np.max(np.abs(got_r[1:-1, 1:-1, 1:-1] - r[1:-1, 1:-1, 1:-1])) <= tol
+        assert abs(got_n[0] - nr) <= np.sqrt(nx * ny * nz) * tol + 1e-12 * nr
+        assert abs(got_n[1] - nf) <= 1e-13 * nf
+        fresh = Context(0)
+        ref_n, ref_r = run(fresh, u, f)
+        fresh.close()
+        assert np.array_equal(got_n, ref_n) and np.array_equal(got_r, ref_r), scale
+    shared.close()
+
+
 def test_residual_full_size_norms():
     """512^3 with the benchmark's source (k^-3 field) and a U[0,1) iterate:
     norms agree with the oracle's (all host cores)."""
