@@ -26,6 +26,8 @@ struct stencil_ctx {
   int resid_choice;  // fixed-point residual configuration index
   int advect_choice; // advection tile configuration index
   int resid_guess;   // a residual ran on this ctx: its magnitudes are the next call's scale guess
+  int apply_guess;   // the same for the fixed-point linear apply
+  int advect_guess;  // the same for the fixed-point advection
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)
@@ -61,7 +63,19 @@ constexpr int kMaxPartials = 2048;        // blocks of the residual kernel
 // fixed-point residual: CTA count, then 4 words per CTA (up to 2047 CTAs)
 constexpr size_t kScratchResidFx = kScratchPartials + sizeof(double) * 2 * kMaxPartials;
 constexpr int kMaxResidFxCtas = 2047;
-constexpr size_t kScratchBytes = kScratchResidFx + 32 * (kMaxResidFxCtas + 1);
+// scale guesses of the fixed-point apply and advection: for each, the
+// previous call's magnitudes (bits), those this call's pass read, those
+// the final pass used, and the flag that makes the second pass run
+constexpr size_t kScratchGuess = kScratchResidFx + 32 * (kMaxResidFxCtas + 1);
+constexpr size_t kScratchApplyGuess = kScratchGuess;        // 1 x uint64 each: max|in|
+constexpr size_t kScratchApplySeen = kScratchGuess + 8;
+constexpr size_t kScratchApplyFinal = kScratchGuess + 16;
+constexpr size_t kScratchApplyRedo = kScratchGuess + 24;    // uint32
+constexpr size_t kScratchAdvGuess = kScratchGuess + 32;     // 5 x uint64 each (kScratchAdvRange layout)
+constexpr size_t kScratchAdvSeen = kScratchGuess + 72;
+constexpr size_t kScratchAdvFinal = kScratchGuess + 112;
+constexpr size_t kScratchAdvRedo = kScratchGuess + 152;     // uint32
+constexpr size_t kScratchBytes = kScratchGuess + 160;
 
 // Internal dtype code: biased 64-bit fixed-point iterate (never in the ABI).
 constexpr int kDtypeU64 = 100;

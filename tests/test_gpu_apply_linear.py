@@ -120,6 +120,39 @@ def test_integer_weights_on_smooth_and_random_fields(name):
         assert np.max(np.abs(got - ref)) <= bound, name
 
 
+@pytest.mark.parametrize("name", ["laplacian13_4th", "box27"])
+def test_scale_follows_each_input(name):
+    """The fixed-point apply takes its scale from the magnitude of what its
+    pass reads.  A context reuses the previous call's magnitude as the guess
+    and repeats the pass when the guess gives another scale.  On one
+    context, fields of very different magnitudes in turn (1e-150, 1e+150,
+    1, 1 again, 1e-150 again) each stay within the oracle's rounding bound
+    and equal bit for bit a fresh context's first call on the same input."""
+    import torch
+    offs, coef = INT_STENCILS[name]
+    nx, ny, nz = 40, 33, 21
+    base = np.random.default_rng(12).standard_normal((nz + 2, ny + 2, nx + 2))
+    shared = S.Context(0)
+
+    def go(c, u):
+        a, b = S.Field.from_numpy(u), S.Field.from_numpy(np.zeros_like(u))
+        S.stencil_apply_linear(c, a, b, offs, coef)
+        torch.cuda.synchronize()
+        S.stencil_ctx_status(c)
+        return b.to_numpy()
+
+    for scale in (1e-150, 1e150, 1.0, 1.0, 1e-150):
+        u = scale * base
+        got = go(shared, u)
+        ref = oracle.apply_linear(u, offs, coef, out=np.zeros_like(u))
+        bound = 2 * len(offs) * np.finfo(float).eps * np.sum(np.abs(coef)) * np.max(np.abs(u))
+        assert np.max(np.abs(got - ref)) <= bound, scale
+        fresh = S.Context(0)
+        assert np.array_equal(got, go(fresh, u)), scale
+        fresh.close()
+    shared.close()
+
+
 def test_arguments():
     a = S.Field(8, 8, 8)
     with pytest.raises(S.StencilError):
