@@ -538,7 +538,12 @@ STENCIL_API int stencil_residual_noalloc(const stencil_grid* u,
  * rounding error, and equal fluxes cancel exactly.  If the three fields' (or
  * the factors') largest magnitudes differ by more than 2^8, or an input is
  * not finite, the launch evaluates the formula in binary64 instead (NaN and
- * Inf propagate as in binary64).  Uses the context's scratch; asynchronous.
+ * Inf propagate as in binary64).  The scales follow from the magnitudes the
+ * pass reads: the first call on a ctx measures them with a range pass;
+ * later calls take the previous call's magnitudes and check on the device
+ * that the values read lead to the same scales, repeating the pass when
+ * they do not, so the result depends on the input alone.  Uses the
+ * context's scratch; asynchronous.
  */
 STENCIL_API int stencil_advect_uvw(stencil_ctx* ctx, const stencil_grid* u,
                        const stencil_grid* v, const stencil_grid* w,

@@ -109,6 +109,36 @@ __global__ void advect_range_kernel(const double* __restrict__ u, const double* 
   }
 }
 
+// Largest and smallest nonzero |factor| (tcx, tcy, tzc1[], tzc2[]) as bits
+// into a[3], a[4] and b[3], b[4] (one warp).
+__global__ void advect_factor_kernel(const double* __restrict__ tzc1, const double* __restrict__ tzc2, int64_t nz,
+                                     double tcx, double tcy, unsigned long long* a, unsigned long long* b) {
+  unsigned long long cmax = 0, cmin = ~0ull;
+  auto take = [&](double x) {
+    const unsigned long long v = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
+    cmax = v > cmax ? v : cmax;
+    if (v != 0) cmin = v < cmin ? v : cmin;
+  };
+  if (threadIdx.x == 0) {
+    take(tcx);
+    take(tcy);
+  }
+  for (int64_t k = threadIdx.x; k < nz; k += 32) {
+    take(tzc1[k]);
+    take(tzc2[k]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, cmax, o);
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, cmin, o);
+    cmax = x > cmax ? x : cmax;
+    cmin = y < cmin ? y : cmin;
+  }
+  if (threadIdx.x == 0) {
+    a[3] = b[3] = cmax;
+    a[4] = b[4] = cmin;
+  }
+}
+
 // ceil(log2 x) for the positive normal double with these bits.
 __device__ __forceinline__ int ceil_log2_bits(unsigned long long b) {
   const int e = static_cast<int>(b >> 52) - 1023;
@@ -122,8 +152,16 @@ struct AdvScales {
 
 // The scales of this launch (the same in every thread) and whether the
 // fixed-point evaluation applies.
-__device__ __forceinline__ AdvScales adv_scales(const unsigned long long* r) {
+// The fields' magnitudes count by their high words only (rounded up to the
+// largest double with that high word; a zero high word counts as zero), so
+// the maxima a pass records from high words give the same decision as the
+// exact maxima of a range pass.
+__device__ __forceinline__ AdvScales adv_scales(const unsigned long long* rb) {
   AdvScales sc{0, 0, 0, false};
+  unsigned long long r[5];
+  for (int f = 0; f < 3; ++f) r[f] = (rb[f] >> 32) ? (rb[f] | 0xffffffffull) : 0ull;
+  r[3] = rb[3];
+  r[4] = rb[4];
   unsigned long long M = 0;
   for (int f = 0; f < 3; ++f) {
     if (r[f] >= kInfBits) return sc;
@@ -309,7 +347,7 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
                                              const double* __restrict__ tzc1, const double* __restrict__ tzc2,
                                              double tcx, double tcy, int64_t nx, int64_t ny, int64_t sy, int64_t sz,
                                              int64_t osy, int64_t osz, int64_t i0, int64_t j0, int64_t k0, int kn,
-                                             const AdvScales& sc, long long* zfac) {
+                                             const AdvScales& sc, long long* zfac, uint32_t (&mx)[3]) {
   using G = AdvGeom<BY, RPT>;
   extern __shared__ long long adv_ring[];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * G::BX + tx;
@@ -357,6 +395,9 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
 #pragma unroll
     for (int n = 0; n < G::NE; ++n) {
       if (soff[n] >= 0) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+          mx[f] = max(mx[f], static_cast<uint32_t>(__double2hiint(raw[f][n])) & 0x7fffffffu);
         // the first QF fields on the FP64 pipe's conversion, the rest in
         // integer instructions (the same integers either way)
         d[soff[n]] = QF >= 1 ? quant(raw[0][n]) : quant_i(raw[0][n]);
@@ -434,20 +475,45 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
   }
 }
 
+// One pass of the advection: the magnitudes it takes its scales from
+// (`used`: the kScratchAdvRange layout), where it records the fields'
+// magnitudes it reads (`seen`), and the flag that makes it run (null:
+// always).
+struct AdvPass {
+  const unsigned long long* used;
+  unsigned long long* seen;
+  const uint32_t* run_flag;
+};
+
 template <bool POW2, int BY, int MINB, bool FASTCVT, int QF = 3, int RPT = 1>
 __global__ void __launch_bounds__(32 * BY, MINB)
     advect_kernel(const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ w,
                   double* __restrict__ su, double* __restrict__ sv, double* __restrict__ sw,
                   const double* __restrict__ tzc1, const double* __restrict__ tzc2, double tcx, double tcy,
                   int64_t nx, int64_t ny, int64_t nz, int64_t sy, int64_t sz, int64_t osy, int64_t osz,
-                  int zc, const unsigned long long* __restrict__ range) {
+                  int zc, const AdvPass ps) {
+  if (ps.run_flag && *ps.run_flag == 0u) return;  // uniform
   __shared__ long long zfac[2 * kAdvZcMax];  // tzc1, tzc2 of the chunk's planes at scale T
-  const AdvScales sc = adv_scales(range);
+  const AdvScales sc = adv_scales(ps.used);
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;  // halo index of the plane box's first column
   const int64_t j0 = static_cast<int64_t>(blockIdx.y) * BY * RPT;
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * zc;
   const int kn = static_cast<int>(min(static_cast<int64_t>(zc), nz - k0));  // cells of this chunk along z
+  uint32_t mx[3] = {0u, 0u, 0u};  // largest high words of |u|, |v|, |w| read
   if (!sc.fixed) {  // uniform over the launch
+    // the magnitudes of the cells the fixed-point path would have loaded
+    // (this CTA's box, halo included), then binary64 cell by cell
+    const int PXb = 34, PYb = BY * RPT + 2;
+    for (int e = threadIdx.y * 32 + threadIdx.x; e < PXb * PYb; e += 32 * BY) {
+      const int64_t gi = i0 + e % PXb, gj = j0 + e / PXb;
+      if (gi > nx + 1 || gj > ny + 1) continue;
+      for (int kk = 0; kk <= kn + 1; ++kk) {
+        const int64_t c = gi + gj * sy + (k0 + kk) * sz;
+        mx[0] = max(mx[0], static_cast<uint32_t>(__double2hiint(u[c])) & 0x7fffffffu);
+        mx[1] = max(mx[1], static_cast<uint32_t>(__double2hiint(v[c])) & 0x7fffffffu);
+        mx[2] = max(mx[2], static_cast<uint32_t>(__double2hiint(w[c])) & 0x7fffffffu);
+      }
+    }
     const int64_t i = i0 + 1 + threadIdx.x;
     for (int rr = 0; rr < RPT; ++rr) {
       const int64_t j = j0 + 1 + threadIdx.y + rr * BY;
@@ -459,14 +525,39 @@ __global__ void __launch_bounds__(32 * BY, MINB)
                         sw[o]);
       }
     }
-    return;
-  }
-  if (FASTCVT && sc.S >= 0 && sc.S <= 1000 && sc.Q >= -960 && sc.Q <= 1022)
+  } else if (FASTCVT && sc.S >= 0 && sc.S <= 1000 && sc.Q >= -960 && sc.Q <= 1022) {
     advect_march<POW2, BY, FASTCVT, QF, RPT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz,
-                                             i0, j0, k0, kn, sc, zfac);
-  else
+                                             i0, j0, k0, kn, sc, zfac, mx);
+  } else {
     advect_march<POW2, BY, false, 3, RPT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0,
-                                          j0, k0, kn, sc, zfac);
+                                          j0, k0, kn, sc, zfac, mx);
+  }
+  // publish (every thread of every warp arrives here)
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const uint32_t m = __reduce_max_sync(0xffffffffu, mx[f]);
+    if ((threadIdx.x & 31) == 0 && m)
+      atomicMax(ps.seen + f, (static_cast<unsigned long long>(m) << 32) | 0xffffffffull);
+  }
+}
+
+// Accepts the first pass if the magnitudes it read lead to the same
+// decision (fixed point or binary64) and the same scales as those it used;
+// otherwise the second pass runs with the magnitudes read.  The fields'
+// magnitudes read become the next call's guess.
+__global__ void advect_check_kernel(const unsigned long long* used, const unsigned long long* __restrict__ seen,
+                                    unsigned long long* __restrict__ final_bits, uint32_t* __restrict__ redo,
+                                    unsigned long long* guess) {
+  unsigned long long a[5], b[5];
+  for (int f = 0; f < 5; ++f) {
+    a[f] = used[f];
+    b[f] = seen[f];
+  }
+  const AdvScales x = adv_scales(a), y = adv_scales(b);
+  const bool ok = x.fixed == y.fixed && (!x.fixed || (x.S == y.S && x.T == y.T));
+  for (int f = 0; f < 5; ++f) final_bits[f] = ok ? a[f] : b[f];
+  *redo = ok ? 0u : 1u;
+  for (int f = 0; f < 3; ++f) guess[f] = b[f];
 }
 
 // Compiled tile shapes (thread rows BY, CTAs per SM, fields quantised on
@@ -476,7 +567,7 @@ __global__ void __launch_bounds__(32 * BY, MINB)
 // per thread lost 30%).
 using AdvKernel = void (*)(const double*, const double*, const double*, double*, double*, double*, const double*,
                            const double*, double, double, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
-                           int64_t, int, const unsigned long long*);
+                           int64_t, int, AdvPass);
 struct AdvVariant {
   int BY, minb, rpt;  // thread rows, CTAs per SM, rows per thread
   AdvKernel kern[2];  // tcx, tcy general / powers of two
@@ -512,16 +603,39 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
   while (zc > 4 && gx * gy * ((u.nz + zc - 1) / zc) < int64_t(4) * av.minb * ctx->num_sms) zc /= 2;
   const int64_t gz = (u.nz + zc - 1) / zc;
   if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return set_error(STENCIL_ERR_ARG, "advect: grid too large");
-  unsigned long long* range = reinterpret_cast<unsigned long long*>(ctx->scratch + kScratchAdvRange);
-  int rc = check_cuda(cudaMemsetAsync(range, 0, 4 * sizeof(unsigned long long), st), "advect range init");
-  if (!rc) rc = check_cuda(cudaMemsetAsync(range + 4, 0xff, sizeof(unsigned long long), st), "advect range init");
+  // The scales: the first call on a context measures the magnitudes with a
+  // range pass; later calls take the previous call's field magnitudes as the
+  // guess (the factors' magnitudes are measured every call: a one-warp
+  // kernel over nz values).  The pass records the fields' magnitudes it
+  // reads; a one-thread check keeps its output only if they lead to the same
+  // decision and scales, otherwise a second pass (launched every call,
+  // returning at once when not needed) recomputes with them -- the output
+  // is a function of the input alone, and a call whose magnitudes keep the
+  // previous scales reads u, v, w once.
+  unsigned char* scr = ctx->scratch;
+  auto* guess = reinterpret_cast<unsigned long long*>(scr + kScratchAdvGuess);
+  auto* seen = reinterpret_cast<unsigned long long*>(scr + kScratchAdvSeen);
+  auto* final_bits = reinterpret_cast<unsigned long long*>(scr + kScratchAdvFinal);
+  auto* redo = reinterpret_cast<uint32_t*>(scr + kScratchAdvRedo);
+  unsigned long long* used = guess;
+  int rc = check_cuda(cudaMemsetAsync(seen, 0, 3 * sizeof(unsigned long long), st), "advect magnitude init");
   if (rc) return rc;
-  const int64_t rows = (u.ny + 2) * (u.nz + 2);
-  const int rblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
-  advect_range_kernel<<<rblocks, dim3(32, 8), 0, st>>>(
-      static_cast<const double*>(u.data), static_cast<const double*>(v.data), static_cast<const double*>(w.data),
-      u.nx, u.ny, u.nz, u.sy, u.sz, tzc1, tzc2, tcx, tcy, range);
-  rc = check_cuda(cudaGetLastError(), "advect range kernel");
+  if (!ctx->advect_guess) {
+    unsigned long long* range = reinterpret_cast<unsigned long long*>(scr + kScratchAdvRange);
+    rc = check_cuda(cudaMemsetAsync(range, 0, 4 * sizeof(unsigned long long), st), "advect range init");
+    if (!rc) rc = check_cuda(cudaMemsetAsync(range + 4, 0xff, sizeof(unsigned long long), st), "advect range init");
+    if (rc) return rc;
+    const int64_t rows = (u.ny + 2) * (u.nz + 2);
+    const int rblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
+    advect_range_kernel<<<rblocks, dim3(32, 8), 0, st>>>(
+        static_cast<const double*>(u.data), static_cast<const double*>(v.data), static_cast<const double*>(w.data),
+        u.nx, u.ny, u.nz, u.sy, u.sz, tzc1, tzc2, tcx, tcy, range);
+    rc = check_cuda(cudaGetLastError(), "advect range kernel");
+    if (rc) return rc;
+    used = range;
+  }
+  advect_factor_kernel<<<1, 32, 0, st>>>(tzc1, tzc2, u.nz, tcx, tcy, used, seen);
+  rc = check_cuda(cudaGetLastError(), "advect factor kernel");
   if (rc) return rc;
   // tcx and tcy positive powers of two (within the fixed-point range): their
   // factor products are shifts (the quantised factor is then exactly
@@ -537,11 +651,22 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
   if (rc) return rc;
   const dim3 block(32, av.BY);
   const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(gz));
-  kern<<<grid, block, av.smem, st>>>(
-      static_cast<const double*>(u.data), static_cast<const double*>(v.data),
-      static_cast<const double*>(w.data), static_cast<double*>(su.data), static_cast<double*>(sv.data),
-      static_cast<double*>(sw.data), tzc1, tzc2, tcx, tcy, u.nx, u.ny, u.nz, u.sy, u.sz, su.sy, su.sz, zc, range);
-  return check_cuda(cudaGetLastError(), "advect kernel");
+  auto launch = [&](const AdvPass& ps) {
+    kern<<<grid, block, av.smem, st>>>(
+        static_cast<const double*>(u.data), static_cast<const double*>(v.data),
+        static_cast<const double*>(w.data), static_cast<double*>(su.data), static_cast<double*>(sv.data),
+        static_cast<double*>(sw.data), tzc1, tzc2, tcx, tcy, u.nx, u.ny, u.nz, u.sy, u.sz, su.sy, su.sz, zc, ps);
+    return check_cuda(cudaGetLastError(), "advect kernel");
+  };
+  rc = launch(AdvPass{used, seen, nullptr});
+  if (rc) return rc;
+  advect_check_kernel<<<1, 1, 0, st>>>(used, seen, final_bits, redo, guess);
+  rc = check_cuda(cudaGetLastError(), "advect check kernel");
+  if (rc) return rc;
+  rc = launch(AdvPass{final_bits, seen, redo});
+  if (rc) return rc;
+  ctx->advect_guess = 1;
+  return STENCIL_OK;
 }
 
 }  // namespace stencil

@@ -215,6 +215,46 @@ def test_advect_every_config():
             c.close()
 
 
+def test_advect_scales_follow_each_input():
+    """The advection's scales (and its choice between fixed point and
+    binary64) come from the magnitudes of what its pass reads.  A context
+    reuses the previous call's magnitudes as the guess and repeats the pass
+    when the guess leads elsewhere.  On one context, winds scaled by 1e-150,
+    1e+150, 1, 1 again, then uneven magnitudes (w times 1e-7: binary64),
+    then 1 again each match the oracle and equal bit for bit a fresh
+    context's first call on the same input."""
+    import torch
+    from paper_2310_01882_b300.stencil import Context
+    nx, ny, nz = 37, 29, 13
+    u0, v0, w0 = inputs.winds(nx, ny, nz, seeds=(51, 52, 53))
+    t1, t2 = inputs.tzc(nz, 7), inputs.tzc(nz, 8)
+    d1, d2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
+    shared = Context(0)
+
+    def go(c, u, v, w):
+        fu, fv, fw = (S.Field.from_numpy(a) for a in (u, v, w))
+        outs = [fu.like() for _ in range(3)]
+        S.stencil_advect_uvw(c, fu, fv, fw, *outs, d1, d2, 0.25, 0.25)
+        torch.cuda.synchronize()
+        return [o.to_numpy() for o in outs]
+
+    for case in ("tiny", "huge", "one", "one", "uneven", "one"):
+        sc = {"tiny": 1e-150, "huge": 1e150}.get(case, 1.0)
+        u, v, w = sc * u0, sc * v0, sc * w0
+        if case == "uneven":
+            w = 1e-7 * w
+        ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, 0.25)
+        got = go(shared, u, v, w)
+        for g, r in zip(got, ref):
+            assert rel_err(g, r) <= 1e-13, case
+        fresh = Context(0)
+        again = go(fresh, u, v, w)
+        fresh.close()
+        for g, a in zip(got, again):
+            assert np.array_equal(g, a), case
+    shared.close()
+
+
 def test_advect_full_size():
     """512 x 512 x 256, winds per the benchmark recipe, oracle on all cores."""
     u, v, w = inputs.winds(512, 512, 256)
