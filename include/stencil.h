@@ -179,7 +179,12 @@ STENCIL_API int stencil_jacobi_sweep(stencil_ctx* ctx, const stencil_grid* u,
  *   point, the input converted at one scale 2^-S per call (S from max|in|
  *   and sum |k_p|), sum k_p q_p exact and rounded to binary64 once, so the
  *   result is within 2^-61 sum|coeffs| max|in| of the exact sum (exactly it
- *   for inputs on the 2^-S grid, e.g. integer-valued ones).  Any other
+ *   for inputs on the 2^-S grid, e.g. integer-valued ones).  max|in| is
+ *   that of the values read (high word, rounded up): the first call on a
+ *   ctx measures it with a range pass, later calls take the previous
+ *   call's and check on the device that the values read give the same
+ *   scale, repeating the pass when not, so the result depends on the input
+ *   alone.  Any other
  *   coefficients: each product rounded, then added in the listed order
  *   (binary64, no fused multiply-add): bitwise that order's result.
  *   in, out   F64 grids of equal extents, distinct (out of place).
