@@ -6,6 +6,9 @@ namespace stencil {
 
 int sweep_variants_bf16(int T, const SweepVariant** out) {
   static const SweepVariant t1[] = {
+      variant<PolBF16, TbCfg<PolBF16, 1, 8, 8, 4, 2, true, true>>(),
+      variant<PolBF16, TbCfg<PolBF16, 1, 8, 16, 4, 1, true, true>>(),
+      variant<PolBF16, TbCfg<PolBF16, 1, 4, 8, 5, 3, true, true>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 8, 8, 4, 2>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 8, 4, 5, 3>>(),
       variant<PolBF16, TbCfg<PolBF16, 1, 4, 8, 6, 3>>(),

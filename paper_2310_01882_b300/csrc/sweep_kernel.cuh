@@ -66,11 +66,16 @@ __device__ __forceinline__ Item decode_item(const SweepGeom& g, int64_t item) {
 // EDGE is the default at one sweep per pass only: with two sweeps per pass
 // it gains two output columns per tile but stages a wider box (40 instead of
 // 36 FP32 columns), and measured slower on a 512^3 grid and on the batch.
-template <class Pol, int T_, int R_, int WY_, int S_, int MINB_, bool EDGE_ = (T_ == 1)>
+// XSMEM (one sweep per pass, policies whose halo cells convert as interior
+// ones): both x neighbours are read from the staged plane instead of
+// shuffled, so no lane is special.
+template <class Pol, int T_, int R_, int WY_, int S_, int MINB_, bool EDGE_ = (T_ == 1), bool XSMEM_ = false>
 struct TbCfg {
   static constexpr int T = T_, R = R_, WY = WY_, S = S_, MINB = MINB_;
   static constexpr bool RB = false;
   static constexpr bool EDGE = EDGE_;
+  static constexpr bool XSMEM = XSMEM_;
+  static_assert(!XSMEM || (T == 1 && EDGE && !Pol::kFixed), "staged x neighbours: one-sweep float policies");
   static constexpr int A = 16 / Pol::kElem;      // TMA x granule in elements
   // Staged columns from xo - T rounded down to the TMA granule: the 32 lanes
   // (+ A - 1 for an unaligned start), or, with EDGE, the 34 columns
@@ -295,8 +300,17 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
     for (int rr = 0; rr < Cfg::R + 2 * (TT - 1); ++rr) {
       if (rr >= nr) break;
       const C c = st.W[t - 1][MID][rr + 1];
-      C xm = __shfl_up_sync(0xffffffffu, c, 1);
-      C xp = __shfl_down_sync(0xffffffffu, c, 1);
+      C xm, xp;
+      if constexpr (Cfg::XSMEM) {
+        // both x neighbours from the staged middle plane (held until this
+        // step ends)
+        const T* Um = reinterpret_cast<const T*>(ring + ((seq - 1) % S) * Cfg::STAGE);
+        const int e0 = (row0 + rr + 1) * Cfg::BOXW + off + Cfg::COL0 + lane;
+        xm = Pol::in(Um[e0 - 1], k);
+        xp = Pol::in(Um[e0 + 1], k);
+      } else {
+      xm = __shfl_up_sync(0xffffffffu, c, 1);
+      xp = __shfl_down_sync(0xffffffffu, c, 1);
       if (Cfg::EDGE && t == 1) {
         // Lane 0's left and lane 31's right neighbour, from the staged plane
         // of stage 0's middle plane (held until this step ends); the other
@@ -311,6 +325,7 @@ __device__ __forceinline__ void tb_step(LaneState<Pol, Cfg>& st, const typename 
         if (any_edge_halo && edge_halo) ec = Pol::in_halo(e, k);
         if (lane == 0) xm = ec;
         if (lane == 31) xp = ec;
+      }
       }
       const int w = rr - (TT - t);  // warp row, -T..R+T-1
       const bool in = xin && zin && ((ymask >> (w + TT)) & 1u);
