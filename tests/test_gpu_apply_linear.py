@@ -153,6 +153,35 @@ def test_scale_follows_each_input(name):
     shared.close()
 
 
+def test_nonfinite_then_finite():
+    """A NaN (or an infinity) in the input of the fixed-point apply: every
+    output point is NaN and the context reports STENCIL_ERR_NONFINITE; the
+    next call on the same context, with finite input, is right again."""
+    import torch
+    offs, coef = INT_STENCILS["laplacian13_4th"]
+    rng = np.random.default_rng(83)
+    u = rng.integers(-1000, 1001, (14, 13, 17)).astype(np.float64)
+    c = S.Context(0)
+    for bad in (np.nan, np.inf):
+        ub = u.copy()
+        ub[6, 6, 6] = bad
+        a, b = S.Field.from_numpy(ub), S.Field.from_numpy(np.zeros_like(u))
+        S.stencil_apply_linear(c, a, b, offs, coef)
+        torch.cuda.synchronize()
+        got = b.to_numpy()
+        assert np.isnan(got[2:-2, 2:-2, 2:-2]).all()
+        with pytest.raises(S.StencilError) as e:
+            S.stencil_ctx_status(c)
+        assert e.value.code == -6
+        S.stencil_ctx_status(c)  # cleared
+        a, b = S.Field.from_numpy(u), S.Field.from_numpy(np.zeros_like(u))
+        S.stencil_apply_linear(c, a, b, offs, coef)
+        torch.cuda.synchronize()
+        S.stencil_ctx_status(c)
+        assert np.array_equal(b.to_numpy(), oracle.apply_linear(u, offs, coef, out=np.zeros_like(u)))
+    c.close()
+
+
 def test_arguments():
     a = S.Field(8, 8, 8)
     with pytest.raises(S.StencilError):

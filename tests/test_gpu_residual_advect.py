@@ -152,6 +152,38 @@ def test_residual_scale_follows_each_input():
     shared.close()
 
 
+def test_residual_nonfinite_then_finite():
+    """A NaN (or an infinity) in u: the fixed-point residual's norms are NaN
+    and the context reports STENCIL_ERR_NONFINITE; the next call on the same
+    context, with finite input, is right again (its scale guess recovers)."""
+    import torch
+    from paper_2310_01882_b300.stencil import Context
+    n = 20
+    rng = np.random.default_rng(81)
+    u = rng.random((n + 2, n + 2, n + 2))
+    f = rng.standard_normal((n + 2, n + 2, n + 2))
+    h = 1.0 / (n + 1)
+    c = Context(0)
+    norms = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for bad in (np.nan, np.inf):
+        ub = u.copy()
+        ub[7, 8, 9] = bad
+        S.stencil_residual(c, S.Field.from_numpy(ub), S.Field.from_numpy(f), h, norms)
+        torch.cuda.synchronize()
+        assert np.isnan(norms.cpu().numpy()).all()
+        with pytest.raises(S.StencilError) as e:
+            S.stencil_ctx_status(c)
+        assert e.value.code == -6
+        S.stencil_ctx_status(c)  # cleared
+        S.stencil_residual(c, S.Field.from_numpy(u), S.Field.from_numpy(f), h, norms)
+        torch.cuda.synchronize()
+        S.stencil_ctx_status(c)
+        nr, nf = oracle.residual(u, f, h)
+        g = norms.cpu().numpy()
+        assert abs(g[0] - nr) <= 1e-12 * nr and abs(g[1] - nf) <= 1e-13 * nf
+    c.close()
+
+
 def test_residual_full_size_norms():
     """512^3 with the benchmark's source (k^-3 field) and a U[0,1) iterate:
     norms agree with the oracle's (all host cores)."""
