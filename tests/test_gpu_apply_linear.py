@@ -153,6 +153,34 @@ def test_scale_follows_each_input(name):
     shared.close()
 
 
+def test_full_size_benchmark_launch():
+    """The benchmark's linear applies at full size: the 7-point and the
+    fourth-order 13-point Laplacians on the 512^3 U[0,1) field (seed 3), two
+    calls each on one context as bench.py times them (the first takes its
+    scale from a range pass, the second from the first's magnitude): both
+    within the oracle's rounding bound and equal bit for bit."""
+    import torch
+    from paper_2310_01882_b300 import inputs
+    n = 512
+    u = inputs.uniform(n, n, n, seed=3)
+    c = S.Context(0)
+    a = S.Field.from_numpy(u)
+    b = a.like()
+    for name in ("laplacian7", "laplacian13_4th"):
+        offs, coef = INT_STENCILS[name]
+        outs = []
+        for _ in range(2):
+            S.stencil_apply_linear(c, a, b, offs, coef)
+            torch.cuda.synchronize()
+            S.stencil_ctx_status(c)
+            outs.append(b.to_numpy())
+        ref = oracle.apply_linear(u, offs, coef, out=outs[0].copy())
+        bound = 2 * len(offs) * np.finfo(float).eps * np.sum(np.abs(coef)) * np.max(np.abs(u))
+        assert np.max(np.abs(outs[0] - ref)) <= bound, name
+        assert np.array_equal(outs[0], outs[1]), name
+    c.close()
+
+
 def test_nonfinite_then_finite():
     """A NaN (or an infinity) in the input of the fixed-point apply: every
     output point is NaN and the context reports STENCIL_ERR_NONFINITE; the
