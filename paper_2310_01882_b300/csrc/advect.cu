@@ -51,14 +51,11 @@ namespace {
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
-// Reduction of the magnitudes that fix the scales: r[0..2] = bits of
-// max |u|, |v|, |w| over every cell (halos included), r[3] = bits of the
-// largest |factor| (tcx, tcy, tzc1[], tzc2[]), r[4] = bits of the smallest
-// nonzero |factor|.  Non-negative doubles order as their bit patterns.
+// Bits of max |u|, |v|, |w| over every cell (halos included) into
+// r[0..2] (zeroed first).  Non-negative doubles order as their bit patterns.
 __global__ void advect_range_kernel(const double* __restrict__ u, const double* __restrict__ v,
                                     const double* __restrict__ w, int64_t nx, int64_t ny, int64_t nz, int64_t sy,
-                                    int64_t sz, const double* __restrict__ tzc1, const double* __restrict__ tzc2,
-                                    double tcx, double tcy, unsigned long long* r) {
+                                    int64_t sz, unsigned long long* r) {
   const int64_t rows = (ny + 2) * (nz + 2);
   unsigned long long m[3] = {0, 0, 0};
   for (int64_t row = blockIdx.x * int64_t(blockDim.y) + threadIdx.y; row < rows;
@@ -80,32 +77,6 @@ __global__ void advect_range_kernel(const double* __restrict__ u, const double* 
       m[f] = a > m[f] ? a : m[f];
     }
     if ((threadIdx.x & 31) == 0) atomicMax(&r[f], m[f]);
-  }
-  if (blockIdx.x == 0 && threadIdx.y == 0) {
-    unsigned long long cmax = 0, cmin = ~0ull;
-    auto take = [&](double x) {
-      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
-      cmax = b > cmax ? b : cmax;
-      if (b != 0) cmin = b < cmin ? b : cmin;
-    };
-    if (threadIdx.x == 0) {
-      take(tcx);
-      take(tcy);
-    }
-    for (int64_t k = threadIdx.x; k < nz; k += 32) {
-      take(tzc1[k]);
-      take(tzc2[k]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long a = __shfl_xor_sync(0xffffffffu, cmax, o);
-      const unsigned long long b = __shfl_xor_sync(0xffffffffu, cmin, o);
-      cmax = a > cmax ? a : cmax;
-      cmin = b < cmin ? b : cmin;
-    }
-    if (threadIdx.x == 0) {
-      atomicMax(&r[3], cmax);
-      atomicMin(&r[4], cmin);
-    }
   }
 }
 
@@ -622,14 +593,13 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
   if (rc) return rc;
   if (!ctx->advect_guess) {
     unsigned long long* range = reinterpret_cast<unsigned long long*>(scr + kScratchAdvRange);
-    rc = check_cuda(cudaMemsetAsync(range, 0, 4 * sizeof(unsigned long long), st), "advect range init");
-    if (!rc) rc = check_cuda(cudaMemsetAsync(range + 4, 0xff, sizeof(unsigned long long), st), "advect range init");
+    rc = check_cuda(cudaMemsetAsync(range, 0, 3 * sizeof(unsigned long long), st), "advect range init");
     if (rc) return rc;
     const int64_t rows = (u.ny + 2) * (u.nz + 2);
     const int rblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
     advect_range_kernel<<<rblocks, dim3(32, 8), 0, st>>>(
         static_cast<const double*>(u.data), static_cast<const double*>(v.data), static_cast<const double*>(w.data),
-        u.nx, u.ny, u.nz, u.sy, u.sz, tzc1, tzc2, tcx, tcy, range);
+        u.nx, u.ny, u.nz, u.sy, u.sz, range);
     rc = check_cuda(cudaGetLastError(), "advect range kernel");
     if (rc) return rc;
     used = range;
