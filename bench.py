@@ -761,7 +761,8 @@ def apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak):
     """stencil_apply_linear on the 512^3 field: the 7-point and the
     fourth-order 13-point Laplacians with integer weights (the exact
     fixed-point path) and the 7-point average with weights 1/6 (binary64 in
-    the order written).  16 algorithmic bytes per output point."""
+    the order written); stencil_apply_expr on the same field: the 7-point
+    average and a non-linear body.  16 algorithmic bytes per output point."""
     li = S.Field.from_numpy(u0, S.F64, device=dev)
     lo = li.like()
     cases = {
@@ -780,6 +781,22 @@ def apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak):
         S.stencil_ctx_status(ctx)
         gb = 16 * pts / (lms * 1e-3) / 1e9
         out[name] = {"ms": round(lms, 3), "gpts": round(pts / (lms * 1e-3) / 1e9, 2), "terms": len(offs),
+                     "hbm_gbs": round(gb, 1), "frac_of_measured_hbm": round(gb / hbm_peak, 4), "note": note}
+    exprs = {
+        "apply_expr_7pt_sixth_512cubed_f64": (
+            "(a0(0,0,-1) + a0(0,-1,0) + a0(-1,0,0) + a0(1,0,0) + a0(0,1,0) + a0(0,0,1)) / 6",
+            "generated kernel (run-time compiled), binary64 in the expression's order: 5 adds and a divide"),
+        "apply_expr_flux_512cubed_f64": (
+            "a0(0,0,0)*(a0(1,0,0) - a0(-1,0,0)) + a0(0,0,0)*(a0(0,1,0) - a0(0,-1,0))"
+            " - (a0(0,0,1) - a0(0,0,-1))*(a0(0,0,1) + a0(0,0,-1))",
+            "generated kernel, a non-linear body: 9 binary64 operations per point"),
+    }
+    for name, (expr, note) in exprs.items():
+        pts = (N + 2 - 2) ** 3
+        lms = timed_steps(lambda: S.stencil_apply_expr(ctx, [li], lo, expr), 5, 2)
+        S.stencil_ctx_status(ctx)
+        gb = 16 * pts / (lms * 1e-3) / 1e9
+        out[name] = {"ms": round(lms, 3), "gpts": round(pts / (lms * 1e-3) / 1e9, 2),
                      "hbm_gbs": round(gb, 1), "frac_of_measured_hbm": round(gb / hbm_peak, 4), "note": note}
     del li, lo
     return out

@@ -200,6 +200,50 @@ STENCIL_API int stencil_apply_linear(stencil_ctx* ctx, const stencil_grid* in, c
                                      void* stream);
 
 /*
+ * stencil_apply_expr -- the general stencil.apply (Section 2.2: an apply
+ * reads its inputs at constant offsets and yields one value per point of
+ * its output's bounds; its body may be any arithmetic, as in the
+ * Piacsek-Williams products of Section 4.1):
+ *   out(x) = expr, at every point x with r <= index <= n + 1 - r on each
+ *   axis, r = max(1, largest |offset|) (as stencil_apply_linear).
+ * expr is a NUL-terminated expression over the inputs:
+ *   aN(dx,dy,dz)   input N (0 <= N < ninputs) at offset (dx, dy, dz),
+ *                  each offset an integer in -3..3;
+ *   numbers        decimal literals (e.g. 0.25, 6, 1e-3);
+ *   + - * /        left-associative, * and / binding tighter; unary minus;
+ *   ( )            grouping.
+ * Evaluated in binary64, every operation rounded on its own (no fused
+ * multiply-add) in the order the expression's tree gives, so the result is
+ * bitwise that of evaluating the same expression in IEEE binary64.  The
+ * library translates the expression into a CUDA C kernel, compiles it for
+ * the device at run time with the CUDA run-time compiler (NVRTC, loaded on
+ * first use) and keeps it in ctx: the first call with an expression
+ * compiles it (tens of milliseconds), later calls reuse it.
+ *   inputs   HOST array of ninputs (1..8) pointers to F64 grids of equal
+ *            extents and equal strides.
+ *   out      F64 grid of the same extents, distinct from every input;
+ *            points outside the bounds are not written.
+ * Errors: STENCIL_ERR_ARG (syntax, an offset beyond three cells, an input
+ * index beyond ninputs, mismatched grids, aliasing), STENCIL_ERR_DTYPE,
+ * STENCIL_ERR_CUDA (NVRTC unavailable or the compilation failed: the
+ * message carries the compiler log).  Asynchronous after the first call
+ * with an expression (the compilation runs on the host).
+ */
+STENCIL_API int stencil_apply_expr(stencil_ctx* ctx, const stencil_grid* const* inputs,
+                                   int32_t ninputs, const stencil_grid* out,
+                                   const char* expr, void* stream);
+
+/*
+ * stencil_expr_source -- the CUDA C source stencil_apply_expr generates for
+ * expr over ninputs inputs (no device needed): written NUL-terminated into
+ * buf (truncated to len - 1 characters; buf may be NULL to validate only),
+ * the bounds' radius r into *radius (may be NULL).  Errors: STENCIL_ERR_ARG
+ * as stencil_apply_expr.
+ */
+STENCIL_API int stencil_expr_source(const char* expr, int32_t ninputs, char* buf,
+                                    size_t len, int32_t* radius);
+
+/*
  * stencil_average2d -- the paper's running example (Section 2.2, Listing 1):
  * nsweeps sweeps of the four-neighbour average
  *   u'(x, y) = (u(x-1, y) + u(x+1, y) + u(x, y-1) + u(x, y+1)) * 0.25

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -192,6 +193,7 @@ int stencil_ctx_destroy(stencil_ctx* ctx) {
   if (!ctx) return STENCIL_OK;
   DeviceGuard dg(ctx->device);
   int rc = check_cuda(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+  expr_cache_free(ctx);
   cudaFree(ctx->scratch);
   cudaFreeHost(ctx->host_word);
   cudaEventDestroy(ctx->solve_event);
@@ -291,6 +293,39 @@ int stencil_apply_linear(stencil_ctx* ctx, const stencil_grid* in, const stencil
   DeviceGuard dg(ctx->device);
   if (dg.rc) return dg.rc;
   return launch_apply_linear(ctx, gi, go, offsets, coeffs, npoints, static_cast<cudaStream_t>(stream));
+}
+
+int stencil_apply_expr(stencil_ctx* ctx, const stencil_grid* const* inputs, int32_t ninputs,
+                       const stencil_grid* out, const char* expr, void* stream) {
+  if (!ctx) return set_error(STENCIL_ERR_ARG, "apply_expr: null ctx");
+  if (!inputs || ninputs < 1 || ninputs > 8) return set_error(STENCIL_ERR_ARG, "apply_expr: need 1..8 inputs");
+  Grid gi[8], go;
+  int rc = validate_grid(out, "out", &go, false);
+  if (rc) return rc;
+  if (go.dtype != STENCIL_F64) return set_error(STENCIL_ERR_DTYPE, "apply_expr: out must be F64");
+  for (int q = 0; q < ninputs; ++q) {
+    if ((rc = validate_grid(inputs[q], "input", &gi[q], false))) return rc;
+    if ((rc = same_extents(gi[q], go, "input", "out"))) return rc;
+    if (gi[q].dtype != STENCIL_F64) return set_error(STENCIL_ERR_DTYPE, "apply_expr: inputs must be F64");
+    if (gi[q].data == go.data) return set_error(STENCIL_ERR_ARG, "apply_expr: out aliases input %d", q);
+  }
+  DeviceGuard dg(ctx->device);
+  if (dg.rc) return dg.rc;
+  return launch_apply_expr(ctx, gi, ninputs, go, expr, static_cast<cudaStream_t>(stream));
+}
+
+int stencil_expr_source(const char* expr, int32_t ninputs, char* buf, size_t len, int32_t* radius) {
+  std::string src;
+  int r = 1;
+  const int rc = expr_source(expr, ninputs, &src, &r);
+  if (rc) return rc;
+  if (radius) *radius = r;
+  if (buf && len > 0) {
+    const size_t n = std::min(len - 1, src.size());
+    memcpy(buf, src.data(), n);
+    buf[n] = '\0';
+  }
+  return STENCIL_OK;
 }
 
 int stencil_average2d(stencil_ctx* ctx, const stencil_grid* u, const stencil_grid* u_tmp, int64_t nsweeps,

@@ -5,9 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/stencil.h"
 
 namespace stencil {
+struct ExprCache;  // generated stencil.apply kernels of a context (apply_expr.cu)
 // Sweep policies (storage / arithmetic) and the registry of compiled
 // configurations of the sweep kernel, indexed by policy and pass length T.
 enum SweepPolicy { kPolResident = 0, kPolFixed = 1, kPolF64 = 2, kPolF32 = 3, kPolBF16 = 4, kNumPolicies = 5 };
@@ -28,6 +31,7 @@ struct stencil_ctx {
   int resid_guess;   // a residual ran on this ctx: its magnitudes are the next call's scale guess
   int apply_guess;   // the same for the fixed-point linear apply
   int advect_guess;  // the same for the fixed-point advection
+  stencil::ExprCache* expr_cache;  // kernels generated by stencil_apply_expr (null until the first)
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
   unsigned long long* host_word;  // pinned host word (batch solve progress)
@@ -146,5 +150,10 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
                   const Grid& sv, const Grid& sw, const double* tzc1, const double* tzc2,
                   double tcx, double tcy, cudaStream_t st);
 int advect_config_count();
+// General stencil.apply from an expression (apply_expr.cu).
+int expr_source(const char* expr, int ninputs, std::string* src, int* radius);
+int launch_apply_expr(stencil_ctx* ctx, const Grid* in, int ninputs, const Grid& out, const char* expr,
+                      cudaStream_t st);
+void expr_cache_free(stencil_ctx* ctx);
 
 }  // namespace stencil

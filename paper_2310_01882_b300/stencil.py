@@ -68,6 +68,9 @@ SIGNATURES = {
                               ctypes.c_int32, _P], ctypes.c_int),
     "stencil_average2d": ([_P, _G, _G, ctypes.c_int64, _P], ctypes.c_int),
     "stencil_apply_linear": ([_P, _G, _G, _P, _P, ctypes.c_int32, _P], ctypes.c_int),
+    "stencil_apply_expr": ([_P, ctypes.POINTER(_G), ctypes.c_int32, _G, ctypes.c_char_p, _P], ctypes.c_int),
+    "stencil_expr_source": ([ctypes.c_char_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_size_t,
+                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "stencil_redblack_sweep": ([_P, _G, _G, _G, _G, ctypes.c_double, ctypes.c_int64, ctypes.c_int32,
                                 ctypes.c_int32, _P], ctypes.c_int),
     "stencil_residual": ([_P, _G, _G, ctypes.c_double, _G, _P, _P], ctypes.c_int),
@@ -237,6 +240,25 @@ def stencil_apply_linear(ctx, inp, out, offsets, coeffs, stream=None):
     return _check(lib().stencil_apply_linear(ctx.handle, ctypes.byref(gi), ctypes.byref(go),
                                              ctypes.c_void_p(off.ctypes.data), ctypes.c_void_p(c.ctypes.data),
                                              int(c.size) if c.size == off.shape[0] else -1, _stream(stream)))
+
+
+def stencil_apply_expr(ctx, inputs, out, expr, stream=None):
+    """out = expr over the F64 Fields `inputs` (a0, a1, ...) on the points
+    whose reads lie in the field; the kernel is generated from expr and
+    compiled at run time (see include/stencil.h for the grammar)."""
+    grids = [f.grid() for f in inputs]
+    arr = (_G * len(grids))(*[ctypes.pointer(g) for g in grids])
+    go = out.grid()
+    return _check(lib().stencil_apply_expr(ctx.handle, arr, len(grids), ctypes.byref(go), expr.encode(),
+                                           _stream(stream)))
+
+
+def stencil_expr_source(expr, ninputs):
+    """(CUDA C source of the kernel stencil_apply_expr generates, radius)."""
+    buf = ctypes.create_string_buffer(1 << 17)
+    r = ctypes.c_int32(0)
+    _check(lib().stencil_expr_source(expr.encode(), int(ninputs), buf, len(buf), ctypes.byref(r)))
+    return buf.value.decode(), r.value
 
 
 def stencil_average2d(ctx, u, u_tmp, nsweeps, stream=None):

@@ -103,6 +103,10 @@ def test_residual_advect_average_apply_stay_in_bounds(shape):
     offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 1), (1, 1, -1)]
     S.stencil_apply_linear(ctx(), gi.field, go.field, offs, [1.0, -2.0, 0.5, 0.25, 3.0])
     assert gi.intact() and go.intact()
+    ge, gw = Guarded(*shape, values=u), Guarded(*shape, values=f)
+    go2 = Guarded(*shape)
+    S.stencil_apply_expr(ctx(), [ge.field, gw.field], go2.field, "a0(1,0,0)*a1(0,-1,0) - a0(0,0,-1)/2")
+    assert ge.intact() and gw.intact() and go2.intact()
 
 
 def test_batch_solve_stays_in_bounds():

@@ -136,3 +136,50 @@ def test_net_mutation_harness_passes_unmutated(tmp_path):
                           os.path.join(ROOT, "pytest.ini"), "--rootdir", ROOT, str(probe)], cwd=str(tmp_path),
                          env=env, capture_output=True, text=True, timeout=120)
     assert res.returncode == 0, res.stdout[-2000:]
+
+
+EXPR_SRC = os.path.join(ROOT, "oracle", "expr.py")
+EXPR_MUTANTS = {
+    "operands_swapped": ("node = (op, node, self.term())", "node = (op, self.term(), node)"),
+    "product_looser_than_sum": ("node = (op, node, self.unary())", "node = (op, node, self.expr())"),
+    "divide_as_multiply": ('"/": np.divide', '"/": np.multiply'),
+    "minus_dropped": ("return np.negative(ev(node[1]))", "return ev(node[1])"),
+    "y_offset_sign": ("r + dy:ny2 - r + dy", "r - dy:ny2 - r - dy"),
+    "x_and_z_swapped": ("dx, dy, dz = d", "dz, dy, dx = d"),
+    "radius_ignores_z": ("for d in node[2]:", "for d in node[2][:2]:"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EXPR_MUTANTS))
+def test_expr_pins_catch_mutant(name, tmp_path):
+    """The same for the expression oracle (oracle/expr.py)."""
+    import shutil
+    import oracle
+    old, new = EXPR_MUTANTS[name]
+    src = open(EXPR_SRC).read()
+    assert src.count(old) == 1, name
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so", "_build"))
+    (pkg / "expr.py").write_text(src.replace(old, new, 1))
+    env = dict(os.environ, ORACLE_LIB=oracle.lib()._name,
+               PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT, os.environ.get("PYTHONPATH", "")]))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_expr.py")], cwd=str(tmp_path), env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"mutant {name} survived the pins:\n{res.stdout[-2000:]}"
+
+
+def test_expr_mutation_harness_passes_unmutated(tmp_path):
+    """Control: the unmutated copy passes the expression pins."""
+    import shutil
+    import oracle
+    pkg = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg,
+                    ignore=shutil.ignore_patterns("__pycache__", "*.so", "_build"))
+    env = dict(os.environ, ORACLE_LIB=oracle.lib()._name,
+               PYTHONPATH=os.pathsep.join([str(tmp_path), ROOT, os.environ.get("PYTHONPATH", "")]))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_expr.py")], cwd=str(tmp_path), env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:]
