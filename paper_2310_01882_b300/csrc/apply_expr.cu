@@ -116,11 +116,28 @@ struct ExprParser {
       return true;
     }
     if ((c >= '0' && c <= '9') || c == '.') {
-      const char* start = s + pos;
-      char* end = nullptr;
-      const double v = strtod(start, &end);
-      if (end == start) return fail("malformed number");
-      pos += static_cast<size_t>(end - start);
+      // digits [. digits] [(e|E) [+|-] digits], at least one digit before
+      // the exponent (no hexadecimal or other strtod forms)
+      auto digit = [&](size_t q) { return s[q] >= '0' && s[q] <= '9'; };
+      size_t q = pos;
+      int ndig = 0;
+      while (digit(q)) ++q, ++ndig;
+      if (s[q] == '.') {
+        ++q;
+        while (digit(q)) ++q, ++ndig;
+      }
+      if (ndig == 0) return fail("malformed number");
+      if (s[q] == 'e' || s[q] == 'E') {
+        size_t e = q + 1;
+        if (s[e] == '+' || s[e] == '-') ++e;
+        if (digit(e)) {
+          q = e;
+          while (digit(q)) ++q;
+        }
+      }
+      const std::string lit(s + pos, q - pos);
+      pos = q;
+      const double v = strtod(lit.c_str(), nullptr);
       if (!(v - v == 0.0)) return fail("number out of range");
       char b[64];
       snprintf(b, sizeof(b), "%.17g", v);  // round-trips to the same binary64 value

@@ -14,11 +14,13 @@ from paper_2310_01882_b300 import stencil as S
 
 GOOD = [
     ("a0(0,0,0)", 1),
+    ("1.e2*a0(0,0,0) - .5E-1 + 7.", 1),
     ("0.25*(a0(-1,0,0) + a0(1,0,0)) - -a1(0,2,-1)/3", 2),
     ("a0(1,-2,3)*a2(0,0,0) + 1e-3*(a1(0,0,1) - a1(0,0,-1))", 3),
     ("((a0(0,0,0)))", 1),
 ]
-BAD = ["a0(4,0,0)", "a3(0,0,0)", "1 +", "a0(0,0)", "b0(0,0,0)", "((1)", "1e999", "2 3", ""]
+BAD = ["a0(4,0,0)", "a3(0,0,0)", "1 +", "a0(0,0)", "b0(0,0,0)", "((1)", "1e999", "2 3", "", "0x10", "0x1p3",
+       "1e", ".", "1.5.2", "inf", "a0(0,0,0) ^ 2"]
 
 
 @pytest.mark.parametrize("expr,ninputs", GOOD)

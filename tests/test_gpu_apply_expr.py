@@ -21,6 +21,8 @@ EXPRS = [
     ("a0(0,0,0)*a0(0,0,0) - a1(1,0,0)/(1 + a1(0,0,0)*a1(0,0,0))", 2),
     ("-(a0(0,0,1) - a0(0,0,-1)) * 0.5 + a2(3,0,0) - 3*a2(0,-3,2)", 3),
     ("(16*(a0(1,0,0) + a0(-1,0,0)) - (a0(2,0,0) + a0(-2,0,0)) - 30*a0(0,0,0)) / 12", 1),
+    ("1.e2*a0(0,0,0) - .5E-1 + 7. / 3 * 0.1", 1),  # literals round-trip to the same binary64 values
+    (" + ".join(f"a{q}({q % 3 - 1},{(q // 3) % 3 - 1},{q % 2})" for q in range(8)) + " * a7(0,0,-1)", 8),
 ]
 SHAPES = [(1, 1, 1), (9, 8, 7), (67, 35, 19), (130, 17, 40)]
 
