@@ -766,10 +766,10 @@ def apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak):
     li = S.Field.from_numpy(u0, S.F64, device=dev)
     lo = li.like()
     cases = {
-        "apply_linear_7pt_int_512cubed_f64": star_stencil(1, [-6.0, 1.0]) + ("fixed point (integer weights)",),
-        "apply_linear_13pt_r2_int_512cubed_f64": star_stencil(2, [-90.0, 16.0, -1.0])
+        f"apply_linear_7pt_int_{N}cubed_f64": star_stencil(1, [-6.0, 1.0]) + ("fixed point (integer weights)",),
+        f"apply_linear_13pt_r2_int_{N}cubed_f64": star_stencil(2, [-90.0, 16.0, -1.0])
         + ("fixed point (integer weights), radius 2",),
-        "apply_linear_7pt_sixth_512cubed_f64": star_stencil(1, [0.0, 1.0 / 6.0]) + (
+        f"apply_linear_7pt_sixth_{N}cubed_f64": star_stencil(1, [0.0, 1.0 / 6.0]) + (
             "binary64 in the order written (weights 1/6, not integer multiples of a power of two): "
             "FP64-pipe bound",),
     }
@@ -783,10 +783,10 @@ def apply_perf(S, ctx, u0, dev, timed_steps, hbm_peak):
         out[name] = {"ms": round(lms, 3), "gpts": round(pts / (lms * 1e-3) / 1e9, 2), "terms": len(offs),
                      "hbm_gbs": round(gb, 1), "frac_of_measured_hbm": round(gb / hbm_peak, 4), "note": note}
     exprs = {
-        "apply_expr_7pt_sixth_512cubed_f64": (
+        f"apply_expr_7pt_sixth_{N}cubed_f64": (
             "(a0(0,0,-1) + a0(0,-1,0) + a0(-1,0,0) + a0(1,0,0) + a0(0,1,0) + a0(0,0,1)) / 6",
             "generated kernel (run-time compiled), binary64 in the expression's order: 5 adds and a divide"),
-        "apply_expr_flux_512cubed_f64": (
+        f"apply_expr_flux_{N}cubed_f64": (
             "a0(0,0,0)*(a0(1,0,0) - a0(-1,0,0)) + a0(0,0,0)*(a0(0,1,0) - a0(0,-1,0))"
             " - (a0(0,0,1) - a0(0,0,-1))*(a0(0,0,1) + a0(0,0,-1))",
             "generated kernel, a non-linear body: 9 binary64 operations per point"),
