@@ -267,7 +267,7 @@ __device__ __forceinline__ void sts64(uint32_t a, unsigned long long v) {
   asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
 }
 
-template <int R, bool FASTQ, bool EXACT_EXP>
+template <int R, bool FASTQ, bool EXACT_EXP, bool SYM>
 __device__ __forceinline__ void apply_star_march(const double* __restrict__ in, double* __restrict__ out,
                                                  int64_t nx, int64_t ny, int64_t nz, int64_t sy, int64_t sz,
                                                  int64_t osy, int64_t osz, const FxTerms& t, int S, int Cu, int sh,
@@ -324,6 +324,7 @@ __device__ __forceinline__ void apply_star_march(const double* __restrict__ in, 
 #pragma unroll
   for (int d = 0; d < D - 1; ++d) issue(d, rbase + d * kPlaneBytes);
   int WL[ROWS][NW], WH[ROWS][NW];  // own columns: plane n's pre-split value in window slot n mod NW
+  long long WQ[ROWS][NW];          // SYM: plane n's value q in window slot n mod NW
   double* dst = out + i + (oy + ty) * osy + zs * osz;  // row r: + r * 8 osy
   uint32_t qslot = qbase;                               // quantised slot of plane n
   uint32_t rslot = rbase;                               // raw slot of plane n
@@ -344,17 +345,24 @@ __device__ __forceinline__ void apply_star_march(const double* __restrict__ in, 
           const double x = lds64f(rslot + mine8 + m * NT * 8);
           const long long q = (FASTQ && m == 0) ? quant(x) : fx_quant_signed(x, Cu);
           seen = max(seen, static_cast<uint32_t>(__double2hiint(x)) & 0x7fffffffu);
-          sts64(qslot + mine8 + m * NT * 8,
-                (static_cast<unsigned long long>(static_cast<unsigned>(static_cast<int>(q >> 31))) << 32) |
-                    static_cast<unsigned>(q & 0x7fffffff));
+          if constexpr (SYM)
+            sts64(qslot + mine8 + m * NT * 8, static_cast<unsigned long long>(q));
+          else
+            sts64(qslot + mine8 + m * NT * 8,
+                  (static_cast<unsigned long long>(static_cast<unsigned>(static_cast<int>(q >> 31))) << 32) |
+                      static_cast<unsigned>(q & 0x7fffffff));
         }
       }
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         const unsigned long long v = lds64(qslot + own8 + r * kApBY * WX * 8);
-        WL[r][rot] = static_cast<int>(v);
-        WH[r][rot] = static_cast<int>(v >> 32);
+        if constexpr (SYM) {
+          WQ[r][rot] = static_cast<long long>(v);
+        } else {
+          WL[r][rot] = static_cast<int>(v);
+          WH[r][rot] = static_cast<int>(v >> 32);
+        }
       }
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
@@ -362,27 +370,46 @@ __device__ __forceinline__ void apply_star_march(const double* __restrict__ in, 
         // output plane zs + n - 2R: its window slot is rot - R, its ring slot R back
         const uint32_t ws = qslot >= qbase + R * kPlaneBytes ? qslot - R * kPlaneBytes
                                                              : qslot + (NS - R) * kPlaneBytes;
-        // two accumulators per half (terms alternate), so the multiply-add
-        // chains are half as long
-        long long aL[2] = {0, 0}, aH[2] = {0, 0};
+        long long acc;
+        if constexpr (SYM) {
+          // one weight per distance d: w_0 q + sum_d w_d (sum of the six
+          // values at distance d).  Integer adds and multiplies wrap modulo
+          // 2^64, so the result -- the same sum of k_p q_p, which fits in 64
+          // bits -- is exact whatever the intermediate values.
+          auto at = [&](int dx, int dy) -> long long {
+            return static_cast<long long>(
+                lds64(ws + own8 + static_cast<uint32_t>((r * kApBY * WX + dy * WX + dx) * 8)));
+          };
+          acc = static_cast<long long>(t.k[0]) * WQ[r][((rot - R) % NW + NW) % NW];
 #pragma unroll
-        for (int q = 0; q < Sh::N; ++q) {
-          const int dz = Sh::d(q, 2);
-          int l, h;
-          if (dz != 0 || q == 0) {
-            const int wi = ((rot - R + dz) % NW + NW) % NW;
-            l = WL[r][wi];
-            h = WH[r][wi];
-          } else {
-            const unsigned long long v =
-                lds64(ws + own8 + static_cast<uint32_t>((r * kApBY * WX + Sh::d(q, 1) * WX + Sh::d(q, 0)) * 8));
-            l = static_cast<int>(v);
-            h = static_cast<int>(v >> 32);
+          for (int d = 1; d <= R; ++d) {
+            const long long g = (at(-d, 0) + at(d, 0)) + (at(0, -d) + at(0, d)) +
+                                (WQ[r][((rot - R - d) % NW + NW) % NW] + WQ[r][((rot - R + d) % NW + NW) % NW]);
+            acc += static_cast<long long>(t.k[1 + 2 * (d - 1)]) * g;
           }
-          aL[q & 1] = madw(t.k[q], l, aL[q & 1]);
-          aH[q & 1] = madw(t.k[q], h, aH[q & 1]);
+        } else {
+          // two accumulators per half (terms alternate), so the multiply-add
+          // chains are half as long
+          long long aL[2] = {0, 0}, aH[2] = {0, 0};
+#pragma unroll
+          for (int q = 0; q < Sh::N; ++q) {
+            const int dz = Sh::d(q, 2);
+            int l, h;
+            if (dz != 0 || q == 0) {
+              const int wi = ((rot - R + dz) % NW + NW) % NW;
+              l = WL[r][wi];
+              h = WH[r][wi];
+            } else {
+              const unsigned long long v =
+                  lds64(ws + own8 + static_cast<uint32_t>((r * kApBY * WX + Sh::d(q, 1) * WX + Sh::d(q, 0)) * 8));
+              l = static_cast<int>(v);
+              h = static_cast<int>(v >> 32);
+            }
+            aL[q & 1] = madw(t.k[q], l, aL[q & 1]);
+            aH[q & 1] = madw(t.k[q], h, aH[q & 1]);
+          }
+          acc = (aH[0] + aH[1]) * (1ll << 31) + (aL[0] + aL[1]);
         }
-        const long long acc = (aH[0] + aH[1]) * (1ll << 31) + (aL[0] + aL[1]);
         double vout;
         if (bad) {
           vout = __longlong_as_double(0x7ff8000000000000ll);
@@ -467,7 +494,7 @@ __global__ void __launch_bounds__(kApBX * kApBY)
   apply_publish(ps.seen, seen);
 }
 
-template <int R>
+template <int R, bool SYM>
 __global__ void __launch_bounds__(kApBX * kApBY, 3)
     apply_star_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t nx, int64_t ny, int64_t nz,
                       int64_t sy, int64_t sz, int64_t osy, int64_t osz, const __grid_constant__ FxTerms t,
@@ -483,13 +510,13 @@ __global__ void __launch_bounds__(kApBX * kApBY, 3)
   const bool fastq = S >= 0 && S <= 1000;
   uint32_t seen = 0;
   if (fastq && exact_exp)
-    apply_star_march<R, true, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk,
+    apply_star_march<R, true, true, SYM>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk,
                                     seen);
   else if (exact_exp)
-    apply_star_march<R, false, true>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk,
+    apply_star_march<R, false, true, SYM>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk,
                                      seen);
   else
-    apply_star_march<R, false, false>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk,
+    apply_star_march<R, false, false, SYM>(in, out, nx, ny, nz, sy, sz, osy, osz, t, S, 1085 - S, sh, bad != 0, zchunk,
                                       seen);
   apply_publish(ps.seen, seen);
 }
@@ -610,7 +637,18 @@ int launch_apply_linear(stencil_ctx* ctx, const Grid& in, const Grid& out, const
         grid = dim3(static_cast<unsigned>((ox + kApBX - 1) / kApBX), static_cast<unsigned>((oy + sty - 1) / sty),
                     static_cast<unsigned>((oz + zc - 1) / zc));
         smem = R == 1 ? ApStar<1>::kSmem : (R == 2 ? ApStar<2>::kSmem : ApStar<3>::kSmem);
-        kern = R == 1 ? apply_star_kernel<1> : (R == 2 ? apply_star_kernel<2> : apply_star_kernel<3>);
+        // one weight per distance (every +-d offset on every axis alike, as
+        // in the isotropic Laplacians): the neighbours at a distance are
+        // summed first, one multiply per distance
+        bool sym = true;
+        for (int d = 1; d <= r; ++d)
+          for (int q = 0; q < 6; ++q)
+            if (t.k[1 + (q / 2) * 2 * r + 2 * (d - 1) + (q & 1)] != t.k[1 + 2 * (d - 1)]) sym = false;
+        if (sym)
+          kern = R == 1 ? apply_star_kernel<1, true> : (R == 2 ? apply_star_kernel<2, true> : apply_star_kernel<3, true>);
+        else
+          kern = R == 1 ? apply_star_kernel<1, false>
+                        : (R == 2 ? apply_star_kernel<2, false> : apply_star_kernel<3, false>);
       } else {
         zc = std::max<int64_t>(8, (oz * tiles + 8 * ctx->num_sms - 1) / (8 * ctx->num_sms));
         zc = std::min<int64_t>(zc, oz);

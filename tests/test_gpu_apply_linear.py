@@ -77,6 +77,13 @@ INT_STENCILS = {
     "laplacian7": star(1, [-6.0, 1.0]),
     "laplacian13_4th": star(2, [-90.0, 16.0, -1.0]),       # 12 h^2 times the fourth-order Laplacian
     "star19_r3": star(3, [-25.0, 3.0, -2.0, 1.0]),
+    # stars whose weights differ by axis and sign (the general star path) and
+    # a symmetric one with a zero weight at one distance
+    "star13_uneven": (star(2, [0.0] * 3)[0],
+                      [float(v) for v in np.random.default_rng(1).integers(-40, 41, 13)]),
+    "star19_uneven_r3": (star(3, [0.0] * 4)[0],
+                         [float(v) for v in np.random.default_rng(2).integers(-40, 41, 19)]),
+    "star13_sym_zero_d2": star(2, [4.0, -1.0, 0.0]),
     "average4": ([(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0)], [0.25] * 4),
     "box27": ([(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)],
               [float(v) for v in np.random.default_rng(0).integers(-9, 10, 27)]),
