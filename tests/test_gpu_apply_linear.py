@@ -108,6 +108,20 @@ def test_integer_weights_exact_on_integer_inputs(name, shape):
     assert np.array_equal(run(u, offs, coef, out0), oracle.apply_linear(u, offs, coef, out=out0))
 
 
+@pytest.mark.parametrize("name", ["laplacian7", "laplacian13_4th", "star19_r3", "star13_uneven", "box27", "random_r2"])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 3, 2), (3, 3, 3), (1, 40, 33), (37, 1, 5), (5, 6, 1)])
+def test_integer_weights_tiny_and_thin_grids(name, shape):
+    """Grids whose output bounds are empty, a single point or one cell
+    thick at the stencil's radius: the fixed-point paths write exactly the
+    oracle's points (bitwise on integer-valued inputs) and nothing else."""
+    nx, ny, nz = shape
+    offs, coef = INT_STENCILS[name]
+    rng = np.random.default_rng(sum(shape) * 7 + len(offs))
+    u = rng.integers(-1000, 1001, (nz + 2, ny + 2, nx + 2)).astype(np.float64)
+    out0 = rng.standard_normal(u.shape)
+    assert np.array_equal(run(u, offs, coef, out0), oracle.apply_linear(u, offs, coef, out=out0))
+
+
 @pytest.mark.parametrize("name", sorted(INT_STENCILS))
 def test_integer_weights_on_smooth_and_random_fields(name):
     """General binary64 inputs: the fixed-point sum is exact up to the
