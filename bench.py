@@ -51,16 +51,16 @@ ALGO_BYTES = {"f64": 24, "f32": 12, "bf16": 6}   # read u, read f, write u' per 
 #   python bench.py --grid 320 --sweeps 8 --only f64 --steps 1 --warmup 1 --no-cpu --f64-config i
 _SCALE_320 = (512 / 320) ** 3
 MEASURED_TRAFFIC = {
-    "jacobi_tb<PolResident,T=1,R=4,WY=16,S=5>": (574407680 + 233541120) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=6>": (550171904 + 234793984) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=5>": (550025984 + 235125504) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=2,WY=8,S=5>": (547156736 + 234843136) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (567644160 + 231931648) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (587555584 + 232088832) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (571086336 + 232422400) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (574176768 + 234781440) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=1,WY=16,S=5>": (565510400 + 238744320) * _SCALE_320,
-    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (564643840 + 230349312) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=16,S=5>": (576382464 + 233808640) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=6>": (550465024 + 235093248) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=16,S=5>": (550335488 + 235381248) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=2,WY=8,S=5>": (547666688 + 235258368) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=8,S=5>": (568621568 + 231979776) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=4>": (587781632 + 232406528) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=4,S=6>": (570871808 + 232552960) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=8,WY=8,S=4>": (575851520 + 235176704) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=1,WY=16,S=5>": (565452800 + 238698752) * _SCALE_320,
+    "jacobi_tb<PolResident,T=1,R=4,WY=4,S=6>": (564600576 + 231073792) * _SCALE_320,
 }
 
 
