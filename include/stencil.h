@@ -338,7 +338,8 @@ STENCIL_API int stencil_residual_config_select(stencil_ctx* ctx, int32_t index);
 
 /*
  * The same for stencil_advect_uvw's fixed-point kernel (its thread-block
- * shape and CTAs per SM): the number of compiled configurations, and the
+ * shape, CTAs per SM and z chunk length): the number of compiled
+ * configurations, and the
  * one ctx uses (index 0 unless selected).  Errors: STENCIL_ERR_ARG (null
  * count or ctx, index out of range).
  */

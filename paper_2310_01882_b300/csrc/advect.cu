@@ -24,15 +24,15 @@
 // When the fields' magnitudes differ by more than 2^8, or the factors' do,
 // or a value is not finite, a single scale would cost the smaller field its
 // precision, so the launch evaluates the formula in binary64 instead (the
-// decision is taken on the device from the range reduction: the call stays
-// asynchronous).
+// decision is taken on the device from the magnitudes the pass read: the
+// call stays asynchronous).
 //
 // Each CTA owns a 32 x (RPT BY) column of cells and marches up a chunk of
-// z planes: every plane of u, v, w is loaded once (coalesced, one plane
-// ahead in registers), quantised once into a ring of four shared-memory
-// plane slots, and each thread computes su, sv, sw of its RPT cells from
-// the three slots around them -- one CTA barrier per plane.  48 algorithmic bytes per
-// cell (three fields in, three out).  The quantisation and the final
+// z planes (48 by default): every plane of u, v, w is loaded once
+// (coalesced, one plane ahead in registers), quantised once into a ring of
+// four shared-memory plane slots, and each thread computes su, sv, sw of
+// its RPT cells from the three slots around them -- one CTA barrier per
+// plane.  48 algorithmic bytes per cell (three fields in, three out).  The quantisation and the final
 // rounding run as 64-bit conversions on B300's FP64 pipe (about two per
 // clock per SM), so the integer pipes keep the products.
 // (Computing sw in binary64 on the FP64 pipe while su and sv use the
@@ -80,10 +80,15 @@ __global__ void advect_range_kernel(const double* __restrict__ u, const double* 
   }
 }
 
-// Largest and smallest nonzero |factor| (tcx, tcy, tzc1[], tzc2[]) as bits
-// into a[3], a[4] and b[3], b[4] (one warp).
+// A magnitude record (5 x uint64, zeroed = nothing recorded, every entry
+// raised with atomicMax): the bits of max |u|, |v|, |w| (high words, see
+// adv_scales), the bits of the largest |factor| (tcx, tcy, tzc1[], tzc2[])
+// and the complement of the bits of the smallest nonzero |factor|.
+//
+// The factors' entries of a context's first record (one warp; the fields'
+// entries come from advect_range_kernel).
 __global__ void advect_factor_kernel(const double* __restrict__ tzc1, const double* __restrict__ tzc2, int64_t nz,
-                                     double tcx, double tcy, unsigned long long* a, unsigned long long* b) {
+                                     double tcx, double tcy, unsigned long long* rec) {
   unsigned long long cmax = 0, cmin = ~0ull;
   auto take = [&](double x) {
     const unsigned long long v = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
@@ -105,8 +110,8 @@ __global__ void advect_factor_kernel(const double* __restrict__ tzc1, const doub
     cmin = y < cmin ? y : cmin;
   }
   if (threadIdx.x == 0) {
-    a[3] = b[3] = cmax;
-    a[4] = b[4] = cmin;
+    rec[3] = cmax;
+    rec[4] = ~cmin;
   }
 }
 
@@ -149,6 +154,12 @@ __device__ __forceinline__ AdvScales adv_scales(const unsigned long long* rb) {
   sc.Q = 2 * sc.S + sc.T - 128;
   sc.fixed = true;
   return sc;
+}
+
+// The scales a magnitude record gives.
+__device__ __forceinline__ AdvScales adv_scales_rec(const unsigned long long* rec) {
+  const unsigned long long r[5] = {rec[0], rec[1], rec[2], rec[3], ~rec[4]};
+  return adv_scales(r);
 }
 
 // round(x 2^S) for |x| 2^S <= 2^62 (half away from zero; zero and subnormal
@@ -302,7 +313,7 @@ struct AdvGeom {
   static constexpr int kSlot = 3 * PL;            // u, v, w of one plane
   static constexpr int kSmem = 4 * kSlot * 8;
 };
-constexpr int kAdvZcMax = 64;  // z planes per CTA at most (factor table size)
+constexpr int kAdvZcMax = 128;  // z planes per CTA at most (factor table size)
 
 // The fixed-point z march of one CTA.  FAST: the conversions leave the
 // integer pipes -- a value is quantised as trunc(x 2^S) by adding S to its
@@ -446,16 +457,23 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
   }
 }
 
-// One pass of the advection: the magnitudes it takes its scales from
-// (`used`: the kScratchAdvRange layout), where it records the fields'
-// magnitudes it reads (`seen`), and the flag that makes it run (null:
-// always).
+// One pass of the advection.  The first pass takes its scales from the
+// record `prev` (the previous call's, or the range pass's on a context's
+// first call) and records into `cur` the magnitudes it reads: the fields'
+// and the factors' (tcx, tcy and the tzc entries of its planes).  The
+// second pass compares the decision (fixed point or binary64) and the
+// scales that `prev` gave with those of what the first pass read, and
+// runs only when they differ, with the scales of `cur`; it records nothing
+// and clears `next`, the record the next call's first pass fills.
 struct AdvPass {
-  const unsigned long long* used;
-  unsigned long long* seen;
-  const uint32_t* run_flag;
+  const unsigned long long* prev;
+  unsigned long long* cur;
+  unsigned long long* next;
+  int second;
 };
 
+// Each CTA owns one column of 32 x (BY RPT) cells (blockIdx.x, blockIdx.y)
+// and one chunk of zc planes (blockIdx.z).
 template <bool POW2, int BY, int MINB, bool FASTCVT, int QF = 3, int RPT = 1>
 __global__ void __launch_bounds__(32 * BY, MINB)
     advect_kernel(const double* __restrict__ u, const double* __restrict__ v, const double* __restrict__ w,
@@ -463,19 +481,45 @@ __global__ void __launch_bounds__(32 * BY, MINB)
                   const double* __restrict__ tzc1, const double* __restrict__ tzc2, double tcx, double tcy,
                   int64_t nx, int64_t ny, int64_t nz, int64_t sy, int64_t sz, int64_t osy, int64_t osz,
                   int zc, const AdvPass ps) {
-  if (ps.run_flag && *ps.run_flag == 0u) return;  // uniform
   __shared__ long long zfac[2 * kAdvZcMax];  // tzc1, tzc2 of the chunk's planes at scale T
-  const AdvScales sc = adv_scales(ps.used);
+  __shared__ unsigned long long fac[2];      // largest |factor| read, complement of the smallest nonzero (bits)
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  AdvScales sc;
+  if (ps.second) {
+    const AdvScales x = adv_scales_rec(ps.prev), y = adv_scales_rec(ps.cur);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
+      for (int f = 0; f < 5; ++f) ps.next[f] = 0ull;
+    if (x.fixed == y.fixed && (!x.fixed || (x.S == y.S && x.T == y.T))) return;  // uniform
+    sc = y;
+  } else {
+    sc = adv_scales_rec(ps.prev);
+  }
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * 32;  // halo index of the plane box's first column
   const int64_t j0 = static_cast<int64_t>(blockIdx.y) * BY * RPT;
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * zc;
   const int kn = static_cast<int>(min(static_cast<int64_t>(zc), nz - k0));  // cells of this chunk along z
+  if (!ps.second) {
+    // the factors this chunk reads (tcx, tcy and its planes' tzc1, tzc2),
+    // gathered in shared memory
+    auto take = [&](double x) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
+      atomicMax(&fac[0], b);
+      if (b != 0) atomicMax(&fac[1], ~b);
+    };
+    if (tid == 0) fac[0] = fac[1] = 0ull;
+    __syncthreads();
+    if (tid == 0) {
+      take(tcx);
+      take(tcy);
+    }
+    if (tid < 2 * kn) take((tid & 1) ? tzc2[k0 + (tid >> 1)] : tzc1[k0 + (tid >> 1)]);
+  }
   uint32_t mx[3] = {0u, 0u, 0u};  // largest high words of |u|, |v|, |w| read
   if (!sc.fixed) {  // uniform over the launch
     // the magnitudes of the cells the fixed-point path would have loaded
     // (this CTA's box, halo included), then binary64 cell by cell
     const int PXb = 34, PYb = BY * RPT + 2;
-    for (int e = threadIdx.y * 32 + threadIdx.x; e < PXb * PYb; e += 32 * BY) {
+    for (int e = tid; e < PXb * PYb; e += 32 * BY) {
       const int64_t gi = i0 + e % PXb, gj = j0 + e / PXb;
       if (gi > nx + 1 || gj > ny + 1) continue;
       for (int kk = 0; kk <= kn + 1; ++kk) {
@@ -503,53 +547,45 @@ __global__ void __launch_bounds__(32 * BY, MINB)
     advect_march<POW2, BY, false, 3, RPT>(u, v, w, su, sv, sw, tzc1, tzc2, tcx, tcy, nx, ny, sy, sz, osy, osz, i0,
                                           j0, k0, kn, sc, zfac, mx);
   }
-  // publish (every thread of every warp arrives here)
+  if (ps.second) return;  // uniform
+  // record (every thread of every warp arrives here)
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     const uint32_t m = __reduce_max_sync(0xffffffffu, mx[f]);
     if ((threadIdx.x & 31) == 0 && m)
-      atomicMax(ps.seen + f, (static_cast<unsigned long long>(m) << 32) | 0xffffffffull);
+      atomicMax(ps.cur + f, (static_cast<unsigned long long>(m) << 32) | 0xffffffffull);
   }
-}
-
-// Accepts the first pass if the magnitudes it read lead to the same
-// decision (fixed point or binary64) and the same scales as those it used;
-// otherwise the second pass runs with the magnitudes read.  The fields'
-// magnitudes read become the next call's guess.
-__global__ void advect_check_kernel(const unsigned long long* used, const unsigned long long* __restrict__ seen,
-                                    unsigned long long* __restrict__ final_bits, uint32_t* __restrict__ redo,
-                                    unsigned long long* guess) {
-  unsigned long long a[5], b[5];
-  for (int f = 0; f < 5; ++f) {
-    a[f] = used[f];
-    b[f] = seen[f];
+  __syncthreads();
+  if (tid == 0) {
+    if (fac[0]) atomicMax(ps.cur + 3, fac[0]);
+    if (fac[1]) atomicMax(ps.cur + 4, fac[1]);
   }
-  const AdvScales x = adv_scales(a), y = adv_scales(b);
-  const bool ok = x.fixed == y.fixed && (!x.fixed || (x.S == y.S && x.T == y.T));
-  for (int f = 0; f < 5; ++f) final_bits[f] = ok ? a[f] : b[f];
-  *redo = ok ? 0u : 1u;
-  for (int f = 0; f < 3; ++f) guess[f] = b[f];
 }
 
 // Compiled tile shapes (thread rows BY, CTAs per SM, fields quantised on
-// the FP64 pipe QF, rows per thread RPT); index 0 is the default, the
-// fastest at 512 x 512 x 256 (two rows per thread and one field quantised in
-// integer instructions gained 5% over one row and three fields; four rows
-// per thread lost 30%).
+// the FP64 pipe QF, rows per thread RPT) and the longest z chunk (zc, at
+// most kAdvZcMax), fastest first at 512 x 512 x 256: two rows per thread
+// and one field quantised in integer instructions gained 5% over one row
+// and three fields (four rows per thread lost 30%); chunks of 48 or 64
+// planes beat 32 by 1% (each chunk re-reads and re-quantises two planes and
+// fills its ring before its first output plane; that outweighs the last,
+// partly filled round of CTAs), 16 to 30 planes were slower than 32.
 using AdvKernel = void (*)(const double*, const double*, const double*, double*, double*, double*, const double*,
                            const double*, double, double, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t,
                            int64_t, int, AdvPass);
 struct AdvVariant {
   int BY, minb, rpt;  // thread rows, CTAs per SM, rows per thread
+  int zc;             // longest z chunk
   AdvKernel kern[2];  // tcx, tcy general / powers of two
   int smem;
 };
-#define STENCIL_ADV_VARIANT(BY, MINB, QF, RPT)                                            \
-  {BY, MINB, RPT, {advect_kernel<false, BY, MINB, true, QF, RPT>, advect_kernel<true, BY, MINB, true, QF, RPT>}, \
+#define STENCIL_ADV_VARIANT(BY, MINB, QF, RPT, ZC)                                                          \
+  {BY, MINB, RPT, ZC, {advect_kernel<false, BY, MINB, true, QF, RPT>, advect_kernel<true, BY, MINB, true, QF, RPT>}, \
    AdvGeom<BY, RPT>::kSmem}
 const AdvVariant kAdvVariants[] = {
-    STENCIL_ADV_VARIANT(8, 3, 2, 2), STENCIL_ADV_VARIANT(8, 3, 1, 2), STENCIL_ADV_VARIANT(8, 3, 3, 2),
-    STENCIL_ADV_VARIANT(4, 6, 2, 2), STENCIL_ADV_VARIANT(8, 3, 2, 1),
+    STENCIL_ADV_VARIANT(8, 3, 2, 2, 48), STENCIL_ADV_VARIANT(8, 3, 2, 2, 64), STENCIL_ADV_VARIANT(8, 3, 2, 2, 32),
+    STENCIL_ADV_VARIANT(8, 3, 2, 2, 128), STENCIL_ADV_VARIANT(8, 3, 3, 2, 64), STENCIL_ADV_VARIANT(8, 3, 1, 2, 64),
+    STENCIL_ADV_VARIANT(8, 3, 2, 1, 64), STENCIL_ADV_VARIANT(4, 6, 2, 2, 64),
 };
 #undef STENCIL_ADV_VARIANT
 constexpr int kNumAdvVariants = sizeof(kAdvVariants) / sizeof(kAdvVariants[0]);
@@ -568,45 +604,13 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
   const AdvVariant& av =
       kAdvVariants[(ctx->advect_choice >= 0 && ctx->advect_choice < kNumAdvVariants) ? ctx->advect_choice : 0];
   const int64_t gx = (u.nx + 31) / 32, gy = (u.ny + av.BY * av.rpt - 1) / (av.BY * av.rpt);
-  // z chunk: the longest (up to 32 planes) that still gives every SM several
-  // CTAs to interleave
-  int zc = 32;
-  while (zc > 4 && gx * gy * ((u.nz + zc - 1) / zc) < int64_t(4) * av.minb * ctx->num_sms) zc /= 2;
+  // z chunk: the longest (up to the shape's, and to what the factor table
+  // holds when one thread fills each entry) that still gives every SM two
+  // rounds of CTAs
+  int zc = std::min(av.zc, std::min(kAdvZcMax, 16 * av.BY));
+  while (zc > 4 && gx * gy * ((u.nz + zc - 1) / zc) < int64_t(2) * av.minb * ctx->num_sms) zc /= 2;
   const int64_t gz = (u.nz + zc - 1) / zc;
   if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return set_error(STENCIL_ERR_ARG, "advect: grid too large");
-  // The scales: the first call on a context measures the magnitudes with a
-  // range pass; later calls take the previous call's field magnitudes as the
-  // guess (the factors' magnitudes are measured every call: a one-warp
-  // kernel over nz values).  The pass records the fields' magnitudes it
-  // reads; a one-thread check keeps its output only if they lead to the same
-  // decision and scales, otherwise a second pass (launched every call,
-  // returning at once when not needed) recomputes with them -- the output
-  // is a function of the input alone, and a call whose magnitudes keep the
-  // previous scales reads u, v, w once.
-  unsigned char* scr = ctx->scratch;
-  auto* guess = reinterpret_cast<unsigned long long*>(scr + kScratchAdvGuess);
-  auto* seen = reinterpret_cast<unsigned long long*>(scr + kScratchAdvSeen);
-  auto* final_bits = reinterpret_cast<unsigned long long*>(scr + kScratchAdvFinal);
-  auto* redo = reinterpret_cast<uint32_t*>(scr + kScratchAdvRedo);
-  unsigned long long* used = guess;
-  int rc = check_cuda(cudaMemsetAsync(seen, 0, 3 * sizeof(unsigned long long), st), "advect magnitude init");
-  if (rc) return rc;
-  if (!ctx->advect_guess) {
-    unsigned long long* range = reinterpret_cast<unsigned long long*>(scr + kScratchAdvRange);
-    rc = check_cuda(cudaMemsetAsync(range, 0, 3 * sizeof(unsigned long long), st), "advect range init");
-    if (rc) return rc;
-    const int64_t rows = (u.ny + 2) * (u.nz + 2);
-    const int rblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
-    advect_range_kernel<<<rblocks, dim3(32, 8), 0, st>>>(
-        static_cast<const double*>(u.data), static_cast<const double*>(v.data), static_cast<const double*>(w.data),
-        u.nx, u.ny, u.nz, u.sy, u.sz, range);
-    rc = check_cuda(cudaGetLastError(), "advect range kernel");
-    if (rc) return rc;
-    used = range;
-  }
-  advect_factor_kernel<<<1, 32, 0, st>>>(tzc1, tzc2, u.nz, tcx, tcy, used, seen);
-  rc = check_cuda(cudaGetLastError(), "advect factor kernel");
-  if (rc) return rc;
   // tcx and tcy positive powers of two (within the fixed-point range): their
   // factor products are shifts (the quantised factor is then exactly
   // 2^(m + T), see hfactor)
@@ -616,9 +620,43 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
   };
   const bool p2 = pow2(tcx) && pow2(tcy);
   auto kern = av.kern[p2 ? 1 : 0];
-  rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, av.smem),
-                  "advect smem attribute");
+  int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, av.smem),
+                      "advect smem attribute");
   if (rc) return rc;
+  // The scales.  Each call's first pass takes them from the previous call's
+  // record (a context's first call measures the magnitudes with a range
+  // pass and a one-warp pass over the factors) and records what it reads;
+  // its second pass (launched every call, returning at once when not
+  // needed) recomputes with the recorded magnitudes when they lead to
+  // another decision or other scales -- the output is a function of the
+  // input alone, and a call whose magnitudes keep the previous scales reads
+  // u, v, w once.  Three records rotate: the previous call's, this call's,
+  // and the next call's (cleared by this call's second pass).
+  unsigned char* scr = ctx->scratch;
+  auto* rec = reinterpret_cast<unsigned long long*>(scr + kScratchAdvRec);
+  const int pos = ctx->advect_pos;
+  unsigned long long* cur = rec + 5 * pos;
+  unsigned long long* next = rec + 5 * ((pos + 1) % 3);
+  const unsigned long long* prev = rec + 5 * ((pos + 2) % 3);
+  if (!ctx->advect_guess) {
+    unsigned long long* range = reinterpret_cast<unsigned long long*>(scr + kScratchAdvRange);
+    rc = check_cuda(cudaMemsetAsync(rec, 0, 15 * sizeof(unsigned long long), st), "advect record init");
+    if (rc) return rc;
+    rc = check_cuda(cudaMemsetAsync(range, 0, 5 * sizeof(unsigned long long), st), "advect range init");
+    if (rc) return rc;
+    const int64_t rows = (u.ny + 2) * (u.nz + 2);
+    const int rblocks = static_cast<int>(std::min<int64_t>((rows + 7) / 8, 8 * ctx->num_sms));
+    advect_range_kernel<<<rblocks, dim3(32, 8), 0, st>>>(
+        static_cast<const double*>(u.data), static_cast<const double*>(v.data), static_cast<const double*>(w.data),
+        u.nx, u.ny, u.nz, u.sy, u.sz, range);
+    rc = check_cuda(cudaGetLastError(), "advect range kernel");
+    if (rc) return rc;
+    advect_factor_kernel<<<1, 32, 0, st>>>(tzc1, tzc2, u.nz, tcx, tcy, range);
+    rc = check_cuda(cudaGetLastError(), "advect factor kernel");
+    if (rc) return rc;
+    prev = range;
+  }
+  ctx->advect_guess = 0;  // until both passes are enqueued
   const dim3 block(32, av.BY);
   const dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy), static_cast<unsigned>(gz));
   auto launch = [&](const AdvPass& ps) {
@@ -628,13 +666,11 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
         static_cast<double*>(sw.data), tzc1, tzc2, tcx, tcy, u.nx, u.ny, u.nz, u.sy, u.sz, su.sy, su.sz, zc, ps);
     return check_cuda(cudaGetLastError(), "advect kernel");
   };
-  rc = launch(AdvPass{used, seen, nullptr});
+  rc = launch(AdvPass{prev, cur, next, 0});
   if (rc) return rc;
-  advect_check_kernel<<<1, 1, 0, st>>>(used, seen, final_bits, redo, guess);
-  rc = check_cuda(cudaGetLastError(), "advect check kernel");
+  rc = launch(AdvPass{prev, cur, next, 1});
   if (rc) return rc;
-  rc = launch(AdvPass{final_bits, seen, redo});
-  if (rc) return rc;
+  ctx->advect_pos = (pos + 1) % 3;
   ctx->advect_guess = 1;
   return STENCIL_OK;
 }

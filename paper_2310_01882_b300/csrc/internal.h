@@ -31,6 +31,7 @@ struct stencil_ctx {
   int resid_guess;   // a residual ran on this ctx: its magnitudes are the next call's scale guess
   int apply_guess;   // the same for the fixed-point linear apply
   int advect_guess;  // the same for the fixed-point advection
+  int advect_pos;    // which of the three advection magnitude records this call fills
   stencil::ExprCache* expr_cache;  // kernels generated by stencil_apply_expr (null until the first)
   unsigned char* scratch;  // device memory owned by the ctx
   size_t scratch_bytes;
@@ -48,7 +49,7 @@ constexpr uint32_t kStatusRange = 4u;
 
 // Layout of the ctx scratch block (device memory).
 constexpr size_t kScratchStatus = 0;      // uint32 status bits
-constexpr size_t kScratchAdvRange = 32;   // 5 x uint64: max|u|, max|v|, max|w|, max and min nonzero |coef|
+constexpr size_t kScratchAdvRange = 32;   // 5 x uint64: an advection magnitude record (advect.cu), first call
 constexpr size_t kScratchRange = 176;     // 3 x uint64 bits: max|u| halo, max|f|, max|u| interior
 constexpr size_t kScratchFxMag = 208;     // 4 x uint32: fixed-point magnitude keys (ring of 3)
 constexpr size_t kScratchFxScale = 224;   // 4 x int32: fixed-point scales (ring of 3)
@@ -75,11 +76,10 @@ constexpr size_t kScratchApplyGuess = kScratchGuess;        // 1 x uint64 each: 
 constexpr size_t kScratchApplySeen = kScratchGuess + 8;
 constexpr size_t kScratchApplyFinal = kScratchGuess + 16;
 constexpr size_t kScratchApplyRedo = kScratchGuess + 24;    // uint32
-constexpr size_t kScratchAdvGuess = kScratchGuess + 32;     // 5 x uint64 each (kScratchAdvRange layout)
-constexpr size_t kScratchAdvSeen = kScratchGuess + 72;
-constexpr size_t kScratchAdvFinal = kScratchGuess + 112;
-constexpr size_t kScratchAdvRedo = kScratchGuess + 152;     // uint32
-constexpr size_t kScratchBytes = kScratchGuess + 160;
+// advection: three magnitude records of 5 x uint64 (the kScratchAdvRange
+// layout) in rotation: the previous call's, this call's, the next call's
+constexpr size_t kScratchAdvRec = kScratchGuess + 32;
+constexpr size_t kScratchBytes = kScratchGuess + 152;
 
 // Internal dtype code: biased 64-bit fixed-point iterate (never in the ABI).
 constexpr int kDtypeU64 = 100;

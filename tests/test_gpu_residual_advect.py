@@ -249,38 +249,48 @@ def test_advect_every_config():
 
 def test_advect_scales_follow_each_input():
     """The advection's scales (and its choice between fixed point and
-    binary64) come from the magnitudes of what its pass reads.  A context
-    reuses the previous call's magnitudes as the guess and repeats the pass
-    when the guess leads elsewhere.  On one context, winds scaled by 1e-150,
-    1e+150, 1, 1 again, then uneven magnitudes (w times 1e-7: binary64),
-    then 1 again each match the oracle and equal bit for bit a fresh
-    context's first call on the same input."""
+    binary64) come from the magnitudes of what its pass reads, the fields'
+    and the factors'.  A context reuses the previous call's magnitudes as
+    the guess and repeats the pass when the guess leads elsewhere.  On one
+    context, winds scaled by 1e-150, 1e+150, 1, 1 again, then uneven
+    magnitudes (w times 1e-7: binary64), then 1 again, then factors tzc1,
+    tzc2 scaled by 2^-40 (another factor scale), factors of uneven
+    magnitudes (tzc1 times 1e-5: binary64), the first factors again, and
+    tcy = 0.3 (multiplied, not shifted) each match the oracle and equal bit
+    for bit a fresh context's first call on the same input."""
     import torch
     from paper_2310_01882_b300.stencil import Context
     nx, ny, nz = 37, 29, 13
     u0, v0, w0 = inputs.winds(nx, ny, nz, seeds=(51, 52, 53))
-    t1, t2 = inputs.tzc(nz, 7), inputs.tzc(nz, 8)
-    d1, d2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
+    t10, t20 = inputs.tzc(nz, 7), inputs.tzc(nz, 8)
     shared = Context(0)
 
-    def go(c, u, v, w):
+    def go(c, u, v, w, t1, t2, tcy):
         fu, fv, fw = (S.Field.from_numpy(a) for a in (u, v, w))
+        d1, d2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
         outs = [fu.like() for _ in range(3)]
-        S.stencil_advect_uvw(c, fu, fv, fw, *outs, d1, d2, 0.25, 0.25)
+        S.stencil_advect_uvw(c, fu, fv, fw, *outs, d1, d2, 0.25, tcy)
         torch.cuda.synchronize()
         return [o.to_numpy() for o in outs]
 
-    for case in ("tiny", "huge", "one", "one", "uneven", "one"):
+    cases = ("tiny", "huge", "one", "one", "uneven", "one", "tzc_small", "tzc_uneven", "one", "tcy", "one")
+    for case in cases:
         sc = {"tiny": 1e-150, "huge": 1e150}.get(case, 1.0)
         u, v, w = sc * u0, sc * v0, sc * w0
         if case == "uneven":
             w = 1e-7 * w
-        ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, 0.25)
-        got = go(shared, u, v, w)
+        t1, t2 = t10, t20
+        if case == "tzc_small":
+            t1, t2 = t10 * 2.0 ** -40, t20 * 2.0 ** -40
+        elif case == "tzc_uneven":
+            t1 = t10 * 1e-5
+        tcy = 0.3 if case == "tcy" else 0.25
+        ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, tcy)
+        got = go(shared, u, v, w, t1, t2, tcy)
         for g, r in zip(got, ref):
             assert rel_err(g, r) <= 1e-13, case
         fresh = Context(0)
-        again = go(fresh, u, v, w)
+        again = go(fresh, u, v, w, t1, t2, tcy)
         fresh.close()
         for g, a in zip(got, again):
             assert np.array_equal(g, a), case
@@ -288,13 +298,30 @@ def test_advect_scales_follow_each_input():
 
 
 def test_advect_full_size():
-    """512 x 512 x 256, winds per the benchmark recipe, oracle on all cores."""
+    """512 x 512 x 256, winds per the benchmark recipe, oracle on all cores;
+    every compiled tile shape (at this size each keeps its own z chunk
+    length); the default shape twice on one context, as the benchmark
+    times it.  The normwise error is taken on the GPU (binary64)."""
+    import torch
+    from paper_2310_01882_b300.stencil import Context
     u, v, w = inputs.winds(512, 512, 256)
     t1, t2 = inputs.tzc(256, 7), inputs.tzc(256, 8)
-    ref = oracle.advect_uvw(u, v, w, t1, t2, 0.25, 0.25, nthreads=0)
-    got = run_advect(u, v, w, t1, t2)
-    for g, r in zip(got, ref):
-        assert rel_err(g, r) <= 1e-13
+    ref = [torch.from_numpy(r[1:-1, 1:-1, 1:-1].copy()).cuda()
+           for r in oracle.advect_uvw(u, v, w, t1, t2, 0.25, 0.25, nthreads=0)]
+    fu, fv, fw = (S.Field.from_numpy(a) for a in (u, v, w))
+    d1, d2 = torch.from_numpy(t1).cuda(), torch.from_numpy(t2).cuda()
+    outs = [fu.like() for _ in range(3)]
+    for idx in range(S.stencil_advect_config_count()):
+        c = Context(0)
+        S.stencil_advect_config_select(c, idx)
+        for call in range(2 if idx == 0 else 1):
+            for o in outs:
+                o.cells.fill_(float("nan"))
+            S.stencil_advect_uvw(c, fu, fv, fw, *outs, d1, d2, 0.25, 0.25)
+            for o, r in zip(outs, ref):
+                err = ((o.cells[1:-1, 1:-1, 1:-1] - r).abs().max() / r.abs().max()).item()
+                assert err <= 1e-13, (idx, call, err)
+        c.close()
 
 
 def test_advect_constant_fields_zero():
