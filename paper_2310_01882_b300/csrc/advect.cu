@@ -460,7 +460,8 @@ __device__ __forceinline__ void advect_march(const double* __restrict__ u, const
 // One pass of the advection.  The first pass takes its scales from the
 // record `prev` (the previous call's, or the range pass's on a context's
 // first call) and records into `cur` the magnitudes it reads: the fields'
-// and the factors' (tcx, tcy and the tzc entries of its planes).  The
+// and the factors' (tcx, tcy and the tzc entries, recorded by the CTAs of
+// column (0, 0), whose chunks cover every plane).  The
 // second pass compares the decision (fixed point or binary64) and the
 // scales that `prev` gave with those of what the first pass read, and
 // runs only when they differ, with the scales of `cur`; it records nothing
@@ -498,22 +499,6 @@ __global__ void __launch_bounds__(32 * BY, MINB)
   const int64_t j0 = static_cast<int64_t>(blockIdx.y) * BY * RPT;
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * zc;
   const int kn = static_cast<int>(min(static_cast<int64_t>(zc), nz - k0));  // cells of this chunk along z
-  if (!ps.second) {
-    // the factors this chunk reads (tcx, tcy and its planes' tzc1, tzc2),
-    // gathered in shared memory
-    auto take = [&](double x) {
-      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
-      atomicMax(&fac[0], b);
-      if (b != 0) atomicMax(&fac[1], ~b);
-    };
-    if (tid == 0) fac[0] = fac[1] = 0ull;
-    __syncthreads();
-    if (tid == 0) {
-      take(tcx);
-      take(tcy);
-    }
-    if (tid < 2 * kn) take((tid & 1) ? tzc2[k0 + (tid >> 1)] : tzc1[k0 + (tid >> 1)]);
-  }
   uint32_t mx[3] = {0u, 0u, 0u};  // largest high words of |u|, |v|, |w| read
   if (!sc.fixed) {  // uniform over the launch
     // the magnitudes of the cells the fixed-point path would have loaded
@@ -555,10 +540,30 @@ __global__ void __launch_bounds__(32 * BY, MINB)
     if ((threadIdx.x & 31) == 0 && m)
       atomicMax(ps.cur + f, (static_cast<unsigned long long>(m) << 32) | 0xffffffffull);
   }
-  __syncthreads();
-  if (tid == 0) {
-    if (fac[0]) atomicMax(ps.cur + 3, fac[0]);
-    if (fac[1]) atomicMax(ps.cur + 4, fac[1]);
+  // the factors (tcx, tcy, tzc1, tzc2): the chunks of column (0, 0) read
+  // every plane's between them, so they alone record the factors' range,
+  // after their march (uniform per CTA), gathered in shared memory first
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    auto take = [&](double x) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x)) & kAbsMask;
+      atomicMax(&fac[0], b);
+      if (b != 0) atomicMax(&fac[1], ~b);
+    };
+    if (t == 0) fac[0] = fac[1] = 0ull;
+    __syncthreads();
+    if (t == 0) {
+      take(tcx);
+      take(tcy);
+    }
+    const int64_t kb = static_cast<int64_t>(blockIdx.z) * zc;
+    const int kc = static_cast<int>(min(static_cast<int64_t>(zc), nz - kb));
+    if (t < 2 * kc) take((t & 1) ? tzc2[kb + (t >> 1)] : tzc1[kb + (t >> 1)]);
+    __syncthreads();
+    if (t == 0) {
+      if (fac[0]) atomicMax(ps.cur + 3, fac[0]);
+      if (fac[1]) atomicMax(ps.cur + 4, fac[1]);
+    }
   }
 }
 
@@ -604,11 +609,18 @@ int launch_advect(stencil_ctx* ctx, const Grid& u, const Grid& v, const Grid& w,
   const AdvVariant& av =
       kAdvVariants[(ctx->advect_choice >= 0 && ctx->advect_choice < kNumAdvVariants) ? ctx->advect_choice : 0];
   const int64_t gx = (u.nx + 31) / 32, gy = (u.ny + av.BY * av.rpt - 1) / (av.BY * av.rpt);
-  // z chunk: the longest (up to the shape's, and to what the factor table
-  // holds when one thread fills each entry) that still gives every SM two
-  // rounds of CTAs
-  int zc = std::min(av.zc, std::min(kAdvZcMax, 16 * av.BY));
-  while (zc > 4 && gx * gy * ((u.nz + zc - 1) / zc) < int64_t(2) * av.minb * ctx->num_sms) zc /= 2;
+  // z chunk: the longest of these lengths (up to the shape's, and to what
+  // the factor table holds when one thread fills each entry) that still
+  // gives four rounds of resident CTAs (on smaller grids the last, partly
+  // filled round costs more than the two planes each chunk re-reads)
+  const int zmax = std::min(av.zc, std::min(kAdvZcMax, 16 * av.BY));
+  static const int kChunks[] = {128, 64, 48, 32, 24, 16, 12, 8, 6, 4};
+  int zc = 4;
+  for (int c : kChunks)
+    if (c <= zmax && gx * gy * ((u.nz + c - 1) / c) >= int64_t(4) * av.minb * ctx->num_sms) {
+      zc = c;
+      break;
+    }
   const int64_t gz = (u.nz + zc - 1) / zc;
   if (gx > 0x7fffffff || gy > 65535 || gz > 65535) return set_error(STENCIL_ERR_ARG, "advect: grid too large");
   // tcx and tcy positive powers of two (within the fixed-point range): their
