@@ -550,7 +550,8 @@ STENCIL_API int wsnet_loss_grad(wsnet* net, const float* x, const float* t,
  *   reproducible run to run.
  *   The first call in each CUDA context on a device looks up the array's
  *   device address (with that device current; again after the context is
- *   replaced, e.g. by cudaDeviceReset).  Every call on a device shares
+ *   replaced, e.g. by cudaDeviceReset); make that first call before any
+ *   stream capture on the device.  Every call on a device shares
  *   the one array: calls that overlap on the GPU (different streams, or
  *   threads without ordering) race and give wrong norms.  Each call
  *   overwrites every partial sum it reads, so nothing has to be cleared

@@ -285,7 +285,8 @@ static __device__ __align__(256) double g_noalloc_partials[2 * kNoAllocMaxPartia
 // first call in each context and kept per device together with that
 // context's unique id, so a new context on the device -- after
 // cudaDeviceReset, or one the caller created with the driver API -- gets its
-// own lookup instead of a stale address.
+// own lookup instead of a stale address.  The first call in a context
+// belongs before any stream capture on the device.
 static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 static unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};
